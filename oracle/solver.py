@@ -1,0 +1,230 @@
+"""Adaptive Dormand-Prince driver, step control, rollback and sparsification.
+
+Secs. 3.1 (the step recipe), 3.5 (adaptive ODE solver) and 3.6 (selective history
+reduction). Readings where the paper is silent:
+
+* Step rule (Sec. 3.5): eps_RK = sum_i |dC_i| + |dR_i| from the embedded 4th-order
+  estimate. eps_RK > 2 tol: reject, revert the last min(10, N-1) stored slices and
+  halve dt. Otherwise accept; then dt *= 0.9 if eps_RK > tol, dt *= 1.01 if
+  eps_RK < tol/2. dt < dt_min ends the run with status "step underflow" (App. B).
+  The last step is shortened to land on t_max.
+* The stored derivative of a slice is the right-hand side at that slice (DP's
+  FSAL stage k7), so k1 of the next step is the stored derivative.
+* Sparsification (Sec. 3.6): candidates n = 1 .. N-12 (slice 0, the last slice
+  and the 10-slice rollback window are kept). eps_sparse(n) = sum_i |Delta^C| +
+  |Delta^R| with Delta the difference of the integrals over [t_{n-1}, t_{n+1}] of
+  the Hermite interpolants with and without slice n. Scanning n upwards, n is
+  removed if eps_sparse(n) < tol/10, and then n+1 is skipped. A pass runs when
+  the store is full; if it frees nothing, the candidate with the smallest
+  eps_sparse is removed and counted as forced.
+
+Pins: tests/test_oracle_solver.py (DP5 order and error-estimate order on scalar
+ODEs, the p = 2 energy against the closed form, f = 0 exact solution, agreement
+with the brute-force uniform-grid solver, equilibrium FDT above T_d, the Hermite
+integral identity and cubic slices being removed by sparsification).
+"""
+
+import numpy as np
+
+from .integrals import Grid, History, rhs
+from .interp import lagrange_stencil, hermite, hermite_integral
+from . import grid as gridmod
+
+# Dormand & Prince (1980) RK5(4)7M tableau.
+DP_C = np.array([0.0, 1 / 5, 3 / 10, 4 / 5, 8 / 9, 1.0, 1.0])
+DP_A = [
+    [],
+    [1 / 5],
+    [3 / 40, 9 / 40],
+    [44 / 45, -56 / 15, 32 / 9],
+    [19372 / 6561, -25360 / 2187, 64448 / 6561, -212 / 729],
+    [9017 / 3168, -355 / 33, 46732 / 5247, 49 / 176, -5103 / 18656],
+    [35 / 384, 0.0, 500 / 1113, 125 / 192, -2187 / 6784, 11 / 84],
+]
+DP_B5 = np.array([35 / 384, 0.0, 500 / 1113, 125 / 192, -2187 / 6784, 11 / 84, 0.0])
+DP_B4 = np.array([5179 / 57600, 0.0, 7571 / 16695, 393 / 640, -92097 / 339200, 187 / 2100, 1 / 40])
+DP_E = DP_B5 - DP_B4
+
+OK, ERR_STEP_UNDERFLOW, ERR_CAPACITY, ERR_NONFINITE = 0, -4, -5, -3
+
+
+def dp5_step(f, t, y, h, k1):
+    """One Dormand-Prince 5(4) step of y' = f(t, y) with k1 = f(t, y) given (FSAL).
+
+    Returns (y_new, err, ks): the 5th-order solution, the embedded error estimate
+    h * sum_l e_l k_l and the seven stage derivatives (ks[6] = f(t + h, y_new)).
+    """
+    ks = [k1]
+    for st in range(1, 7):
+        yk = y + h * sum(DP_A[st][l] * ks[l] for l in range(st))
+        ks.append(f(t + DP_C[st] * h, yk))
+    y_new = y + h * sum(DP_B5[l] * ks[l] for l in range(7))
+    err = h * sum(DP_E[l] * ks[l] for l in range(7))
+    return y_new, err, ks
+
+
+def sparsify_residuals(hist):
+    """eps_sparse(n) for every slice n = 1 .. N-2 (Sec. 3.6); entry n of the result."""
+    t = hist.t
+    N = hist.N
+    eps = np.full(N, np.inf)
+    for n in range(1, N - 1):
+        h1, h2 = t[n] - t[n - 1], t[n + 1] - t[n]
+        tot = 0.0
+        for Y, dY in ((hist.C, hist.dC), (hist.R, hist.dR)):
+            with_n = hermite_integral(Y[n - 1], dY[n - 1], Y[n], dY[n], h1) + \
+                hermite_integral(Y[n], dY[n], Y[n + 1], dY[n + 1], h2)
+            without = hermite_integral(Y[n - 1], dY[n - 1], Y[n + 1], dY[n + 1], h1 + h2)
+            tot += np.sum(np.abs(with_n - without))
+        eps[n] = tot
+    return eps
+
+
+def sparsify_pass(hist, tol, stats=None):
+    """One pass of Sec. 3.6 on a full store; returns the thinned history."""
+    N = hist.N
+    last = N - 12
+    if last < 1:
+        return hist, False
+    eps = sparsify_residuals(hist)
+    keep = np.ones(N, dtype=bool)
+    n = 1
+    removed = 0
+    while n <= last:
+        if eps[n] < tol / 10.0:
+            keep[n] = False
+            removed += 1
+            if stats is not None:
+                stats["max_eps_sparse"] = max(stats["max_eps_sparse"], eps[n])
+            n += 2
+        else:
+            n += 1
+    if removed == 0:
+        m = 1 + int(np.argmin(eps[1:last + 1]))
+        keep[m] = False
+        removed = 1
+        if stats is not None:
+            stats["forced_removals"] += 1
+            stats["max_eps_sparse"] = max(stats["max_eps_sparse"], eps[m])
+    if stats is not None:
+        stats["sparsify_passes"] += 1
+        stats["slices_removed"] += removed
+    return hist.keep(keep), True
+
+
+class Solver:
+    """Plain FP64 solver state: grid, model, history and step control."""
+
+    def __init__(self, coefs, T, L, grid_t_max, s=4, beta0=0.0, alpha=0.0, delta=0.0,
+                 history_cap=None, dt0=1e-4, dt_min=1e-12, sparsify=True):
+        from .model import Model
+        self.model = Model(coefs, T, beta0)
+        self.grid = Grid(L, grid_t_max, s, alpha, delta)
+        self.cap = int(history_cap if history_cap is not None else L)
+        if self.cap < 16:
+            raise ValueError("history_cap must be at least 16")
+        self.dt = float(dt0)
+        self.dt_min = float(dt_min)
+        self.sparsify = sparsify
+        ones = np.ones(L)
+        dC0, dR0, mu0, E0 = rhs(self.model, self.grid, None, 0.0, ones, ones)
+        self.hist = History([0.0], ones[None, :], dC0[None, :], ones[None, :], dR0[None, :])
+        self.mu, self.E = mu0, E0
+        self.stats = dict(steps_accepted=0, steps_rejected=0, rhs_evals=0, sparsify_passes=0,
+                          slices_removed=0, forced_removals=0, max_eps_sparse=0.0)
+        self.log = []  # (t, h, eps_RK, accepted)
+
+    @property
+    def t(self):
+        return self.hist.t[-1]
+
+    def _f(self, t, y):
+        L = self.grid.L
+        dC, dR, _, _ = rhs(self.model, self.grid, self.hist, t, y[:L], y[L:])
+        self.stats["rhs_evals"] += 1
+        return np.concatenate([dC, dR])
+
+    def step(self, h):
+        """Trial step of size h from the last slice; returns (y_new, k7, eps_RK)."""
+        L = self.grid.L
+        y = np.concatenate([self.hist.C[-1], self.hist.R[-1]])
+        k1 = np.concatenate([self.hist.dC[-1], self.hist.dR[-1]])
+        y_new, err, ks = dp5_step(self._f, self.t, y, h, k1)
+        return y_new, ks[6], float(np.sum(np.abs(err)))
+
+    def integrate(self, t_max, tol):
+        """Advance to t_max (Secs. 3.1, 3.5, 3.6); returns a status code."""
+        L = self.grid.L
+        while self.t < t_max:
+            h = min(self.dt, t_max - self.t)
+            t0 = self.t
+            y_new, k7, eps = self.step(h)
+            if not np.isfinite(eps):
+                return ERR_NONFINITE
+            if eps > 2.0 * tol:
+                self.log.append((t0, h, eps, False))
+                self.stats["steps_rejected"] += 1
+                drop = min(10, self.hist.N - 1)
+                self.hist = self.hist.keep(np.arange(self.hist.N) < self.hist.N - drop)
+                self.dt *= 0.5
+            else:
+                self.log.append((t0, h, eps, True))
+                self.stats["steps_accepted"] += 1
+                if self.hist.N >= self.cap:
+                    if not self.sparsify:
+                        return ERR_CAPACITY
+                    self.hist, ran = sparsify_pass(self.hist, tol, self.stats)
+                    if not ran:
+                        return ERR_CAPACITY
+                t1 = t0 + h if h < t_max - t0 else t_max
+                self.hist = self.hist.append(t1, y_new[:L], k7[:L], y_new[L:], k7[L:])
+                if eps > tol:
+                    self.dt *= 0.9
+                elif eps < 0.5 * tol:
+                    self.dt *= 1.01
+            if self.dt < self.dt_min:
+                return ERR_STEP_UNDERFLOW
+        C, R = self.hist.C[-1], self.hist.R[-1]
+        from .integrals import row_prep
+        _, _, self.mu, self.E = row_prep(self.model, self.grid, self.t, C, R)
+        return OK
+
+    def get_C(self, t, tp):
+        return get_two_time(self.grid, self.hist, t, tp, "C")
+
+    def get_R(self, t, tp):
+        return get_two_time(self.grid, self.hist, t, tp, "R")
+
+
+def get_two_time(grid, hist, t, tp, which):
+    """C(t, t') (symmetric) or R(t, t') (0 for t' > t) from the stored history.
+
+    The slice interval containing max(t, t') is found, the theta stencil is placed
+    at t_small / t_big on both slices and the result is Hermite-interpolated in t.
+    """
+    t = np.atleast_1d(np.asarray(t, dtype=float))
+    tp = np.atleast_1d(np.asarray(tp, dtype=float))
+    t, tp = np.broadcast_arrays(t, tp)
+    out = np.zeros(t.shape)
+    big = np.maximum(t, tp)
+    small = np.minimum(t, tp)
+    if np.any(big > hist.t[-1] * (1 + 1e-15)):
+        raise ValueError("time beyond the stored history")
+    ok = np.ones(t.shape, dtype=bool) if which == "C" else (tp <= t)
+    pos = big > 0
+    th = np.where(pos, small / np.where(pos, big, 1.0), 1.0)
+    om = np.where(pos, (big - small) / np.where(pos, big, 1.0), 0.0)
+    x = gridmod.frac_index(th, om, grid.L, grid.gamma, grid.alpha, grid.delta)
+    b, w = lagrange_stencil(x, grid.L, grid.s)
+    Y, dY = (hist.C, hist.dC) if which == "C" else (hist.R, hist.dR)
+    N = hist.N
+    if N == 1:
+        val = sum(w[..., k] * Y[0, b + k] for k in range(grid.s))
+    else:
+        n = np.clip(np.searchsorted(hist.t, big, side="right") - 1, 0, N - 2)
+        h = hist.t[n + 1] - hist.t[n]
+        sig = (big - hist.t[n]) / h
+        g = lambda rows, m: sum(w[..., k] * rows[m, b + k] for k in range(grid.s))
+        val = hermite(g(Y, n), g(dY, n), g(Y, n + 1), g(dY, n + 1), h, sig)
+    out[ok] = val[ok]
+    return out
