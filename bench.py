@@ -1,0 +1,307 @@
+"""Benchmark: Dormand-Prince steps of the DMFE history-integral path on GB300.
+
+Workload (mixed (3+4)-spin, f = (q^3 + q^4)/4, T = 0.5, theta grid L = 2049 for
+t_max = 1e5, stencil width 4, history store of 2049 slices, FP64): one step is one
+device-driven Dormand-Prince trial step -- six stages of (history integrals, RHS
+assembly), the error estimate and step rule, the append, and a sparsification pass
+whenever the store is full. The state is a seeded synthetic history of 2049 - 6
+slices on geometric times in [1e-2, 9e4], so that the store fills and a pass runs
+inside the timed steps.
+
+value: trial steps per second over all ranks (device time, CUDA events on the
+solver's stream, barrier + synchronize around the timed region, max over ranks).
+e2e: the same through the public C ABI from the host: per step dmfe_step(1) and a
+dmfe_get_row read of the new row (device -> host), synchronised.
+roofline: the history-integral kernel, timed alone with CUDA events on the same state.
+
+--impl reference runs the FP64 CPU oracle on the same workload (a bounded sample of
+output rows per step, scaled to whole steps).
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+COEFS = {3: 0.25, 4: 0.25}
+T_BATH = 0.5
+GRID_T_MAX = 1e5
+TOL = 1e-8
+# Algorithmic FP64 operations per (i, j) pair of the FP64 kernel at stencil width 4,
+# counted from the source (FMA = 2): interpolation weights 3 x 16, A1 4 x 4 FMA, A2
+# 2 x 4 FMA, B1 2 x 4 FMA, B2 2 x 4 x 4 FMA + 2 x 4 FMA Hermite + 14 time weights,
+# f' and f'' at two points (10 FMA), nine products and sums (27).
+FLOP_PER_PAIR_S4 = 48 + 32 + 16 + 16 + 64 + 16 + 14 + 20 + 27
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--L", type=int, default=2049)
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="only launch the history-integral kernel (for profiler captures)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(L):
+    from paper_2604_06309_gb300.inputs import geometric_times
+    n = L - 6
+    return n, geometric_times(n, 1e-2, 9e4)
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, idx):
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench.csv"
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(idx), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        self.p.wait()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        mx = max(r[1] for r in rows)
+        loaded = [r[0] for r in rows if r[0] > 0.5 * mx] or [r[0] for r in rows]
+        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2604_06309_gb300 import Solver
+    from paper_2604_06309_gb300.inputs import synthetic_history
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        return _run_ours(args, rank, world, dev, stream)
+
+
+def _run_ours(args, rank, world, dev, stream):
+    import torch
+    from paper_2604_06309_gb300 import Solver
+    from paper_2604_06309_gb300.inputs import synthetic_history
+    L = args.L
+    n0, times = workload(L)
+    sv = Solver(COEFS, T_BATH, L, GRID_T_MAX, s=4, history_cap=L, precision=args.precision,
+                dt0=1e-2, stream=stream.cuda_stream)
+    C, dC, R, dR = synthetic_history(20260406 + rank, times, sv.theta, sv.omega)
+    sv.set_history(times, C, dC, R, dR)
+    row = torch.tensor(np.concatenate([C[-1], R[-1]]), dtype=torch.float64, device="cuda")
+    S = torch.empty((10, L), dtype=torch.float64, device="cuda")
+    flush = torch.empty(int(256 * 2 ** 20), dtype=torch.uint8, device="cuda")
+    t_frozen = float(times[-1])
+
+    if args.kernel_only:
+        for _ in range(args.warmup + args.steps):
+            sv.history_integrals_dev(t_frozen, row.data_ptr(), S.data_ptr(), stream.cuda_stream)
+        torch.cuda.synchronize()
+        return None
+
+    # ---- kernel alone: history integrals on the frozen state (L2 flushed before each)
+    kt = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sv.history_integrals_dev(t_frozen, row.data_ptr(), S.data_ptr(), stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            kt.append(e0.elapsed_time(e1) * 1e-3)
+    k_avg = float(np.mean(kt))
+
+    # ---- device-timed steps
+    sv.step(args.warmup, GRID_T_MAX, TOL, stream.cuda_stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(dev)
+    evs = []
+    for k in range(args.steps):
+        flush.zero_()  # inputs exceed L2 for FP64; the flush keeps FP32 honest too
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sv.step(1, GRID_T_MAX, TOL, stream.cuda_stream)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    dev_time = float(sum(a.elapsed_time(b) for a, b in evs) * 1e-3)
+    st = sv.stats()
+    if st["status"] != 0:
+        raise RuntimeError("device status %d during the timed steps" % st["status"])
+
+    # ---- end to end through the public API (host buffers, synchronous row read)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sv.step(1, GRID_T_MAX, TOL)
+        sv.get_row()
+    e2e_time = time.perf_counter() - t0
+    st2 = sv.stats()
+
+    pairs = L * L
+    n_mid = st["n_slices"]
+    bytes_hist = 4 * n0 * L * (8 if args.precision == "fp64" else 4)
+    bytes_tab = 3 * pairs * (8 if args.precision == "fp64" else 4)
+    bytes_io = 2 * L * 8 + 10 * L * 8
+    res = dict(dev_time=dev_time, e2e_time=e2e_time, k_avg=k_avg, clocks=clk, stats=st, stats_after=st2,
+               bytes=(bytes_hist, bytes_tab, bytes_io), pairs=pairs, n0=n0)
+    sv.close()
+    return res
+
+
+class OracleSample:
+    """The oracle on the same workload: one stage of history integrals on a sample of
+    output rows, scaled to a whole step (6 stages x L rows)."""
+
+    def __init__(self, L):
+        from oracle import integrals as OI
+        from oracle.model import Model
+        from paper_2604_06309_gb300.inputs import synthetic_history
+        self.OI, self.L = OI, L
+        n0, times = workload(L)
+        self.G = OI.Grid(L, GRID_T_MAX, 4)
+        C, dC, R, dR = synthetic_history(20260406, times, self.G.theta, self.G.omega)
+        self.H = OI.History(times, C, dC, R, dR)
+        self.model = Model(COEFS, T_BATH)
+        self.t, self.C, self.R = float(times[-1]), C[-1], R[-1]
+
+    def step_time(self, rows):
+        js = np.linspace(0, self.L - 1, rows).astype(int)
+        t0 = time.perf_counter()
+        self.OI.history_integrals(self.model, self.G, self.H, self.t, self.C, self.R, js=js)
+        el = time.perf_counter() - t0
+        return el * (self.L / rows) * 6, el
+
+
+def cpu_baseline(L, rows=512):
+    o = OracleSample(L)
+    per_step, el = o.step_time(rows)
+    return {"value": 1.0 / per_step, "unit": "RK steps/s", "cores": 1, "kind": "oracle",
+            "sample": "history integrals of %d of %d output rows for one stage (%.1f s of CPU), "
+                      "scaled to all rows and 6 stages per step" % (rows, L, el)}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    cfg = {"workload": "mixed (3+4)-spin T=0.5 quench, theta grid L=%d (t_max 1e5), %d-slice store, s=4"
+                       % (args.L, args.L),
+           "model": "spherical mixed p-spin DMFE, f=(q^3+q^4)/4", "global_batch": world, "seq_len": args.L,
+           "parallelism": "replicas x%d" % world, "l2": "flushed before every timed step (256 MB write)"}
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        o = OracleSample(args.L)
+        steps_t = [o.step_time(64)[0] for _ in range(args.warmup + args.steps)]
+        v = 1.0 / float(np.mean(steps_t[args.warmup:]))
+        line = {"impl": "reference", "metric": "RK steps/s", "value": v, "unit": "RK steps/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+                "cpu_baseline": {"value": v, "unit": "RK steps/s", "cores": 1, "kind": "oracle",
+                                 "sample": "per step: history integrals of 64 of %d output rows, one stage, scaled to 6 stages x all rows" % args.L},
+                "e2e": {"value": v, "unit": "RK steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, rank, world)
+    if res is None:
+        return
+    dev_time = res["dev_time"]
+    if world > 1:
+        t = torch.tensor([dev_time, res["e2e_time"]], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dev_time, e2e_time = float(t[0]), float(t[1])
+    else:
+        e2e_time = res["e2e_time"]
+    if rank != 0:
+        return
+    value = world * args.steps / dev_time
+    hbm, src = peaks()
+    bh, bt, bio = res["bytes"]
+    k = res["k_avg"]
+    L = args.L
+    if args.precision == "fp64":
+        flops = res["pairs"] * FLOP_PER_PAIR_S4
+        fp64_peak = 1250.0  # GFLOP/s, nominal GB300 FP64 (derived peak)
+        roof = {"kernel": "k_hi_f64 (history integrals)", "bound": "alu", "achieved": flops / k / 1e9,
+                "peak": fp64_peak, "unit": "GFLOP/s", "frac": flops / k / 1e9 / fp64_peak, "traffic": None,
+                "peak_source": "nominal FP64 1.25 TFLOP/s", "algorithmic_bytes": bh + bt + bio,
+                "hbm_frac_of_%s" % src: (bh + bt + bio) / k / 1e9 / hbm, "kernel_ms": k * 1e3}
+    else:
+        ach = (bh + bt + bio) / k / 1e9
+        roof = {"kernel": "k_hi_f32 (history integrals)", "bound": "hbm", "achieved": ach, "peak": hbm,
+                "unit": "GB/s", "frac": ach / hbm, "traffic": None, "peak_source": src,
+                "algorithmic_bytes": bh + bt + bio, "history_bytes": bh, "table_bytes": bt, "kernel_ms": k * 1e3}
+    line = {"metric": "RK steps/s", "value": value, "unit": "RK steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dev_time / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic", "config": cfg,
+            "e2e": {"value": world * args.steps / e2e_time, "unit": "RK steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 2 * L * 8 + 3 * 8},
+            "gpu_launches": args.steps * 18,
+            "roofline": roof, "clocks": res["clocks"],
+            "solver": {k2: res["stats"][k2] for k2 in ("steps_accepted", "steps_rejected", "sparsify_passes",
+                                                        "slices_removed", "n_slices", "dt", "last_eps")}}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(L)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

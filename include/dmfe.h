@@ -1,0 +1,184 @@
+/*
+ * dmfe.h -- C ABI of libdmfe.so, a GB300 (sm_103a) solver for the causal history
+ * integrals of the spherical mixed p-spin dynamical mean-field equations on the
+ * non-uniform two-time grid (DYNAMITE, arXiv 2604.06309).
+ *
+ * Fields are stored on the grid (t_n, theta_i t_n): Cf(t, theta) = C(t, theta t),
+ * Rf(t, theta) = R(t, theta t) (Sec. 3.1). theta_i, i = 0..L-1, is the fixed grid of
+ * Eq. (theta) (Sec. 3.2); t_n are the slices accepted by the adaptive Dormand-Prince
+ * integrator (Sec. 3.5), thinned by sparsification (Sec. 3.6).
+ *
+ * Conventions for every entry point:
+ *  - Return value: DMFE_OK (0) or a negative DMFE_ERR_* code; dmfe_strerror maps it
+ *    to text. A failed call leaves the solver at its last accepted slice, readable.
+ *  - Pointers named *_dev are device pointers; every other pointer is host memory,
+ *    owned by the caller, read or written only during the call.
+ *  - Rows are double arrays of length L in grid order (theta ascending). Histories
+ *    are row-major [n][L].
+ *  - One solver must not be used from two host threads at once; distinct solvers
+ *    are independent (the library keeps no global state besides the CUDA context).
+ *  - The solver owns all its device memory; dmfe_destroy frees it.
+ */
+#ifndef DMFE_H
+#define DMFE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define DMFE_OK                  0
+#define DMFE_ERR_ARG            -1  /* invalid argument or size                        */
+#define DMFE_ERR_OOM            -2  /* device or host allocation failed                 */
+#define DMFE_ERR_NONFINITE      -3  /* NaN/Inf in the step error estimate               */
+#define DMFE_ERR_STEP_UNDERFLOW -4  /* step below dt_min: the run ends (App. B)         */
+#define DMFE_ERR_CAPACITY       -5  /* history full and sparsification disabled         */
+#define DMFE_ERR_CUDA           -6  /* a CUDA runtime call failed                       */
+#define DMFE_ERR_TIMEOUT        -7  /* a bounded device wait gave up                    */
+#define DMFE_ERR_UNSUPPORTED    -8  /* valid but not implemented (e.g. stencil width)   */
+#define DMFE_ERR_IO             -9  /* checkpoint file could not be written or read     */
+
+/* ---- precision of the history-integral bulk -------------------------------- */
+#define DMFE_FP64              0  /* everything in FP64                                 */
+#define DMFE_FP32_COMPENSATED  1  /* interpolation and sums in FP32 with compensated
+                                     (Kahan) accumulation over an FP32 history replica;
+                                     times, theta, mu, the RK error, step control and
+                                     the sparsification test stay FP64                 */
+
+#define DMFE_NS 10   /* rows of the history-integral output S, see dmfe_history_integrals */
+#define DMFE_MAX_TERMS 16
+#define DMFE_MAX_POWER 24
+
+typedef struct dmfe_solver dmfe_solver;
+
+/* Problem and numerical parameters (Secs. 2.1, 3.2, 3.5, 3.6). */
+typedef struct {
+    int           n_terms;      /* f(q) = sum_k coefs[k] q^powers[k], 1 <= n_terms <= 16   */
+    const int*    powers;       /* 1 <= powers[k] <= 24; copied at create                  */
+    const double* coefs;        /* copied at create                                        */
+    double        T;            /* bath temperature                                        */
+    double        beta0;        /* inverse temperature of the initial state (0: random)   */
+    int           L;            /* theta-grid length, 16 <= L <= 8192                      */
+    int           s;            /* theta stencil width: 4, 6, 8 or 10                      */
+    double        grid_t_max;   /* t_max of Eq. (theta): gamma = -W_{-1}(-1/grid_t_max) > 1 */
+    double        alpha, delta; /* trade-off parameters of Eq. (theta) (default 0, 0)      */
+    int           history_cap;  /* stored slices, >= 16 (default L)                        */
+    double        dt0, dt_min;  /* initial and minimal step (defaults 1e-4, 1e-12)         */
+    int           precision;    /* DMFE_FP64 or DMFE_FP32_COMPENSATED                      */
+    int           sparsify;     /* 1: sparsification pass whenever the store is full (default);
+                                   0: off (a full store ends the run with DMFE_ERR_CAPACITY) */
+    void*         stream;       /* cudaStream_t for all work; NULL: the solver's own stream */
+} dmfe_params;
+
+/* Per-solve counters. */
+typedef struct {
+    double    t;                 /* time of the last accepted slice           */
+    double    dt;                /* current controller step                   */
+    double    mu, E;             /* mu(t) and E(t) of the last slice (Sec. 2.1) */
+    double    last_eps;          /* eps_RK of the last trial step (Sec. 3.5)  */
+    double    max_eps_sparse;    /* largest eps_sparse of a removed slice     */
+    long long steps_accepted, steps_rejected, stages;
+    long long sparsify_passes, slices_removed, forced_removals;
+    int       n_slices;          /* stored slices                             */
+    int       status;            /* device status word (0 or DMFE_ERR_*)      */
+    int       L, history_cap;    /* sizes fixed at create                     */
+    int       s, precision;
+} dmfe_stats_t;
+
+/* Fill p with defaults for the given f (pointers are kept, not copied). */
+void dmfe_default_params(dmfe_params* p);
+
+const char* dmfe_strerror(int code);
+
+/* Create a solver: builds the theta grid and nu (host, FP64), the stencil tables on
+ * the device (kernel a), allocates the history at history_cap slices and stores the
+ * initial slice t = 0, Cf = Rf = 1 with its derivative. Returns DMFE_ERR_ARG for
+ * parameters outside the ranges above, DMFE_ERR_UNSUPPORTED for other stencil widths. */
+int  dmfe_create(const dmfe_params* p, dmfe_solver** out);
+void dmfe_destroy(dmfe_solver* h);
+
+/* Grid of Eq. (theta) and the quadrature weights nu of Sec. 3.4 (host arrays of L). */
+int dmfe_grid(dmfe_solver* h, double* theta, double* omega, double* nu);
+
+/* Fractional stencil positions of kernel (a), FP64, [L][L] each, row j = output index:
+ * x1 for phi1 = theta_i theta_j, x2 for phi2 = theta_j + (1 - theta_j) theta_i,
+ * x3 for psi = theta_j / phi2 (Sec. 3.3). Any pointer may be NULL. */
+int dmfe_tables(dmfe_solver* h, double* x1, double* x2, double* x3);
+
+/* Advance with adaptive Dormand-Prince 5(4) to t_max <= grid_t_max with tolerance tol
+ * (Secs. 3.1, 3.5, 3.6). Step control runs on the device; the host polls a status
+ * word. Returns DMFE_ERR_STEP_UNDERFLOW, DMFE_ERR_NONFINITE or DMFE_ERR_CAPACITY when
+ * the device stops the run; the solver then holds the last accepted slice. */
+int dmfe_integrate(dmfe_solver* h, double t_max, double tol);
+
+/* Launch exactly nsteps Dormand-Prince trial steps toward t_max with tolerance tol on
+ * the solver's stream (or `stream` if not NULL) without synchronising: each step is one
+ * CUDA-graph launch of the stages, the device-side step rule and, when the store is
+ * full, a sparsification pass. Steps after t_max is reached or after a device error
+ * do nothing. dmfe_sync / dmfe_stats read the outcome. Used by benchmarks and by
+ * callers that interleave their own work between steps. */
+int dmfe_step(dmfe_solver* h, int nsteps, double t_max, double tol, void* stream);
+
+/* Two-time functions at n points (t[k], tp[k]), both <= the current time:
+ * C is symmetric; R(t, t') = 0 for t' > t (causality, Sec. 2.2). Cubic Hermite in t
+ * between stored slices and the theta stencil at t_small/t_big (Sec. 3.3). */
+int dmfe_get_C(dmfe_solver* h, int n, const double* t, const double* tp, double* out);
+int dmfe_get_R(dmfe_solver* h, int n, const double* t, const double* tp, double* out);
+
+/* Last accepted slice: time, rows Cf, Rf (length L, may be NULL), mu(t), E(t). */
+int dmfe_get_row(dmfe_solver* h, double* t, double* C, double* R, double* mu, double* E);
+
+/* Replace the stored history by n slices (1 <= n <= history_cap): times t[n] with
+ * t[0] = 0 strictly increasing, rows C, dC, R, dR [n][L] (dC, dR: d/dt at fixed theta).
+ * Used for frozen-history benchmarks and parity tests. */
+int dmfe_set_history(dmfe_solver* h, int n, const double* t, const double* C,
+                     const double* dC, const double* R, const double* dR);
+/* Copy the stored history out; *n receives the slice count, arrays must hold
+ * history_cap slices (any array may be NULL). */
+int dmfe_get_history(dmfe_solver* h, int* n, double* t, double* C, double* dC,
+                     double* R, double* dR);
+
+/* The history integrals of one Runge-Kutta stage (Secs. 3.3, 3.4, Eq. int) at time
+ * t >= t_last for the stage row (C_row, R_row) over the stored history, and mu(t)
+ * (Sec. 2.1). Output S is [DMFE_NS][L]; with t' = theta_j t and the interpolated
+ * values A (current row at phi1 or phi2), B1 = (C, R)(theta_j t, theta_i),
+ * B2 = (C, R)(phi2 t, theta_j/phi2):
+ *   S[0] = sum_i nu_i K_A1 C_B1   S[1] = sum nu K_A2 C_B2   S[2] = sum nu D_A1 R_B1
+ *   S[3] = sum nu K_A2 R_B2       S[4] = sum nu f''(C_B1) R_B1 C_A1
+ *   S[5] = sum nu f'(C_B1) R_A1   S[6] = sum nu f'(C_B2) R_A2
+ *   S[7] = sum nu f''(C_B2) R_B2 R_A2
+ *   S[8] = sum nu [f''(C_B1) C_B1 + f'(C_B1)] R_B1   S[9] = C(theta_j t, 0)
+ * (K = f''(C) R, D = f'(C)). Times in (t_last, t] use the quadratic through the last
+ * slice and the stage row. mu may be NULL. Host pointers; synchronous. */
+int dmfe_history_integrals(dmfe_solver* h, double t, const double* C_row, const double* R_row,
+                           double* S, double* mu);
+/* Same on device memory, stream-ordered on `stream` (NULL: the solver's stream):
+ * row_dev is [2][L] (C then R), S_dev is [DMFE_NS][L]. Does not synchronise. */
+int dmfe_history_integrals_dev(dmfe_solver* h, double t, const double* row_dev,
+                               double* S_dev, void* stream);
+
+/* Right-hand side of the theta-grid ODE for a stage (t, C_row, R_row): the total
+ * derivatives dCf/dt, dRf/dt at fixed theta (d1 + theta d2, with d2 from the DMFE's
+ * second-argument equations), theta = 1 pinned to 0; mu(t), E(t). Host pointers. */
+int dmfe_rhs(dmfe_solver* h, double t, const double* C_row, const double* R_row,
+             double* dC, double* dR, double* mu, double* E);
+
+/* One sparsification pass (Sec. 3.6) on the stored history with tolerance tol, as
+ * dmfe_integrate runs it when the store is full. removed (may be NULL, size
+ * history_cap) receives 1 for each slice index that was removed. */
+int dmfe_sparsify(dmfe_solver* h, double tol, int* removed);
+
+int dmfe_stats(dmfe_solver* h, dmfe_stats_t* out);
+
+/* Binary checkpoint (parameters, grid key, history, step-control state, counters);
+ * a restored solver continues bit-identically. stream as in dmfe_params. */
+int dmfe_checkpoint(dmfe_solver* h, const char* path);
+int dmfe_restore(const char* path, void* stream, dmfe_solver** out);
+
+/* Synchronise the solver's stream and return the device status word. */
+int dmfe_sync(dmfe_solver* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMFE_H */

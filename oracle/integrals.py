@@ -69,7 +69,14 @@ NS = 10  # number of rows of S
 
 
 class Grid:
-    """The theta grid, its complement, the weights nu and the three stencil sets."""
+    """The theta grid, its complement, the weights nu and the three stencil sets.
+
+    The stencil positions (Sec. 3.3) of output rows j are produced by ``stencils(js)``;
+    they depend only on the grid and are kept for small L (the "precomputed" weights
+    of the paper), recomputed per block of rows otherwise.
+    """
+
+    CACHE_MAX_L = 1024
 
     def __init__(self, L, t_max, s=4, alpha=0.0, delta=0.0):
         from . import grid as g
@@ -79,9 +86,14 @@ class Grid:
         self.gamma = g.gamma_from_tmax(t_max)
         self.theta, self.omega = g.theta_grid(self.L, self.gamma, alpha, delta)
         self.nu = spline_weights(self.theta)
+        self._cache = self.positions(slice(0, self.L)) if self.L <= self.CACHE_MAX_L else None
+
+    def positions(self, js):
+        """(phi2, x1, x2, x3) for output rows js: fractional indices of phi1, phi2, psi."""
+        from . import grid as g
         th, om = self.theta, self.omega
-        thj, omj = th[:, None], om[:, None]  # output index j along axis 0
-        thi, omi = th[None, :], om[None, :]  # summation index i along axis 1
+        thj, omj = th[js][:, None], om[js][:, None]  # output index j along axis 0
+        thi, omi = th[None, :], om[None, :]          # summation index i along axis 1
         # phi1 = theta_i theta_j, 1 - phi1 = omega_i + theta_i omega_j
         phi1, ophi1 = thj * thi, omi + thi * omj
         # phi2 = theta_j + omega_j theta_i, 1 - phi2 = omega_j omega_i
@@ -90,12 +102,17 @@ class Grid:
         safe = np.where(phi2 > 0, phi2, 1.0)
         psi = np.where(phi2 > 0, thj / safe, 0.0)
         opsi = np.where(phi2 > 0, omj * thi / safe, 1.0)
-        fi = lambda a, b: g.frac_index(a, b, self.L, self.gamma, alpha, delta)
-        self.phi1, self.phi2 = phi1, phi2
-        self.x1, self.x2, self.x3 = fi(phi1, ophi1), fi(phi2, ophi2), fi(psi, opsi)
-        self.st1 = lagrange_stencil(self.x1, self.L, self.s)
-        self.st2 = lagrange_stencil(self.x2, self.L, self.s)
-        self.st3 = lagrange_stencil(self.x3, self.L, self.s)
+        fi = lambda a, b: g.frac_index(a, b, self.L, self.gamma, self.alpha, self.delta)
+        return phi2, fi(phi1, ophi1), fi(phi2, ophi2), fi(psi, opsi)
+
+    def stencils(self, js):
+        """(phi2, st1, st2, st3) for rows js; st = (base, weights) of lagrange_stencil."""
+        if self._cache is not None:
+            phi2, x1, x2, x3 = (a[js] for a in self._cache)
+        else:
+            phi2, x1, x2, x3 = self.positions(js)
+        return (phi2, lagrange_stencil(x1, self.L, self.s), lagrange_stencil(x2, self.L, self.s),
+                lagrange_stencil(x3, self.L, self.s))
 
 
 class History:
@@ -186,19 +203,21 @@ def row_prep(model, grid, t, C, R):
     return K, D, mu, E
 
 
-def history_integrals(model, grid, hist, t, C, R, j_chunk=256):
-    """The NS x L sums S of the module docstring for the stage at time t with row (C, R)."""
+def history_integrals(model, grid, hist, t, C, R, js=None, j_chunk=256):
+    """The NS x L sums S of the module docstring for the stage at time t with row (C, R).
+
+    js: optional list of output rows; the other columns of S are left at zero.
+    """
     L = grid.L
     nu = grid.nu
     K, D, _, _ = row_prep(model, grid, t, C, R)
     S = np.zeros((NS, L))
     cols = np.arange(L)
-    for j0 in range(0, L, j_chunk):
-        js = slice(j0, min(L, j0 + j_chunk))
-        thj = grid.theta[js][:, None]
-        b1, w1 = grid.st1[0][js], grid.st1[1][js]
-        b2, w2 = grid.st2[0][js], grid.st2[1][js]
-        b3, w3 = grid.st3[0][js], grid.st3[1][js]
+    rows = np.arange(L) if js is None else np.asarray(js)
+    for c0 in range(0, len(rows), j_chunk):
+        jr = rows[c0:c0 + j_chunk]
+        thj = grid.theta[jr][:, None]
+        phi2, (b1, w1), (b2, w2), (b3, w3) = grid.stencils(jr)
         # A: current row at phi1 and phi2
         K_A1, D_A1 = _gather_row(K, b1, w1), _gather_row(D, b1, w1)
         C_A1, R_A1 = _gather_row(C, b1, w1), _gather_row(R, b1, w1)
@@ -206,15 +225,15 @@ def history_integrals(model, grid, hist, t, C, R, j_chunk=256):
         # B1: on-grid theta_i at time theta_j t
         C_B1, R_B1 = lookup(hist, thj * t, cols[None, :], None, t, C, R)
         # B2: theta position psi_ij at time phi2_ij t
-        C_B2, R_B2 = lookup(hist, grid.phi2[js] * t, b3, w3, t, C, R)
+        C_B2, R_B2 = lookup(hist, phi2 * t, b3, w3, t, C, R)
         fpp1, fp1 = model.fpp(C_B1), model.fp(C_B1)
         fpp2, fp2 = model.fpp(C_B2), model.fp(C_B2)
         terms = (K_A1 * C_B1, K_A2 * C_B2, D_A1 * R_B1, K_A2 * R_B2,
                  fpp1 * R_B1 * C_A1, fp1 * R_A1, fp2 * R_A2, fpp2 * R_B2 * R_A2,
                  (fpp1 * C_B1 + fp1) * R_B1)
         for r, term in enumerate(terms):
-            S[r, js] = np.sum(nu[None, :] * term, axis=1)
-        S[9, js] = C_B1[:, 0]
+            S[r, jr] = np.sum(nu[None, :] * term, axis=1)
+        S[9, jr] = C_B1[:, 0]
     return S
 
 

@@ -1,0 +1,658 @@
+// Host side of the C ABI declared in include/dmfe.h: solver lifecycle, the integrate
+// loop (one CUDA graph per Dormand-Prince step, step control on the device, the host
+// polls a status word), lookups and checkpoint/restore.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "dmfe_internal.h"
+
+struct dmfe_solver {
+    dmfe_params p{};
+    std::vector<int> powers;
+    std::vector<double> coefs;
+    std::vector<double> theta, omega, nu;
+    SolverView v{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;  // private stream used only to capture the step graph
+    cudaGraphExec_t step_exec = nullptr;
+    int hi_grid = 0;
+    size_t hi_smem = 0;
+    DevState* hstate = nullptr;  // pinned mirror of the device state
+    double* scratch = nullptr;   // device [4L + 16]
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+int dev_alloc(dmfe_solver* h, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return DMFE_ERR_OOM;
+    }
+    h->allocs.push_back(*p);
+    return DMFE_OK;
+}
+
+#define TRY(x)                   \
+    do {                         \
+        int rc_ = (x);           \
+        if (rc_) return rc_;     \
+    } while (0)
+
+int read_state(dmfe_solver* h) {
+    DMFE_CUDA_TRY(cudaMemcpyAsync(h->hstate, h->v.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return DMFE_OK;
+}
+
+int write_state(dmfe_solver* h) {
+    DMFE_CUDA_TRY(cudaMemcpyAsync(h->v.st, h->hstate, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
+    DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return DMFE_OK;
+}
+
+void build_poly(const std::vector<int>& pw, const std::vector<double>& cf, Poly& P) {
+    std::memset(&P, 0, sizeof(P));
+    int pmax = 1;
+    for (size_t k = 0; k < pw.size(); ++k) {
+        const int p = pw[k];
+        const double c = cf[k];
+        pmax = std::max(pmax, p);
+        P.a0[p] += c;
+        P.a1[p - 1] += c * p;
+        if (p >= 2) P.a2[p - 2] += c * p * (p - 1);
+    }
+    P.deg0 = pmax;
+    P.deg1 = pmax - 1;
+    P.deg2 = std::max(pmax - 2, 0);
+    for (int m = 0; m < DMFE_MAX_POWER; ++m) {
+        P.f1[m] = (float)P.a1[m];
+        P.f2[m] = (float)P.a2[m];
+    }
+}
+
+int validate(const dmfe_params* p) {
+    if (!p || p->n_terms < 1 || p->n_terms > DMFE_MAX_TERMS || !p->powers || !p->coefs) return DMFE_ERR_ARG;
+    for (int k = 0; k < p->n_terms; ++k) {
+        if (p->powers[k] < 1 || p->powers[k] > DMFE_MAX_POWER) return DMFE_ERR_ARG;
+        if (!std::isfinite(p->coefs[k])) return DMFE_ERR_ARG;
+    }
+    if (!(p->T >= 0.0) || !std::isfinite(p->T) || !std::isfinite(p->beta0)) return DMFE_ERR_ARG;
+    if (p->L < 16 || p->L > 8192) return DMFE_ERR_ARG;
+    if (p->s < 2 || p->s > 16 || p->s > p->L) return DMFE_ERR_ARG;
+    if (!(p->grid_t_max > 2.718281828459046) || !std::isfinite(p->grid_t_max)) return DMFE_ERR_ARG;
+    if (!(p->alpha >= 0.0 && p->alpha <= 1.0) || !(p->delta >= 0.0)) return DMFE_ERR_ARG;
+    if (p->history_cap < 16) return DMFE_ERR_ARG;
+    if (!(p->dt0 > 0.0) || !(p->dt_min > 0.0)) return DMFE_ERR_ARG;
+    if (p->precision != DMFE_FP64 && p->precision != DMFE_FP32_COMPENSATED) return DMFE_ERR_ARG;
+    if (p->s != 4 && p->s != 6 && p->s != 8 && p->s != 10) return DMFE_ERR_UNSUPPORTED;
+    return DMFE_OK;
+}
+
+int create_impl(const dmfe_params* pin, dmfe_solver* h) {
+    h->p = *pin;
+    h->powers.assign(pin->powers, pin->powers + pin->n_terms);
+    h->coefs.assign(pin->coefs, pin->coefs + pin->n_terms);
+    h->p.powers = h->powers.data();
+    h->p.coefs = h->coefs.data();
+    const int L = pin->L, cap = pin->history_cap;
+    SolverView& v = h->v;
+    v.L = L;
+    v.s = pin->s;
+    v.cap = cap;
+    v.precision = pin->precision;
+    v.sparsify = pin->sparsify ? 1 : 0;
+    v.T = pin->T;
+    v.beta0 = pin->beta0;
+    build_poly(h->powers, h->coefs, v.poly);
+    v.gamma = host_gamma_from_tmax(pin->grid_t_max);
+    v.ga = std::atan(std::exp(-v.gamma));
+    v.gD = std::atan(std::exp(v.gamma)) - v.ga;
+    v.alpha = pin->alpha;
+    v.delta = pin->delta;
+    host_theta_grid(L, v.gamma, pin->alpha, pin->delta, h->theta, h->omega);
+    TRY(host_spline_weights(h->theta, h->nu));
+
+    if (pin->stream) {
+        h->stream = (cudaStream_t)pin->stream;
+    } else {
+        DMFE_CUDA_TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    DMFE_CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    if (cudaMallocHost((void**)&h->hstate, sizeof(DevState)) != cudaSuccess) return DMFE_ERR_OOM;
+
+    const size_t LL = (size_t)L * L;
+    void* p;
+    TRY(dev_alloc(h, &p, L * sizeof(double))); v.theta = (double*)p;
+    TRY(dev_alloc(h, &p, L * sizeof(double))); v.omega = (double*)p;
+    TRY(dev_alloc(h, &p, L * sizeof(double))); v.nu = (double*)p;
+    TRY(dev_alloc(h, &p, L * sizeof(float))); v.omega32 = (float*)p;
+    TRY(dev_alloc(h, &p, L * sizeof(float))); v.nu32 = (float*)p;
+    if (v.precision == DMFE_FP64) {
+        TRY(dev_alloc(h, &p, LL * sizeof(double))); v.x1 = (double*)p;
+        TRY(dev_alloc(h, &p, LL * sizeof(double))); v.x2 = (double*)p;
+        TRY(dev_alloc(h, &p, LL * sizeof(double))); v.x3 = (double*)p;
+    } else {
+        TRY(dev_alloc(h, &p, LL * sizeof(uint32_t))); v.p1 = (uint32_t*)p;
+        TRY(dev_alloc(h, &p, LL * sizeof(uint32_t))); v.p2 = (uint32_t*)p;
+        TRY(dev_alloc(h, &p, LL * sizeof(uint32_t))); v.p3 = (uint32_t*)p;
+    }
+    for (int b = 0; b < 2; ++b) {
+        TRY(dev_alloc(h, &p, cap * sizeof(double))); v.ht[b] = (double*)p;
+        TRY(dev_alloc(h, &p, (size_t)cap * L * sizeof(dbl4))); v.hist[b] = (dbl4*)p;
+        if (v.precision != DMFE_FP64) {
+            TRY(dev_alloc(h, &p, (size_t)cap * L * sizeof(float4))); v.hist32[b] = (float4*)p;
+        }
+    }
+    TRY(dev_alloc(h, &p, sizeof(DevState))); v.st = (DevState*)p;
+    TRY(dev_alloc(h, &p, 2 * L * sizeof(double))); v.Y = (double*)p;
+    TRY(dev_alloc(h, &p, 7 * 2 * (size_t)L * sizeof(double))); v.k = (double*)p;
+    TRY(dev_alloc(h, &p, 2 * L * sizeof(double))); v.ynew = (double*)p;
+    TRY(dev_alloc(h, &p, (size_t)DMFE_NS * L * sizeof(double))); v.S = (double*)p;
+    TRY(dev_alloc(h, &p, cap * sizeof(double))); v.eps_sp = (double*)p;
+    TRY(dev_alloc(h, &p, cap * sizeof(int))); v.keep = (int*)p;
+    TRY(dev_alloc(h, &p, cap * sizeof(int))); v.newidx = (int*)p;
+    TRY(dev_alloc(h, &p, (4 * (size_t)L + 16) * sizeof(double))); h->scratch = (double*)p;
+
+    std::vector<float> om32(L), nu32(L);
+    for (int i = 0; i < L; ++i) {
+        om32[i] = (float)h->omega[i];
+        nu32[i] = (float)h->nu[i];
+    }
+    DMFE_CUDA_TRY(cudaMemcpyAsync((void*)v.theta, h->theta.data(), L * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    DMFE_CUDA_TRY(cudaMemcpyAsync((void*)v.omega, h->omega.data(), L * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    DMFE_CUDA_TRY(cudaMemcpyAsync((void*)v.nu, h->nu.data(), L * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    DMFE_CUDA_TRY(cudaMemcpyAsync((void*)v.omega32, om32.data(), L * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    DMFE_CUDA_TRY(cudaMemcpyAsync((void*)v.nu32, nu32.data(), L * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    std::memset(h->hstate, 0, sizeof(DevState));
+    h->hstate->dt = pin->dt0;
+    h->hstate->dt_min = pin->dt_min;
+    h->hstate->tol = 1e-8;
+    TRY(write_state(h));
+    TRY(launch_tables(v, h->stream));
+    TRY(launch_initial_slice(v, h->stream));
+    TRY(hi_config(v, &h->hi_grid, &h->hi_smem));
+    DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    DMFE_CUDA_TRY(cudaGetLastError());
+    return DMFE_OK;
+}
+
+void destroy_impl(dmfe_solver* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->hstate) cudaFreeHost(h->hstate);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+// Capture one Dormand-Prince step into a graph on the private capture stream.
+int build_step_graph(dmfe_solver* h) {
+    if (h->step_exec) return DMFE_OK;
+    cudaGraph_t g = nullptr;
+    DMFE_CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = launch_step(h->v, h->hi_grid, h->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (rc || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc ? rc : DMFE_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&h->step_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->step_exec = nullptr;
+        cudaGetLastError();
+        return DMFE_ERR_CUDA;
+    }
+    return DMFE_OK;
+}
+
+int upload_row(dmfe_solver* h, const double* C, const double* R, double* dst) {
+    const int L = h->v.L;
+    DMFE_CUDA_TRY(cudaMemcpyAsync(dst, C, L * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    DMFE_CUDA_TRY(cudaMemcpyAsync(dst + L, R, L * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    return DMFE_OK;
+}
+
+double last_time(dmfe_solver* h) { return h->hstate->t; }
+
+}  // namespace
+
+extern "C" {
+
+void dmfe_default_params(dmfe_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->T = 0.5;
+    p->L = 513;
+    p->s = 4;
+    p->grid_t_max = 1e5;
+    p->history_cap = 0;  // 0 here means "use L" at create
+    p->dt0 = 1e-4;
+    p->dt_min = 1e-12;
+    p->precision = DMFE_FP64;
+    p->sparsify = 1;
+}
+
+const char* dmfe_strerror(int code) {
+    switch (code) {
+        case DMFE_OK: return "ok";
+        case DMFE_ERR_ARG: return "invalid argument";
+        case DMFE_ERR_OOM: return "out of memory";
+        case DMFE_ERR_NONFINITE: return "non-finite value in the step error estimate";
+        case DMFE_ERR_STEP_UNDERFLOW: return "step size fell below dt_min";
+        case DMFE_ERR_CAPACITY: return "history store full";
+        case DMFE_ERR_CUDA: return "CUDA runtime error";
+        case DMFE_ERR_TIMEOUT: return "bounded device wait timed out";
+        case DMFE_ERR_UNSUPPORTED: return "unsupported configuration";
+        case DMFE_ERR_IO: return "checkpoint i/o error";
+    }
+    return "unknown error";
+}
+
+int dmfe_create(const dmfe_params* pin, dmfe_solver** out) {
+    if (!out) return DMFE_ERR_ARG;
+    *out = nullptr;
+    if (!pin) return DMFE_ERR_ARG;
+    dmfe_params p = *pin;
+    if (p.history_cap == 0) p.history_cap = p.L;
+    int rc = validate(&p);
+    if (rc) return rc;
+    dmfe_solver* h = new (std::nothrow) dmfe_solver();
+    if (!h) return DMFE_ERR_OOM;
+    rc = create_impl(&p, h);
+    if (rc) {
+        destroy_impl(h);
+        return rc;
+    }
+    *out = h;
+    return DMFE_OK;
+}
+
+void dmfe_destroy(dmfe_solver* h) { destroy_impl(h); }
+
+int dmfe_grid(dmfe_solver* h, double* theta, double* omega, double* nu) {
+    if (!h) return DMFE_ERR_ARG;
+    const int L = h->v.L;
+    if (theta) std::memcpy(theta, h->theta.data(), L * sizeof(double));
+    if (omega) std::memcpy(omega, h->omega.data(), L * sizeof(double));
+    if (nu) std::memcpy(nu, h->nu.data(), L * sizeof(double));
+    return DMFE_OK;
+}
+
+int dmfe_tables(dmfe_solver* h, double* x1, double* x2, double* x3) {
+    if (!h) return DMFE_ERR_ARG;
+    const size_t LL = (size_t)h->v.L * h->v.L;
+    const SolverView& v = h->v;
+    double* outs[3] = {x1, x2, x3};
+    if (v.precision == DMFE_FP64) {
+        const double* src[3] = {v.x1, v.x2, v.x3};
+        for (int q = 0; q < 3; ++q)
+            if (outs[q]) DMFE_CUDA_TRY(cudaMemcpyAsync(outs[q], src[q], LL * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    } else {
+        const uint32_t* src[3] = {v.p1, v.p2, v.p3};
+        std::vector<uint32_t> tmp(LL);
+        for (int q = 0; q < 3; ++q) {
+            if (!outs[q]) continue;
+            DMFE_CUDA_TRY(cudaMemcpyAsync(tmp.data(), src[q], LL * sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
+            DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+            for (size_t k = 0; k < LL; ++k) outs[q][k] = tmp[k] / (double)(1u << FIX_FRAC_BITS);
+        }
+    }
+    return DMFE_OK;
+}
+
+int dmfe_integrate(dmfe_solver* h, double t_max, double tol) {
+    if (!h || !std::isfinite(t_max) || !(tol > 0.0)) return DMFE_ERR_ARG;
+    if (t_max > h->p.grid_t_max * (1.0 + 1e-12)) return DMFE_ERR_ARG;
+    TRY(read_state(h));
+    if (h->hstate->status) return h->hstate->status;
+    if (h->hstate->t >= t_max) return DMFE_OK;
+    TRY(launch_begin_integrate(h->v, t_max, tol, h->stream));
+    const bool graph = build_step_graph(h) == DMFE_OK;
+    int batch = 1;
+    for (;;) {
+        for (int it = 0; it < batch; ++it) {
+            if (graph) {
+                DMFE_CUDA_TRY(cudaGraphLaunch(h->step_exec, h->stream));
+            } else {
+                TRY(launch_step(h->v, h->hi_grid, h->stream));
+            }
+        }
+        TRY(read_state(h));
+        if (h->hstate->status || h->hstate->done) break;
+        batch = std::min(batch * 2, 64);
+    }
+    return h->hstate->status;
+}
+
+int dmfe_step(dmfe_solver* h, int nsteps, double t_max, double tol, void* stream) {
+    if (!h || nsteps < 0 || !std::isfinite(t_max) || !(tol > 0.0)) return DMFE_ERR_ARG;
+    if (t_max > h->p.grid_t_max * (1.0 + 1e-12)) return DMFE_ERR_ARG;
+    cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+    TRY(launch_begin_integrate(h->v, t_max, tol, s));
+    const bool graph = build_step_graph(h) == DMFE_OK;
+    for (int it = 0; it < nsteps; ++it) {
+        if (graph) {
+            DMFE_CUDA_TRY(cudaGraphLaunch(h->step_exec, s));
+        } else {
+            TRY(launch_step(h->v, h->hi_grid, s));
+        }
+    }
+    return DMFE_OK;
+}
+
+static int get_two_time(dmfe_solver* h, int n, const double* t, const double* tp, double* out, int which) {
+    if (!h || n < 0 || (n > 0 && (!t || !tp || !out))) return DMFE_ERR_ARG;
+    if (n == 0) return DMFE_OK;
+    TRY(read_state(h));
+    const double tl = h->hstate->t;
+    for (int q = 0; q < n; ++q) {
+        if (!(t[q] >= 0.0) || !(tp[q] >= 0.0)) return DMFE_ERR_ARG;
+        if (std::max(t[q], tp[q]) > tl * (1.0 + 1e-15)) return DMFE_ERR_ARG;
+    }
+    double* buf = nullptr;
+    DMFE_CUDA_TRY(cudaMallocAsync((void**)&buf, 3 * (size_t)n * sizeof(double), h->stream));
+    int rc = DMFE_OK;
+    if (cudaMemcpyAsync(buf, t, n * sizeof(double), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(buf + n, tp, n * sizeof(double), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        rc = DMFE_ERR_CUDA;
+    if (!rc) rc = launch_lookup(h->v, n, buf, buf + n, which, buf + 2 * n, h->stream);
+    if (!rc && cudaMemcpyAsync(out, buf + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        rc = DMFE_ERR_CUDA;
+    cudaFreeAsync(buf, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = DMFE_ERR_CUDA;
+    return rc;
+}
+
+int dmfe_get_C(dmfe_solver* h, int n, const double* t, const double* tp, double* out) {
+    return get_two_time(h, n, t, tp, out, 0);
+}
+
+int dmfe_get_R(dmfe_solver* h, int n, const double* t, const double* tp, double* out) {
+    return get_two_time(h, n, t, tp, out, 1);
+}
+
+int dmfe_get_row(dmfe_solver* h, double* t, double* C, double* R, double* mu, double* E) {
+    if (!h) return DMFE_ERR_ARG;
+    TRY(read_state(h));
+    const int L = h->v.L;
+    const DevState& s = *h->hstate;
+    std::vector<dbl4> row(L);
+    DMFE_CUDA_TRY(cudaMemcpyAsync(row.data(), h->v.hist[s.active] + (size_t)(s.n - 1) * L, L * sizeof(dbl4),
+                                  cudaMemcpyDeviceToHost, h->stream));
+    DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    std::vector<double> Cv(L), Rv(L);
+    for (int i = 0; i < L; ++i) {
+        Cv[i] = row[i].x;
+        Rv[i] = row[i].z;
+    }
+    if (t) *t = s.t;
+    if (C) std::memcpy(C, Cv.data(), L * sizeof(double));
+    if (R) std::memcpy(R, Rv.data(), L * sizeof(double));
+    if (mu || E) {
+        double* d = h->scratch;
+        TRY(upload_row(h, Cv.data(), Rv.data(), d));
+        TRY(launch_assemble(h->v, d, h->v.S, s.t, d + 2 * L, d + 3 * L, d + 4 * L, h->stream));
+        double muE[2];
+        DMFE_CUDA_TRY(cudaMemcpyAsync(muE, d + 4 * L, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        if (mu) *mu = muE[0];
+        if (E) *E = muE[1];
+    }
+    return DMFE_OK;
+}
+
+int dmfe_set_history(dmfe_solver* h, int n, const double* t, const double* C, const double* dC,
+                     const double* R, const double* dR) {
+    if (!h || !t || !C || !dC || !R || !dR) return DMFE_ERR_ARG;
+    const int L = h->v.L;
+    if (n < 1 || n > h->v.cap) return DMFE_ERR_ARG;
+    if (t[0] != 0.0) return DMFE_ERR_ARG;
+    for (int k = 1; k < n; ++k)
+        if (!(t[k] > t[k - 1])) return DMFE_ERR_ARG;
+    std::vector<dbl4> hist((size_t)n * L);
+    for (size_t q = 0; q < (size_t)n * L; ++q) hist[q] = dbl4{C[q], dC[q], R[q], dR[q]};
+    TRY(read_state(h));
+    DevState& s = *h->hstate;
+    s.active = 0;
+    s.n = n;
+    s.t = t[n - 1];
+    s.done = 0;
+    s.pending = 0;
+    s.sp_ran = 0;
+    s.status = 0;
+    DMFE_CUDA_TRY(cudaMemcpyAsync(h->v.hist[0], hist.data(), hist.size() * sizeof(dbl4), cudaMemcpyHostToDevice, h->stream));
+    DMFE_CUDA_TRY(cudaMemcpyAsync(h->v.ht[0], t, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    TRY(write_state(h));
+    TRY(launch_refresh_replica(h->v, h->stream));
+    DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return DMFE_OK;
+}
+
+int dmfe_get_history(dmfe_solver* h, int* n, double* t, double* C, double* dC, double* R, double* dR) {
+    if (!h || !n) return DMFE_ERR_ARG;
+    TRY(read_state(h));
+    const int L = h->v.L;
+    const DevState& s = *h->hstate;
+    *n = s.n;
+    std::vector<dbl4> hist((size_t)s.n * L);
+    DMFE_CUDA_TRY(cudaMemcpyAsync(hist.data(), h->v.hist[s.active], hist.size() * sizeof(dbl4), cudaMemcpyDeviceToHost, h->stream));
+    if (t) DMFE_CUDA_TRY(cudaMemcpyAsync(t, h->v.ht[s.active], s.n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (size_t q = 0; q < hist.size(); ++q) {
+        if (C) C[q] = hist[q].x;
+        if (dC) dC[q] = hist[q].y;
+        if (R) R[q] = hist[q].z;
+        if (dR) dR[q] = hist[q].w;
+    }
+    return DMFE_OK;
+}
+
+int dmfe_history_integrals_dev(dmfe_solver* h, double t, const double* row_dev, double* S_dev, void* stream) {
+    if (!h || !row_dev || !S_dev || !std::isfinite(t)) return DMFE_ERR_ARG;
+    if (t < last_time(h)) return DMFE_ERR_ARG;
+    cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+    return launch_history_integrals(h->v, row_dev, t, false, S_dev, h->hi_grid, s);
+}
+
+int dmfe_history_integrals(dmfe_solver* h, double t, const double* C_row, const double* R_row, double* S,
+                           double* mu) {
+    if (!h || !C_row || !R_row || !S) return DMFE_ERR_ARG;
+    TRY(read_state(h));
+    if (!(t >= h->hstate->t) || !std::isfinite(t)) return DMFE_ERR_ARG;
+    const int L = h->v.L;
+    double* d = h->scratch;
+    TRY(upload_row(h, C_row, R_row, d));
+    TRY(launch_history_integrals(h->v, d, t, false, h->v.S, h->hi_grid, h->stream));
+    DMFE_CUDA_TRY(cudaMemcpyAsync(S, h->v.S, (size_t)DMFE_NS * L * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (mu) {
+        TRY(launch_assemble(h->v, d, h->v.S, t, d + 2 * L, d + 3 * L, d + 4 * L, h->stream));
+        DMFE_CUDA_TRY(cudaMemcpyAsync(mu, d + 4 * L, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    }
+    DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return DMFE_OK;
+}
+
+int dmfe_rhs(dmfe_solver* h, double t, const double* C_row, const double* R_row, double* dC, double* dR,
+             double* mu, double* E) {
+    if (!h || !C_row || !R_row) return DMFE_ERR_ARG;
+    TRY(read_state(h));
+    if (!(t >= h->hstate->t) || !std::isfinite(t)) return DMFE_ERR_ARG;
+    const int L = h->v.L;
+    double* d = h->scratch;
+    TRY(upload_row(h, C_row, R_row, d));
+    if (t == 0.0) {
+        std::vector<double> S0((size_t)DMFE_NS * L, 0.0);
+        std::fill(S0.begin() + 9 * (size_t)L, S0.end(), 1.0);
+        DMFE_CUDA_TRY(cudaMemcpyAsync(h->v.S, S0.data(), S0.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    } else {
+        TRY(launch_history_integrals(h->v, d, t, false, h->v.S, h->hi_grid, h->stream));
+    }
+    TRY(launch_assemble(h->v, d, h->v.S, t, d + 2 * L, d + 3 * L, d + 4 * L, h->stream));
+    std::vector<double> out(2 * L + 2);
+    DMFE_CUDA_TRY(cudaMemcpyAsync(out.data(), d + 2 * L, (2 * L + 2) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (dC) std::memcpy(dC, out.data(), L * sizeof(double));
+    if (dR) std::memcpy(dR, out.data() + L, L * sizeof(double));
+    if (mu) *mu = out[2 * L];
+    if (E) *E = out[2 * L + 1];
+    return DMFE_OK;
+}
+
+int dmfe_sparsify(dmfe_solver* h, double tol, int* removed) {
+    if (!h || !(tol > 0.0)) return DMFE_ERR_ARG;
+    TRY(read_state(h));
+    const int n_old = h->hstate->n;
+    TRY(launch_sparsify(h->v, false, tol, h->stream));
+    TRY(read_state(h));
+    if (removed) {
+        std::vector<int> keep(n_old);
+        DMFE_CUDA_TRY(cudaMemcpyAsync(keep.data(), h->v.keep, n_old * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        const bool ran = h->hstate->n != n_old;
+        for (int k = 0; k < h->v.cap; ++k) removed[k] = 0;
+        if (ran)
+            for (int k = 0; k < n_old; ++k) removed[k] = keep[k] ? 0 : 1;
+    }
+    return DMFE_OK;
+}
+
+int dmfe_stats(dmfe_solver* h, dmfe_stats_t* o) {
+    if (!h || !o) return DMFE_ERR_ARG;
+    TRY(read_state(h));
+    const DevState& s = *h->hstate;
+    std::memset(o, 0, sizeof(*o));
+    o->t = s.t;
+    o->dt = s.dt;
+    o->mu = s.mu;
+    o->E = s.E;
+    o->last_eps = s.eps;
+    o->max_eps_sparse = s.max_eps_sparse;
+    o->steps_accepted = s.steps_accepted;
+    o->steps_rejected = s.steps_rejected;
+    o->stages = s.stages;
+    o->sparsify_passes = s.sparsify_passes;
+    o->slices_removed = s.slices_removed;
+    o->forced_removals = s.forced_removals;
+    o->n_slices = s.n;
+    o->status = s.status;
+    o->L = h->v.L;
+    o->history_cap = h->v.cap;
+    o->s = h->v.s;
+    o->precision = h->v.precision;
+    return DMFE_OK;
+}
+
+int dmfe_sync(dmfe_solver* h) {
+    if (!h) return DMFE_ERR_ARG;
+    TRY(read_state(h));
+    return h->hstate->status;
+}
+
+// ---- checkpoint format: magic, version, parameters, f, device state, history (FP64).
+static const char kMagic[8] = {'D', 'M', 'F', 'E', 'C', 'K', 'P', '1'};
+
+int dmfe_checkpoint(dmfe_solver* h, const char* path) {
+    if (!h || !path) return DMFE_ERR_ARG;
+    TRY(read_state(h));
+    const DevState s = *h->hstate;
+    const int L = h->v.L;
+    std::vector<dbl4> hist((size_t)s.n * L);
+    std::vector<double> ht(s.n);
+    DMFE_CUDA_TRY(cudaMemcpyAsync(hist.data(), h->v.hist[s.active], hist.size() * sizeof(dbl4), cudaMemcpyDeviceToHost, h->stream));
+    DMFE_CUDA_TRY(cudaMemcpyAsync(ht.data(), h->v.ht[s.active], s.n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return DMFE_ERR_IO;
+    bool ok = true;
+    auto W = [&](const void* p, size_t n) { ok = ok && std::fwrite(p, 1, n, f) == n; };
+    const int version = 1;
+    dmfe_params p = h->p;
+    p.powers = nullptr;
+    p.coefs = nullptr;
+    p.stream = nullptr;
+    W(kMagic, 8);
+    W(&version, sizeof(int));
+    W(&p, sizeof(p));
+    W(h->powers.data(), p.n_terms * sizeof(int));
+    W(h->coefs.data(), p.n_terms * sizeof(double));
+    W(&s, sizeof(s));
+    W(ht.data(), ht.size() * sizeof(double));
+    W(hist.data(), hist.size() * sizeof(dbl4));
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? DMFE_OK : DMFE_ERR_IO;
+}
+
+int dmfe_restore(const char* path, void* stream, dmfe_solver** out) {
+    if (!path || !out) return DMFE_ERR_ARG;
+    *out = nullptr;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return DMFE_ERR_IO;
+    bool ok = true;
+    auto R = [&](void* p, size_t n) { ok = ok && std::fread(p, 1, n, f) == n; };
+    char magic[8];
+    int version = 0;
+    dmfe_params p;
+    R(magic, 8);
+    R(&version, sizeof(int));
+    R(&p, sizeof(p));
+    if (!ok || std::memcmp(magic, kMagic, 8) != 0 || version != 1 || p.n_terms < 1 || p.n_terms > DMFE_MAX_TERMS) {
+        std::fclose(f);
+        return DMFE_ERR_IO;
+    }
+    std::vector<int> pw(p.n_terms);
+    std::vector<double> cf(p.n_terms);
+    DevState s;
+    R(pw.data(), pw.size() * sizeof(int));
+    R(cf.data(), cf.size() * sizeof(double));
+    R(&s, sizeof(s));
+    if (!ok || s.n < 1 || s.n > p.history_cap || p.L < 16 || p.L > 8192) {
+        std::fclose(f);
+        return DMFE_ERR_IO;
+    }
+    std::vector<double> ht(s.n);
+    std::vector<dbl4> hist((size_t)s.n * p.L);
+    R(ht.data(), ht.size() * sizeof(double));
+    R(hist.data(), hist.size() * sizeof(dbl4));
+    std::fclose(f);
+    if (!ok) return DMFE_ERR_IO;
+    p.powers = pw.data();
+    p.coefs = cf.data();
+    p.stream = stream;
+    dmfe_solver* h = nullptr;
+    int rc = dmfe_create(&p, &h);
+    if (rc) return rc;
+    s.active = 0;
+    s.pending = 0;
+    s.sp_ran = 0;
+    *h->hstate = s;
+    rc = DMFE_OK;
+    if (cudaMemcpyAsync(h->v.hist[0], hist.data(), hist.size() * sizeof(dbl4), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->v.ht[0], ht.data(), ht.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        rc = DMFE_ERR_CUDA;
+    if (!rc) rc = write_state(h);
+    if (!rc) rc = launch_refresh_replica(h->v, h->stream);
+    if (!rc && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = DMFE_ERR_CUDA;
+    if (rc) {
+        dmfe_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return DMFE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// Internal declarations shared by the translation units of libdmfe.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <vector>
+
+#include "../../include/dmfe.h"
+
+#define DMFE_CUDA_TRY(call)                                   \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return DMFE_ERR_CUDA;          \
+    } while (0)
+
+// 32-byte history element {C, dC/dt, R, dR/dt} (own type: CUDA 13 deprecates double4).
+struct __align__(32) dbl4 {
+    double x, y, z, w;
+};
+
+// Polynomial f(q), f'(q), f''(q) as dense Horner coefficients (kernel argument, so that
+// solvers with different f can run concurrently in one process).
+struct Poly {
+    int deg0, deg1, deg2;                // degrees of f, f' and f''
+    double a0[DMFE_MAX_POWER + 1];       // f(q)   = sum_m a0[m] q^m
+    double a1[DMFE_MAX_POWER];           // f'(q)  = sum_m a1[m] q^m
+    double a2[DMFE_MAX_POWER];           // f''(q) = sum_m a2[m] q^m
+    float f1[DMFE_MAX_POWER];
+    float f2[DMFE_MAX_POWER];
+};
+
+template <typename R>
+__device__ __forceinline__ R poly_eval(const R* a, int deg, R q) {
+    R v = a[deg];
+    for (int m = deg - 1; m >= 0; --m) v = fma(v, q, a[m]);
+    return v;
+}
+__device__ __forceinline__ double fp0(const Poly& P, double q) { return poly_eval(P.a0, P.deg0, q); }
+__device__ __forceinline__ double fp1(const Poly& P, double q) { return poly_eval(P.a1, P.deg1, q); }
+__device__ __forceinline__ double fp2(const Poly& P, double q) { return poly_eval(P.a2, P.deg2, q); }
+__device__ __forceinline__ float fp1(const Poly& P, float q) { return poly_eval(P.f1, P.deg1, q); }
+__device__ __forceinline__ float fp2(const Poly& P, float q) { return poly_eval(P.f2, P.deg2, q); }
+
+// Step-control and history bookkeeping, resident in device memory. Kernels of the
+// integrate loop read and update it; the host reads it only to poll and report.
+struct DevState {
+    double t;            // time of the last accepted slice
+    double dt;           // controller step
+    double h;            // size of the trial step in progress
+    double t_stage;      // time of the stage being evaluated
+    double t_target;     // integrate target
+    double tol;
+    double dt_min;
+    double eps;          // eps_RK of the last trial step
+    double mu, E;        // of the last stage row evaluated by the assemble kernel
+    double max_eps_sparse;
+    double t_pending;    // time of an accepted slice waiting for a sparsification pass
+    long long steps_accepted, steps_rejected, stages;
+    long long sparsify_passes, slices_removed, forced_removals;
+    int n;               // stored slices in the active buffer
+    int active;          // 0/1: which history buffer is live
+    int status;          // 0 or a DMFE_ERR_* code
+    int done;            // 1 once t reached t_target
+    int pending;         // 1: an accepted slice waits for a sparsification pass
+    int removed_count;   // slices removed by the last pass
+    int sp_ran;          // 1 between the select and finish kernels of a pass
+    int n_new;           // slice count after the pass
+};
+
+// Everything a kernel needs about one solver (passed by value).
+struct SolverView {
+    int L, s, cap, precision;
+    int sparsify;         // 1: pass when the store is full
+    double T, beta0;
+    double gamma, ga, gD, alpha, delta;  // grid: gamma, atan(e^-gamma), atan(e^gamma) - atan(e^-gamma)
+    Poly poly;
+    const double* theta;  // [L]
+    const double* omega;  // [L] 1 - theta
+    const double* nu;     // [L]
+    const float* omega32; // [L]
+    const float* nu32;    // [L]
+    const double* x1;     // [L*L] FP64 fractional index (FP64 path)
+    const double* x2;
+    const double* x3;
+    const uint32_t* p1;   // [L*L] fixed-point index, 19 fraction bits (FP32 path)
+    const uint32_t* p2;
+    const uint32_t* p3;
+    double* ht[2];        // slice times [cap], two buffers (compaction ping-pong)
+    dbl4* hist[2];        // [cap][L] {C, dC, R, dR} FP64 master
+    float4* hist32[2];    // [cap][L] FP32 replica (FP32 path)
+    DevState* st;
+    double* Y;            // [2L] stage row (C then R)
+    double* k;            // [7][2L] stage derivatives
+    double* ynew;         // [2L] 5th-order solution of the trial step
+    double* S;            // [NS][L]
+    double* eps_sp;       // [cap] sparsification residuals
+    int* keep;            // [cap]
+    int* newidx;          // [cap]
+};
+
+static const int FIX_FRAC_BITS = 19;  // x = packed / 2^19
+
+// ---- launchers (defined in the .cu files) ----
+int launch_tables(const SolverView& v, cudaStream_t s);
+// history integrals: row_dev = [2L] (C, R); t_dev != NULL reads the stage time from
+// device memory (integrate loop) and gates on the status word; otherwise uses t.
+int launch_history_integrals(const SolverView& v, const double* row_dev, double t, bool from_state,
+                             double* S_dev, int grid_ctas, cudaStream_t s);
+int hi_config(const SolverView& v, int* grid_ctas, size_t* smem);
+int launch_assemble(const SolverView& v, const double* row_dev, const double* S_dev, double t,
+                    double* dC, double* dR, double* muE, cudaStream_t s);
+int launch_step(const SolverView& v, int grid_ctas, cudaStream_t s);
+int launch_begin_integrate(const SolverView& v, double t_target, double tol, cudaStream_t s);
+int launch_initial_slice(const SolverView& v, cudaStream_t s);
+int launch_sparsify(const SolverView& v, bool from_step, double tol, cudaStream_t s);
+int launch_lookup(const SolverView& v, int n, const double* t, const double* tp, int which,
+                  double* out, cudaStream_t s);
+int launch_refresh_replica(const SolverView& v, cudaStream_t s);
+
+// ---- host grid (host_grid.cpp) ----
+double host_gamma_from_tmax(double t_max);
+void host_theta_grid(int L, double gamma, double alpha, double delta, std::vector<double>& theta,
+                     std::vector<double>& omega);
+int host_spline_weights(const std::vector<double>& theta, std::vector<double>& nu);

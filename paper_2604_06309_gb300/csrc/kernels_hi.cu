@@ -1,0 +1,496 @@
+// History integrals of one Runge-Kutta stage (Secs. 3.3, 3.4, Eq. int).
+//
+// For every output index j (t' = theta_j t) and summation index i the kernel forms
+//   A   the current stage row at phi1 = theta_i theta_j and phi2 = theta_j + (1 - theta_j) theta_i
+//       (index-space Lagrange stencil, rows K = f''(C) R, D = f'(C), C, R in shared memory),
+//   B1  (C, R)(theta_j t, theta_i): on-grid in theta, cubic Hermite in t between the two
+//       stored slices around theta_j t,
+//   B2  (C, R)(phi2 t, theta_j / phi2): Lagrange stencil in theta on the two slices around
+//       phi2 t, then cubic Hermite in t,
+// and accumulates the nine nu-weighted products S[0..8] of dmfe.h plus S[9] = C(theta_j t, 0).
+// Times in (t_last, t] come from the quadratic through the last slice and the stage row.
+//
+// Mapping: one warp per output index j, lanes stride over i (coalesced table and B1 rows);
+// each lane sums its terms in i order and the warp reduces with a fixed butterfly, so
+// results are deterministic. The slice containing phi2 t is found from a per-stage
+// table cell -> slice (phi2 lies in grid cell floor(x2)) and a short walk.
+//
+// Precision variants:
+//   FP64: every value in FP64, stencil positions from FP64 tables.
+//   FP32: stage row, history replica and interpolation in FP32, stencil positions from
+//         fixed-point tables (19 fraction bits), per-lane Kahan-compensated sums, slice
+//         times handled as complements v_n = (t - t_n)/t so that 1 - phi2 = omega_j omega_i
+//         keeps its relative precision near the diagonal; per-j quantities, the warp
+//         reduction and the output stay FP64.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dmfe_internal.h"
+
+namespace {
+
+constexpr int HI_THREADS = 256;
+constexpr int HI_WARPS = HI_THREADS / 32;
+
+// Lagrange weights on nodes 0..SW-1 at u: w_k = prod_{m != k} (u - m) / (k - m).
+template <int SW, typename R>
+__device__ __forceinline__ void lagrange(R u, R (&w)[SW]) {
+    R pre[SW], suf[SW];
+    pre[0] = R(1);
+#pragma unroll
+    for (int k = 1; k < SW; ++k) pre[k] = pre[k - 1] * (u - R(k - 1));
+    suf[SW - 1] = R(1);
+#pragma unroll
+    for (int k = SW - 2; k >= 0; --k) suf[k] = suf[k + 1] * (u - R(k + 1));
+#pragma unroll
+    for (int k = 0; k < SW; ++k) {
+        // 1 / prod_{m != k} (k - m) = (-1)^{SW-1-k} / (k! (SW-1-k)!)
+        double c = 1.0;
+        for (int m = 0; m < SW; ++m)
+            if (m != k) c /= double(k - m);
+        w[k] = pre[k] * suf[k] * R(c);
+    }
+}
+
+template <int SW>
+__device__ __forceinline__ int stencil_base(int fl, int L) {
+    int b = fl - SW / 2 + 1;
+    b = b < 0 ? 0 : b;
+    return b > L - SW ? L - SW : b;
+}
+
+// Time weights: value = w0 Y[a0] + w1 dY[a0] + w2 Y[a1] + w3 dY[a1]; a1 < 0 means the
+// stage row (only its value is used, w3 = 0). FP64, shared by both variants (per j).
+struct TimeW {
+    int a0, a1;
+    double w0, w1, w2, w3;
+};
+
+__device__ __forceinline__ TimeW time_weights_f64(const double* sht, int n, bool ext, double tl,
+                                                  double hx, double tau, int hint) {
+    TimeW r;
+    if (ext && tau > tl) {
+        double s = tau - tl, q = s / hx;
+        r.a0 = n - 1; r.a1 = -1;
+        r.w0 = 1.0 - q * q; r.w1 = s - s * q; r.w2 = q * q; r.w3 = 0.0;
+    } else if (n == 1) {
+        r.a0 = 0; r.a1 = 0;
+        r.w0 = 1.0; r.w1 = 0.0; r.w2 = 0.0; r.w3 = 0.0;
+    } else {
+        int k = hint;
+        while (k < n - 2 && sht[k + 1] <= tau) ++k;
+        while (k > 0 && sht[k] > tau) --k;
+        double hh = sht[k + 1] - sht[k];
+        double sg = (tau - sht[k]) / hh;
+        double om = 1.0 - sg;
+        r.a0 = k; r.a1 = k + 1;
+        r.w0 = (1.0 + 2.0 * sg) * om * om;
+        r.w1 = sg * om * om * hh;
+        r.w2 = sg * sg * (3.0 - 2.0 * sg);
+        r.w3 = sg * sg * (sg - 1.0) * hh;
+    }
+    return r;
+}
+
+// Largest k <= n-2 with sht[k] <= tau (0 when n == 1).
+__device__ __forceinline__ int find_slice(const double* sht, int n, double tau) {
+    if (n <= 2) return 0;
+    int lo = 0, hi = n - 2;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (sht[mid] <= tau) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ------------------------------------------------------------------ FP64 variant
+template <int SW>
+__global__ void __launch_bounds__(HI_THREADS) k_hi_f64(SolverView v, const double* __restrict__ row,
+                                                       double t_arg, int from_state, double* __restrict__ S) {
+    extern __shared__ __align__(32) unsigned char smraw[];
+    const DevState* st = v.st;
+    if (from_state && (st->status != 0 || st->done)) return;
+    const int L = v.L;
+    const int n = st->n;
+    const int act = st->active;
+    const double t = from_state ? st->t_stage : t_arg;
+    const dbl4* __restrict__ H = v.hist[act];
+    const double* __restrict__ ht = v.ht[act];
+    dbl4* srow = reinterpret_cast<dbl4*>(smraw);            // [L] {K, D, C, R}
+    double* sht = reinterpret_cast<double*>(srow + L);              // [cap]
+    int* scell = reinterpret_cast<int*>(sht + v.cap);               // [L]
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        double C = row[i], R = row[L + i];
+        srow[i] = dbl4{fp2(v.poly, C) * R, fp1(v.poly, C), C, R};
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sht[i] = ht[i];
+    __syncthreads();
+    for (int m = threadIdx.x; m < L; m += blockDim.x) scell[m] = find_slice(sht, n, v.theta[m] * t);
+    __syncthreads();
+    const double tl = sht[n - 1];
+    const bool ext = t > tl;
+    const double hx = t - tl;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * HI_WARPS;
+    const double* __restrict__ theta = v.theta;
+    const double* __restrict__ omega = v.omega;
+    const double* __restrict__ nu = v.nu;
+
+    for (int j = blockIdx.x * HI_WARPS + (threadIdx.x >> 5); j < L; j += nwarps) {
+        const double thj = theta[j], omj = omega[j];
+        const TimeW b1 = time_weights_f64(sht, n, ext, tl, hx, thj * t, scell[j]);
+        const double* __restrict__ x1r = v.x1 + (size_t)j * L;
+        const double* __restrict__ x2r = v.x2 + (size_t)j * L;
+        const double* __restrict__ x3r = v.x3 + (size_t)j * L;
+        double acc[9];
+#pragma unroll
+        for (int r = 0; r < 9; ++r) acc[r] = 0.0;
+        double c_at_0 = 0.0;
+        for (int i = lane; i < L; i += 32) {
+            // ---- B1: on-grid column i at time theta_j t
+            double CB1, RB1;
+            {
+                dbl4 h0 = H[(size_t)b1.a0 * L + i];
+                CB1 = b1.w0 * h0.x + b1.w1 * h0.y;
+                RB1 = b1.w0 * h0.z + b1.w1 * h0.w;
+                if (b1.a1 >= 0) {
+                    dbl4 h1 = H[(size_t)b1.a1 * L + i];
+                    CB1 += b1.w2 * h1.x + b1.w3 * h1.y;
+                    RB1 += b1.w2 * h1.z + b1.w3 * h1.w;
+                } else {
+                    dbl4 r1 = srow[i];
+                    CB1 += b1.w2 * r1.z;
+                    RB1 += b1.w2 * r1.w;
+                }
+            }
+            // ---- A1: current row at phi1
+            double KA1 = 0, DA1 = 0, CA1 = 0, RA1 = 0;
+            {
+                double x = x1r[i];
+                int b = stencil_base<SW>((int)floor(x), L);
+                double w[SW];
+                lagrange<SW>(x - b, w);
+#pragma unroll
+                for (int k = 0; k < SW; ++k) {
+                    dbl4 q = srow[b + k];
+                    KA1 += w[k] * q.x; DA1 += w[k] * q.y; CA1 += w[k] * q.z; RA1 += w[k] * q.w;
+                }
+            }
+            // ---- A2: current row at phi2
+            double KA2 = 0, RA2 = 0;
+            double x2 = x2r[i];
+            {
+                int b = stencil_base<SW>((int)floor(x2), L);
+                double w[SW];
+                lagrange<SW>(x2 - b, w);
+#pragma unroll
+                for (int k = 0; k < SW; ++k) {
+                    dbl4 q = srow[b + k];
+                    KA2 += w[k] * q.x; RA2 += w[k] * q.w;
+                }
+            }
+            // ---- B2: theta position psi on the slices around phi2 t
+            double CB2, RB2;
+            {
+                const double thi = theta[i];
+                const double tau2 = (thj + omj * thi) * t;
+                int cell = (int)floor(x2);
+                const int h0 = scell[cell];
+                const TimeW b2 = time_weights_f64(sht, n, ext, tl, hx, tau2, h0);
+                double x3 = x3r[i];
+                int b = stencil_base<SW>((int)floor(x3), L);
+                double w[SW];
+                lagrange<SW>(x3 - b, w);
+                double c0 = 0, dc0 = 0, r0 = 0, dr0 = 0, c1 = 0, dc1 = 0, r1 = 0, dr1 = 0;
+                const dbl4* __restrict__ s0 = H + (size_t)b2.a0 * L + b;
+#pragma unroll
+                for (int k = 0; k < SW; ++k) {
+                    dbl4 q = s0[k];
+                    c0 += w[k] * q.x; dc0 += w[k] * q.y; r0 += w[k] * q.z; dr0 += w[k] * q.w;
+                }
+                if (b2.a1 >= 0) {
+                    const dbl4* __restrict__ s1 = H + (size_t)b2.a1 * L + b;
+#pragma unroll
+                    for (int k = 0; k < SW; ++k) {
+                        dbl4 q = s1[k];
+                        c1 += w[k] * q.x; dc1 += w[k] * q.y; r1 += w[k] * q.z; dr1 += w[k] * q.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < SW; ++k) {
+                        dbl4 q = srow[b + k];
+                        c1 += w[k] * q.z; r1 += w[k] * q.w;
+                    }
+                }
+                CB2 = b2.w0 * c0 + b2.w1 * dc0 + b2.w2 * c1 + b2.w3 * dc1;
+                RB2 = b2.w0 * r0 + b2.w1 * dr0 + b2.w2 * r1 + b2.w3 * dr1;
+            }
+            const double f1a = fp1(v.poly, CB1), f2a = fp2(v.poly, CB1);
+            const double f1b = fp1(v.poly, CB2), f2b = fp2(v.poly, CB2);
+            const double nui = nu[i];
+            acc[0] += nui * (KA1 * CB1);
+            acc[1] += nui * (KA2 * CB2);
+            acc[2] += nui * (DA1 * RB1);
+            acc[3] += nui * (KA2 * RB2);
+            acc[4] += nui * (f2a * RB1 * CA1);
+            acc[5] += nui * (f1a * RA1);
+            acc[6] += nui * (f1b * RA2);
+            acc[7] += nui * (f2b * RB2 * RA2);
+            acc[8] += nui * ((f2a * CB1 + f1a) * RB1);
+            if (i == 0) c_at_0 = CB1;
+        }
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+            double s = warp_sum(acc[r]);
+            if (lane == 0) S[(size_t)r * L + j] = s;
+        }
+        if (lane == 0) S[(size_t)9 * L + j] = c_at_0;
+    }
+}
+
+// ------------------------------------------------------------------ FP32 variant
+struct Kahan {
+    float s, c;
+    __device__ __forceinline__ void add(float x) {
+        float y = x - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+template <int SW>
+__global__ void __launch_bounds__(HI_THREADS) k_hi_f32(SolverView v, const double* __restrict__ row,
+                                                       double t_arg, int from_state, double* __restrict__ S) {
+    extern __shared__ __align__(32) unsigned char smraw[];
+    const DevState* st = v.st;
+    if (from_state && (st->status != 0 || st->done)) return;
+    const int L = v.L;
+    const int n = st->n;
+    const int act = st->active;
+    const double t = from_state ? st->t_stage : t_arg;
+    const float4* __restrict__ H = v.hist32[act];
+    const double* __restrict__ ht = v.ht[act];
+    float4* srow = reinterpret_cast<float4*>(smraw);               // [L] {K, D, C, R}
+    double* sht = reinterpret_cast<double*>(srow + L);              // [cap] slice times
+    float* sv = reinterpret_cast<float*>(sht + v.cap);              // [cap] (t - t_k)/t
+    float* sinv = sv + v.cap;                                       // [cap] 1/(v_k - v_{k+1})
+    float* sdt = sinv + v.cap;                                      // [cap] t_{k+1} - t_k
+    int* scell = reinterpret_cast<int*>(sdt + v.cap);               // [L]
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        double C = row[i], R = row[L + i];
+        srow[i] = make_float4((float)(fp2(v.poly, C) * R), (float)fp1(v.poly, C), (float)C, (float)R);
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double tk = ht[i];
+        sht[i] = tk;
+        sv[i] = (float)((t - tk) / t);
+        if (i + 1 < n) {
+            double tk1 = ht[i + 1];
+            sinv[i] = (float)(t / (tk1 - tk));
+            sdt[i] = (float)(tk1 - tk);
+        }
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < L; m += blockDim.x) scell[m] = find_slice(sht, n, v.theta[m] * t);
+    __syncthreads();
+    const double tl = sht[n - 1];
+    const bool ext = t > tl;
+    const double hx = t - tl;
+    const float vlast = sv[n - 1];
+    const float hx32 = (float)hx;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * HI_WARPS;
+    const float* __restrict__ om32 = v.omega32;
+    const float* __restrict__ nu32 = v.nu32;
+    const float fscale = 1.0f / (float)(1u << FIX_FRAC_BITS);
+
+    for (int j = blockIdx.x * HI_WARPS + (threadIdx.x >> 5); j < L; j += nwarps) {
+        const double thj = v.theta[j];
+        const float omj = om32[j];
+        const TimeW b1d = time_weights_f64(sht, n, ext, tl, hx, thj * t, scell[j]);
+        const float bw0 = (float)b1d.w0, bw1 = (float)b1d.w1, bw2 = (float)b1d.w2, bw3 = (float)b1d.w3;
+        const uint32_t* __restrict__ p1r = v.p1 + (size_t)j * L;
+        const uint32_t* __restrict__ p2r = v.p2 + (size_t)j * L;
+        const uint32_t* __restrict__ p3r = v.p3 + (size_t)j * L;
+        Kahan acc[9];
+#pragma unroll
+        for (int r = 0; r < 9; ++r) { acc[r].s = 0.f; acc[r].c = 0.f; }
+        float c_at_0 = 0.f;
+        for (int i = lane; i < L; i += 32) {
+            float CB1, RB1;
+            {
+                float4 h0 = H[(size_t)b1d.a0 * L + i];
+                CB1 = bw0 * h0.x + bw1 * h0.y;
+                RB1 = bw0 * h0.z + bw1 * h0.w;
+                if (b1d.a1 >= 0) {
+                    float4 h1 = H[(size_t)b1d.a1 * L + i];
+                    CB1 += bw2 * h1.x + bw3 * h1.y;
+                    RB1 += bw2 * h1.z + bw3 * h1.w;
+                } else {
+                    float4 r1 = srow[i];
+                    CB1 += bw2 * r1.z;
+                    RB1 += bw2 * r1.w;
+                }
+            }
+            float KA1 = 0.f, DA1 = 0.f, CA1 = 0.f, RA1 = 0.f;
+            {
+                uint32_t p = p1r[i];
+                int b = stencil_base<SW>((int)(p >> FIX_FRAC_BITS), L);
+                float w[SW];
+                lagrange<SW>((float)(p - ((uint32_t)b << FIX_FRAC_BITS)) * fscale, w);
+#pragma unroll
+                for (int k = 0; k < SW; ++k) {
+                    float4 q = srow[b + k];
+                    KA1 += w[k] * q.x; DA1 += w[k] * q.y; CA1 += w[k] * q.z; RA1 += w[k] * q.w;
+                }
+            }
+            float KA2 = 0.f, RA2 = 0.f;
+            const uint32_t pp2 = p2r[i];
+            {
+                int b = stencil_base<SW>((int)(pp2 >> FIX_FRAC_BITS), L);
+                float w[SW];
+                lagrange<SW>((float)(pp2 - ((uint32_t)b << FIX_FRAC_BITS)) * fscale, w);
+#pragma unroll
+                for (int k = 0; k < SW; ++k) {
+                    float4 q = srow[b + k];
+                    KA2 += w[k] * q.x; RA2 += w[k] * q.w;
+                }
+            }
+            float CB2, RB2;
+            {
+                // complement of phi2: 1 - phi2 = omega_j omega_i; slice k holds v_k = (t - t_k)/t
+                const float u = omj * om32[i];
+                int a0, a1;
+                float w0, w1, w2, w3;
+                if (ext && u < vlast) {
+                    float q = (vlast - u) / vlast;
+                    a0 = n - 1; a1 = -1;
+                    w0 = 1.f - q * q; w1 = hx32 * (q - q * q); w2 = q * q; w3 = 0.f;
+                } else if (n == 1) {
+                    a0 = 0; a1 = 0; w0 = 1.f; w1 = 0.f; w2 = 0.f; w3 = 0.f;
+                } else {
+                    int k = scell[pp2 >> FIX_FRAC_BITS];
+                    while (k < n - 2 && sv[k + 1] >= u) ++k;
+                    while (k > 0 && sv[k] < u) --k;
+                    float sg = (sv[k] - u) * sinv[k];
+                    float hh = sdt[k];
+                    float om = 1.f - sg;
+                    a0 = k; a1 = k + 1;
+                    w0 = (1.f + 2.f * sg) * om * om;
+                    w1 = sg * om * om * hh;
+                    w2 = sg * sg * (3.f - 2.f * sg);
+                    w3 = sg * sg * (sg - 1.f) * hh;
+                }
+                const uint32_t p = p3r[i];
+                int b = stencil_base<SW>((int)(p >> FIX_FRAC_BITS), L);
+                float w[SW];
+                lagrange<SW>((float)(p - ((uint32_t)b << FIX_FRAC_BITS)) * fscale, w);
+                float c0 = 0.f, dc0 = 0.f, r0 = 0.f, dr0 = 0.f, c1 = 0.f, dc1 = 0.f, r1 = 0.f, dr1 = 0.f;
+                const float4* __restrict__ s0 = H + (size_t)a0 * L + b;
+#pragma unroll
+                for (int k = 0; k < SW; ++k) {
+                    float4 q = s0[k];
+                    c0 += w[k] * q.x; dc0 += w[k] * q.y; r0 += w[k] * q.z; dr0 += w[k] * q.w;
+                }
+                if (a1 >= 0) {
+                    const float4* __restrict__ s1 = H + (size_t)a1 * L + b;
+#pragma unroll
+                    for (int k = 0; k < SW; ++k) {
+                        float4 q = s1[k];
+                        c1 += w[k] * q.x; dc1 += w[k] * q.y; r1 += w[k] * q.z; dr1 += w[k] * q.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < SW; ++k) {
+                        float4 q = srow[b + k];
+                        c1 += w[k] * q.z; r1 += w[k] * q.w;
+                    }
+                }
+                CB2 = w0 * c0 + w1 * dc0 + w2 * c1 + w3 * dc1;
+                RB2 = w0 * r0 + w1 * dr0 + w2 * r1 + w3 * dr1;
+            }
+            const float f1a = fp1(v.poly, CB1), f2a = fp2(v.poly, CB1);
+            const float f1b = fp1(v.poly, CB2), f2b = fp2(v.poly, CB2);
+            const float nui = nu32[i];
+            acc[0].add(nui * (KA1 * CB1));
+            acc[1].add(nui * (KA2 * CB2));
+            acc[2].add(nui * (DA1 * RB1));
+            acc[3].add(nui * (KA2 * RB2));
+            acc[4].add(nui * (f2a * RB1 * CA1));
+            acc[5].add(nui * (f1a * RA1));
+            acc[6].add(nui * (f1b * RA2));
+            acc[7].add(nui * (f2b * RB2 * RA2));
+            acc[8].add(nui * ((f2a * CB1 + f1a) * RB1));
+            if (i == 0) c_at_0 = CB1;
+        }
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+            double s = warp_sum((double)acc[r].s - (double)acc[r].c);
+            if (lane == 0) S[(size_t)r * L + j] = s;
+        }
+        if (lane == 0) S[(size_t)9 * L + j] = (double)c_at_0;
+    }
+}
+
+size_t hi_smem_bytes(const SolverView& v) {
+    if (v.precision == DMFE_FP64)
+        return (size_t)v.L * sizeof(dbl4) + (size_t)v.cap * sizeof(double) + (size_t)v.L * sizeof(int);
+    return (size_t)v.L * sizeof(float4) + (size_t)v.cap * (sizeof(double) + 3 * sizeof(float)) +
+           (size_t)v.L * sizeof(int);
+}
+
+template <int SW>
+void* hi_kernel(int precision) {
+    return precision == DMFE_FP64 ? (void*)k_hi_f64<SW> : (void*)k_hi_f32<SW>;
+}
+
+void* hi_kernel_for(const SolverView& v) {
+    switch (v.s) {
+        case 4: return hi_kernel<4>(v.precision);
+        case 6: return hi_kernel<6>(v.precision);
+        case 8: return hi_kernel<8>(v.precision);
+        case 10: return hi_kernel<10>(v.precision);
+    }
+    return nullptr;
+}
+
+}  // namespace
+
+int hi_config(const SolverView& v, int* grid_ctas, size_t* smem) {
+    void* fn = hi_kernel_for(v);
+    if (!fn) return DMFE_ERR_UNSUPPORTED;
+    size_t sm = hi_smem_bytes(v);
+    int dev = 0;
+    DMFE_CUDA_TRY(cudaGetDevice(&dev));
+    int max_optin = 0, nsm = 0;
+    DMFE_CUDA_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    DMFE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (sm > (size_t)max_optin) return DMFE_ERR_UNSUPPORTED;
+    DMFE_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int per_sm = 0;
+    DMFE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, HI_THREADS, sm));
+    if (per_sm < 1) return DMFE_ERR_UNSUPPORTED;
+    int want = (v.L + HI_WARPS - 1) / HI_WARPS;
+    int cap = nsm * per_sm;
+    *grid_ctas = want < cap ? want : cap;
+    *smem = sm;
+    return DMFE_OK;
+}
+
+int launch_history_integrals(const SolverView& v, const double* row_dev, double t, bool from_state,
+                             double* S_dev, int grid_ctas, cudaStream_t s) {
+    void* fn = hi_kernel_for(v);
+    if (!fn) return DMFE_ERR_UNSUPPORTED;
+    size_t sm = hi_smem_bytes(v);
+    int fs = from_state ? 1 : 0;
+    void* args[] = {(void*)&v, (void*)&row_dev, (void*)&t, (void*)&fs, (void*)&S_dev};
+    DMFE_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid_ctas), dim3(HI_THREADS), args, sm, s));
+    return DMFE_OK;
+}

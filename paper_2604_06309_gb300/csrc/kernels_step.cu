@@ -1,0 +1,577 @@
+// Kernels around the history integrals:
+//   (a)  stencil tables: fractional grid index of phi1, phi2 and psi for every (j, i)
+//        (Sec. 3.3, the precomputed theta-interpolation positions),
+//   RHS assembly: mu(t), E(t) and the total derivatives at fixed theta (Sec. 2.1),
+//   (c)  Dormand-Prince 5(4) stage combination, error estimate and the step rule with
+//        rollback (Sec. 3.5), all decided on the device,
+//   (d)  sparsification (Sec. 3.6): residuals of every candidate slice, the greedy
+//        "remove n, skip n+1" selection, and compaction into the other history buffer,
+//   two-time lookups C(t,t'), R(t,t') for the API.
+// Single-CTA kernels use a fixed reduction tree, so every result is deterministic.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "dmfe_internal.h"
+
+namespace {
+
+constexpr int CTL_THREADS = 1024;
+
+// Dormand & Prince (1980) RK5(4)7M coefficients. Stage l of the seven uses row l of A.
+__constant__ double kDP_C[7] = {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0};
+__constant__ double kDP_A[7][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5, 0, 0, 0, 0, 0},
+    {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+    {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+    {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84},
+};
+// e = b5 - b4 (embedded error weights)
+__constant__ double kDP_E[7] = {35.0 / 384 - 5179.0 / 57600, 0.0, 500.0 / 1113 - 7571.0 / 16695,
+                                125.0 / 192 - 393.0 / 640, -2187.0 / 6784 + 92097.0 / 339200,
+                                11.0 / 84 - 187.0 / 2100, -1.0 / 40};
+
+// ---------------------------------------------------------------- grid inverse
+__device__ double z_of_i_dev(double i, int L, double alpha, double delta) {
+    double y = (2.0 * i - 1.0 - L) / (L - 1.0);
+    auto g = [delta](double x) {
+        double v = cbrt(fabs(x) * x * x + delta * delta * delta) - delta;
+        return x < 0 ? -v : v;
+    };
+    double phi = 0.5 * (L - 1.0) * (g(y) / g(1.0) + 1.0) + 1.0;
+    return alpha * phi + (1.0 - alpha) * i;
+}
+
+// 0-based fractional index x with theta(x + 1) = th (Eq. theta inverted); om = 1 - th.
+__device__ double frac_index_dev(const SolverView& v, double th, double om) {
+    const int L = v.L;
+    double y = th <= 0.5 ? log(tan(v.ga + th * v.gD)) / v.gamma : -log(tan(v.ga + om * v.gD)) / v.gamma;
+    double z = 0.5 * (y * (L - 1.0) + 1.0 + L);
+    double i = z;
+    if (v.alpha != 0.0 && v.delta != 0.0) {
+        double lo = 1.0, hi = (double)L;
+        for (int it = 0; it < 80; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (z_of_i_dev(mid, L, v.alpha, v.delta) < z) lo = mid; else hi = mid;
+        }
+        i = 0.5 * (lo + hi);
+    }
+    double x = i - 1.0;
+    return x < 0.0 ? 0.0 : (x > L - 1.0 ? L - 1.0 : x);
+}
+
+__global__ void k_tables(SolverView v, double* x1, double* x2, double* x3, uint32_t* p1, uint32_t* p2,
+                         uint32_t* p3) {
+    const long long LL = (long long)v.L * v.L;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < LL;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(idx / v.L), i = (int)(idx % v.L);
+        const double thj = v.theta[j], omj = v.omega[j], thi = v.theta[i], omi = v.omega[i];
+        // phi1 = theta_i theta_j, 1 - phi1 = omega_i + theta_i omega_j
+        const double ph1 = thj * thi, oph1 = omi + thi * omj;
+        // phi2 = theta_j + omega_j theta_i, 1 - phi2 = omega_j omega_i
+        const double ph2 = thj + omj * thi, oph2 = omj * omi;
+        // psi = theta_j / phi2, 1 - psi = omega_j theta_i / phi2 (psi = 0 where phi2 = 0)
+        double ps = 0.0, ops = 1.0;
+        if (ph2 > 0.0) { ps = thj / ph2; ops = omj * thi / ph2; }
+        const double a = frac_index_dev(v, ph1, oph1);
+        const double b = frac_index_dev(v, ph2, oph2);
+        const double c = frac_index_dev(v, ps, ops);
+        if (x1) { x1[idx] = a; x2[idx] = b; x3[idx] = c; }
+        if (p1) {
+            const double sc = (double)(1u << FIX_FRAC_BITS);
+            p1[idx] = (uint32_t)llrint(a * sc);
+            p2[idx] = (uint32_t)llrint(b * sc);
+            p3[idx] = (uint32_t)llrint(c * sc);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- reductions
+__device__ double block_sum(double x, double* red) {
+    const int tid = threadIdx.x;
+    red[tid] = x;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (tid < w) red[tid] += red[tid + w];
+        __syncthreads();
+    }
+    double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// mu, E and the total derivatives (dCf/dt, dRf/dt at fixed theta) of the row (C, R) at
+// time t from the history sums S (layout of dmfe_history_integrals). One CTA.
+//   d1C = -mu C + t [theta (S0 + S2) + omega S1] + beta0 f'(C(t,0)) C(t',0)
+//   d1R = -mu R + t omega S3
+//   mu' = mu(t') = T + t theta S8 + beta0 f'(C(t',0)) C(t',0)
+//   d2C = -mu' C + t [theta (S4 + S5) + omega S6] + 2 T R + beta0 f'(C(t',0)) C(t,0)
+//   d2R =  mu' R - t omega S7
+//   dC  = d1C + theta d2C,  dR = d1R + theta d2R,  0 at theta = 1 (pinned diagonal).
+__device__ void assemble_core(const SolverView& v, const double* row, const double* S, double t,
+                              double* dC, double* dR, double* mu_out, double* E_out, double* red) {
+    const int L = v.L;
+    double pm = 0.0, pe = 0.0;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const double C = row[i], R = row[L + i];
+        const double K = fp2(v.poly, C) * R, D = fp1(v.poly, C);
+        pm += v.nu[i] * (K * C + D * R);
+        pe += v.nu[i] * (D * R);
+    }
+    const double sm = block_sum(pm, red);
+    const double se = block_sum(pe, red);
+    const double C0 = row[0];
+    const double mu = v.T + t * sm + v.beta0 * fp1(v.poly, C0) * C0;
+    const double E = -t * se - v.beta0 * fp0(v.poly, C0);
+    for (int j = threadIdx.x; j < L; j += blockDim.x) {
+        const double th = v.theta[j], om = v.omega[j];
+        const double C = row[j], R = row[L + j];
+        const double* s = S + j;
+        const double S0 = s[0], S1 = s[L], S2 = s[2 * L], S3 = s[3 * L], S4 = s[4 * L];
+        const double S5 = s[5 * L], S6 = s[6 * L], S7 = s[7 * L], S8 = s[8 * L], S9 = s[9 * L];
+        const double d1C = -mu * C + t * (th * (S0 + S2) + om * S1) + v.beta0 * fp1(v.poly, C0) * S9;
+        const double d1R = -mu * R + t * om * S3;
+        const double mup = v.T + t * th * S8 + v.beta0 * fp1(v.poly, S9) * S9;
+        const double d2C = -mup * C + t * (th * (S4 + S5) + om * S6) + 2.0 * v.T * R +
+                           v.beta0 * fp1(v.poly, S9) * C0;
+        const double d2R = mup * R - t * om * S7;
+        const bool diag = (j == L - 1);
+        dC[j] = diag ? 0.0 : d1C + th * d2C;
+        dR[j] = diag ? 0.0 : d1R + th * d2R;
+    }
+    if (mu_out) *mu_out = mu;
+    if (E_out) *E_out = E;
+}
+
+__global__ void __launch_bounds__(CTL_THREADS) k_assemble(SolverView v, const double* row, const double* S,
+                                                          double t, double* dC, double* dR, double* muE) {
+    __shared__ double red[CTL_THREADS];
+    double mu, E;
+    assemble_core(v, row, S, t, dC, dR, &mu, &E, red);
+    if (threadIdx.x == 0 && muE) { muE[0] = mu; muE[1] = E; }
+}
+
+// The initial slice t = 0, Cf = Rf = 1: every history integral carries a factor t, and
+// C(t', 0) = C(0, 0) = 1, so S = 0 except S[9] = 1.
+__global__ void __launch_bounds__(CTL_THREADS) k_initial(SolverView v) {
+    __shared__ double red[CTL_THREADS];
+    const int L = v.L;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        v.Y[i] = 1.0;
+        v.Y[L + i] = 1.0;
+        for (int r = 0; r < DMFE_NS; ++r) v.S[(size_t)r * L + i] = (r == 9) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    double* dC = v.k;
+    double* dR = v.k + L;
+    double mu, E;
+    assemble_core(v, v.Y, v.S, 0.0, dC, dR, &mu, &E, red);
+    __syncthreads();
+    const int act = v.st->active;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        v.hist[act][i] = dbl4{1.0, dC[i], 1.0, dR[i]};
+        if (v.hist32[act]) v.hist32[act][i] = make_float4(1.f, (float)dC[i], 1.f, (float)dR[i]);
+    }
+    if (threadIdx.x == 0) {
+        v.ht[act][0] = 0.0;
+        DevState* st = v.st;
+        st->n = 1;
+        st->t = 0.0;
+        st->mu = mu;
+        st->E = E;
+    }
+}
+
+__device__ __forceinline__ bool gated(const DevState* st) { return st->status != 0 || st->done; }
+
+// Write slice `slot` = (t, Y, dY) to the active buffer (FP64 master and FP32 replica).
+__device__ void append_slice(const SolverView& v, int act, int slot, double t, const double* Y,
+                             const double* dY) {
+    const int L = v.L;
+    dbl4* H = v.hist[act] + (size_t)slot * L;
+    float4* H32 = v.hist32[act] ? v.hist32[act] + (size_t)slot * L : nullptr;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const dbl4 e{Y[i], dY[i], Y[L + i], dY[L + i]};
+        H[i] = e;
+        if (H32) H32[i] = make_float4((float)e.x, (float)e.y, (float)e.z, (float)e.w);
+    }
+    if (threadIdx.x == 0) v.ht[act][slot] = t;
+}
+
+// Stage combination Y = y + h sum_{l <= last} A[row][l] k_l, rounded like the plain sum.
+__device__ void combine(const SolverView& v, const dbl4* yrow, double h, int arow, int nk) {
+    const int L = v.L;
+    const int L2 = 2 * L;
+    for (int q = threadIdx.x; q < L2; q += blockDim.x) {
+        const int i = q < L ? q : q - L;
+        const double y = q < L ? yrow[i].x : yrow[i].z;
+        double acc = 0.0;
+        for (int l = 0; l < nk; ++l) acc = __dadd_rn(acc, __dmul_rn(kDP_A[arow][l], v.k[(size_t)l * L2 + q]));
+        v.Y[q] = __dadd_rn(y, __dmul_rn(h, acc));
+    }
+}
+
+__global__ void __launch_bounds__(CTL_THREADS) k_begin_integrate(SolverView v, double t_target, double tol) {
+    if (threadIdx.x != 0) return;
+    DevState* st = v.st;
+    st->t_target = t_target;
+    st->tol = tol;
+    st->done = (st->t >= t_target) ? 1 : 0;
+}
+
+// Start of a trial step: h = min(dt, t_target - t), k_1 = stored derivative of the last
+// slice (first-same-as-last), Y_2 = y + h a_21 k_1.
+__global__ void __launch_bounds__(CTL_THREADS) k_step_begin(SolverView v) {
+    DevState* st = v.st;
+    if (gated(st)) return;
+    const int L = v.L;
+    const int act = st->active;
+    const dbl4* yrow = v.hist[act] + (size_t)(st->n - 1) * L;
+    const double t = st->t;
+    const double h = fmin(st->dt, st->t_target - t);
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        v.k[i] = yrow[i].y;
+        v.k[L + i] = yrow[i].w;
+    }
+    __syncthreads();
+    combine(v, yrow, h, 1, 1);
+    if (threadIdx.x == 0) {
+        st->h = h;
+        st->t_stage = __dadd_rn(t, __dmul_rn(kDP_C[1], h));
+    }
+}
+
+// End of stage `stg` (1..6): k_stg from the sums S; then either the next stage row or,
+// after the last stage, the error estimate and the step decision of Sec. 3.5.
+__global__ void __launch_bounds__(CTL_THREADS) k_stage_end(SolverView v, int stg) {
+    __shared__ double red[CTL_THREADS];
+    __shared__ int s_append;
+    DevState* st = v.st;
+    if (gated(st)) return;
+    const int L = v.L;
+    const int L2 = 2 * L;
+    const int act = st->active;
+    const int n = st->n;
+    const dbl4* yrow = v.hist[act] + (size_t)(n - 1) * L;
+    const double t = st->t, h = st->h;
+    double mu, E;
+    assemble_core(v, v.Y, v.S, st->t_stage, v.k + (size_t)stg * L2, v.k + (size_t)stg * L2 + L, &mu, &E, red);
+    __syncthreads();
+    if (stg < 6) {
+        combine(v, yrow, h, stg + 1, stg + 1);
+        if (threadIdx.x == 0) {
+            st->stages += 1;
+            st->t_stage = __dadd_rn(t, __dmul_rn(kDP_C[stg + 1], h));
+        }
+        return;
+    }
+    // eps_RK = sum_i |dC_i| + |dR_i| with the embedded estimate h sum_l e_l k_l
+    double pe = 0.0;
+    for (int q = threadIdx.x; q < L2; q += blockDim.x) {
+        double acc = 0.0;
+        for (int l = 0; l < 7; ++l) acc = __dadd_rn(acc, __dmul_rn(kDP_E[l], v.k[(size_t)l * L2 + q]));
+        pe += fabs(__dmul_rn(h, acc));
+    }
+    const double eps = block_sum(pe, red);
+    if (threadIdx.x == 0) {
+        st->stages += 1;
+        st->eps = eps;
+        st->mu = mu;
+        st->E = E;
+        s_append = -1;
+        const double tol = st->tol;
+        if (!isfinite(eps)) {
+            st->status = DMFE_ERR_NONFINITE;
+        } else if (eps > 2.0 * tol) {
+            // reject: revert the last min(10, n-1) slices and halve the step
+            st->steps_rejected += 1;
+            const int drop = n - 1 < 10 ? n - 1 : 10;
+            st->n = n - drop;
+            st->t = v.ht[act][n - drop - 1];
+            st->dt *= 0.5;
+        } else {
+            st->steps_accepted += 1;
+            const double tnew = (h < st->t_target - t) ? t + h : st->t_target;
+            if (n >= v.cap) {
+                if (v.sparsify) { st->pending = 1; st->t_pending = tnew; }
+                else st->status = DMFE_ERR_CAPACITY;
+            } else {
+                s_append = n;
+                st->t_pending = tnew;
+            }
+            if (eps > tol) st->dt *= 0.9;
+            else if (eps < 0.5 * tol) st->dt *= 1.01;
+        }
+        if (st->status == 0 && st->dt < st->dt_min) st->status = DMFE_ERR_STEP_UNDERFLOW;
+    }
+    __syncthreads();
+    if (s_append >= 0) {
+        append_slice(v, act, s_append, st->t_pending, v.Y, v.k + (size_t)6 * L2);
+        if (threadIdx.x == 0) {
+            st->n = s_append + 1;
+            st->t = st->t_pending;
+            if (st->t >= st->t_target) st->done = 1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- sparsification
+__device__ __forceinline__ double herm_int(double y0, double d0, double y1, double d1, double h) {
+    return 0.5 * h * (y0 + y1) + h * h * (d0 - d1) / 12.0;
+}
+
+__device__ __forceinline__ bool sp_active(const DevState* st, int from_step) {
+    return from_step ? (st->pending != 0 && st->status == 0) : true;
+}
+
+// eps_sparse(n) for candidates n = 1 .. N-12: one warp per candidate.
+__global__ void k_sp_residual(SolverView v, int from_step) {
+    const DevState* st = v.st;
+    if (!sp_active(st, from_step)) return;
+    const int L = v.L;
+    const int N = st->n;
+    const int last = N - 12;
+    const int act = st->active;
+    const dbl4* H = v.hist[act];
+    const double* ht = v.ht[act];
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int n = 1 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); n <= last; n += nw) {
+        const double h1 = ht[n] - ht[n - 1], h2 = ht[n + 1] - ht[n];
+        const dbl4* a = H + (size_t)(n - 1) * L;
+        const dbl4* b = H + (size_t)n * L;
+        const dbl4* c = H + (size_t)(n + 1) * L;
+        double acc = 0.0;
+        for (int i = lane; i < L; i += 32) {
+            const dbl4 A = a[i], B = b[i], Cc = c[i];
+            const double wC = herm_int(A.x, A.y, B.x, B.y, h1) + herm_int(B.x, B.y, Cc.x, Cc.y, h2);
+            const double oC = herm_int(A.x, A.y, Cc.x, Cc.y, h1 + h2);
+            const double wR = herm_int(A.z, A.w, B.z, B.w, h1) + herm_int(B.z, B.w, Cc.z, Cc.w, h2);
+            const double oR = herm_int(A.z, A.w, Cc.z, Cc.w, h1 + h2);
+            acc += fabs(wC - oC) + fabs(wR - oR);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) v.eps_sp[n] = acc;
+    }
+}
+
+// Greedy scan of Sec. 3.6 (remove n if eps < tol/10, then skip n+1), forced removal of the
+// smallest residual when nothing qualifies, and the compaction map. Single thread: the
+// scan is sequential by definition and runs once per pass.
+__global__ void k_sp_select(SolverView v, int from_step, double tol_arg) {
+    DevState* st = v.st;
+    if (!sp_active(st, from_step) || threadIdx.x != 0) return;
+    const int N = st->n;
+    const int last = N - 12;
+    const double tol = from_step ? st->tol : tol_arg;
+    st->sp_ran = 0;
+    if (last < 1) {
+        if (from_step) st->status = DMFE_ERR_CAPACITY;
+        return;
+    }
+    for (int k = 0; k < N; ++k) v.keep[k] = 1;
+    int removed = 0;
+    double mx = st->max_eps_sparse;
+    for (int k = 1; k <= last;) {
+        if (v.eps_sp[k] < tol / 10.0) {
+            v.keep[k] = 0;
+            ++removed;
+            mx = fmax(mx, v.eps_sp[k]);
+            k += 2;
+        } else {
+            ++k;
+        }
+    }
+    if (removed == 0) {
+        int m = 1;
+        for (int k = 2; k <= last; ++k)
+            if (v.eps_sp[k] < v.eps_sp[m]) m = k;
+        v.keep[m] = 0;
+        removed = 1;
+        mx = fmax(mx, v.eps_sp[m]);
+        st->forced_removals += 1;
+    }
+    int c = 0;
+    for (int k = 0; k < N; ++k) {
+        v.newidx[k] = c;
+        c += v.keep[k];
+    }
+    st->max_eps_sparse = mx;
+    st->sparsify_passes += 1;
+    st->slices_removed += removed;
+    st->removed_count = removed;
+    st->n_new = c;
+    st->sp_ran = 1;
+}
+
+__global__ void k_sp_compact(SolverView v) {
+    const DevState* st = v.st;
+    if (!st->sp_ran) return;
+    const int L = v.L;
+    const int N = st->n;
+    const int act = st->active, nxt = 1 - act;
+    const long long tot = (long long)N * L;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < tot;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(q / L), i = (int)(q % L);
+        if (!v.keep[k]) continue;
+        const size_t dst = (size_t)v.newidx[k] * L + i;
+        v.hist[nxt][dst] = v.hist[act][q];
+        if (v.hist32[act]) v.hist32[nxt][dst] = v.hist32[act][q];
+        if (i == 0) v.ht[nxt][v.newidx[k]] = v.ht[act][k];
+    }
+}
+
+__global__ void __launch_bounds__(CTL_THREADS) k_sp_finish(SolverView v) {
+    DevState* st = v.st;
+    if (!st->sp_ran) return;
+    __syncthreads();
+    const int nxt = 1 - st->active;
+    const int nn = st->n_new;
+    const bool pend = st->pending != 0;
+    __syncthreads();
+    if (pend) append_slice(v, nxt, nn, st->t_pending, v.Y, v.k + (size_t)6 * 2 * v.L);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->active = nxt;
+        st->n = pend ? nn + 1 : nn;
+        st->sp_ran = 0;
+        if (pend) {
+            st->pending = 0;
+            st->t = st->t_pending;
+            if (st->t >= st->t_target) st->done = 1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- lookups
+__global__ void k_lookup(SolverView v, int nq, const double* tq, const double* tpq, int which, double* out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    const DevState* st = v.st;
+    const int L = v.L, n = st->n, act = st->active, s = v.s;
+    const double t = tq[q], tp = tpq[q];
+    if (which == 1 && tp > t) { out[q] = 0.0; return; }
+    const double big = fmax(t, tp), small = fmin(t, tp);
+    const double th = big > 0 ? small / big : 1.0;
+    const double om = big > 0 ? (big - small) / big : 0.0;
+    const double x = frac_index_dev(v, th, om);
+    int b = (int)floor(x) - s / 2 + 1;
+    b = b < 0 ? 0 : (b > L - s ? L - s : b);
+    const double u = x - b;
+    double w[16];
+    for (int k = 0; k < s; ++k) {
+        double p = 1.0;
+        for (int m = 0; m < s; ++m)
+            if (m != k) p *= (u - m) / (double)(k - m);
+        w[k] = p;
+    }
+    const dbl4* H = v.hist[act];
+    const double* ht = v.ht[act];
+    auto val = [&](int sl, bool deriv) {
+        double acc = 0.0;
+        for (int k = 0; k < s; ++k) {
+            const dbl4 e = H[(size_t)sl * L + b + k];
+            acc += w[k] * (which == 0 ? (deriv ? e.y : e.x) : (deriv ? e.w : e.z));
+        }
+        return acc;
+    };
+    if (n == 1) { out[q] = val(0, false); return; }
+    int lo = 0, hi = n - 2;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ht[mid] <= big) lo = mid; else hi = mid - 1;
+    }
+    const double hh = ht[lo + 1] - ht[lo];
+    const double sg = (big - ht[lo]) / hh, o = 1.0 - sg;
+    out[q] = (1.0 + 2.0 * sg) * o * o * val(lo, false) + sg * o * o * hh * val(lo, true) +
+             sg * sg * (3.0 - 2.0 * sg) * val(lo + 1, false) + sg * sg * (sg - 1.0) * hh * val(lo + 1, true);
+}
+
+__global__ void k_refresh_replica(SolverView v) {
+    const DevState* st = v.st;
+    const int act = st->active;
+    const long long tot = (long long)st->n * v.L;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < tot;
+         q += (long long)gridDim.x * blockDim.x) {
+        const dbl4 e = v.hist[act][q];
+        v.hist32[act][q] = make_float4((float)e.x, (float)e.y, (float)e.z, (float)e.w);
+    }
+}
+
+int grid_for(long long work, int threads) {
+    long long g = (work + threads - 1) / threads;
+    if (g > 152LL * 16) g = 152LL * 16;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+int launch_tables(const SolverView& v, cudaStream_t s) {
+    const bool f64 = v.precision == DMFE_FP64;
+    k_tables<<<grid_for((long long)v.L * v.L, 256), 256, 0, s>>>(
+        v, f64 ? (double*)v.x1 : nullptr, f64 ? (double*)v.x2 : nullptr, f64 ? (double*)v.x3 : nullptr,
+        f64 ? nullptr : (uint32_t*)v.p1, f64 ? nullptr : (uint32_t*)v.p2, f64 ? nullptr : (uint32_t*)v.p3);
+    DMFE_CUDA_TRY(cudaGetLastError());
+    return DMFE_OK;
+}
+
+int launch_assemble(const SolverView& v, const double* row_dev, const double* S_dev, double t,
+                    double* dC, double* dR, double* muE, cudaStream_t s) {
+    k_assemble<<<1, CTL_THREADS, 0, s>>>(v, row_dev, S_dev, t, dC, dR, muE);
+    DMFE_CUDA_TRY(cudaGetLastError());
+    return DMFE_OK;
+}
+
+int launch_initial_slice(const SolverView& v, cudaStream_t s) {
+    k_initial<<<1, CTL_THREADS, 0, s>>>(v);
+    DMFE_CUDA_TRY(cudaGetLastError());
+    return DMFE_OK;
+}
+
+int launch_begin_integrate(const SolverView& v, double t_target, double tol, cudaStream_t s) {
+    k_begin_integrate<<<1, 32, 0, s>>>(v, t_target, tol);
+    DMFE_CUDA_TRY(cudaGetLastError());
+    return DMFE_OK;
+}
+
+int launch_sparsify(const SolverView& v, bool from_step, double tol, cudaStream_t s) {
+    const int fs = from_step ? 1 : 0;
+    k_sp_residual<<<grid_for((long long)v.cap * 32, 256), 256, 0, s>>>(v, fs);
+    k_sp_select<<<1, 32, 0, s>>>(v, fs, tol);
+    k_sp_compact<<<grid_for((long long)v.cap * v.L, 256), 256, 0, s>>>(v);
+    k_sp_finish<<<1, CTL_THREADS, 0, s>>>(v);
+    DMFE_CUDA_TRY(cudaGetLastError());
+    return DMFE_OK;
+}
+
+// One Dormand-Prince step: begin, six stages of (history integrals, stage end), then the
+// sparsification kernels, which do nothing unless the step left a slice pending.
+int launch_step(const SolverView& v, int grid_ctas, cudaStream_t s) {
+    k_step_begin<<<1, CTL_THREADS, 0, s>>>(v);
+    for (int stg = 1; stg <= 6; ++stg) {
+        int rc = launch_history_integrals(v, v.Y, 0.0, true, v.S, grid_ctas, s);
+        if (rc) return rc;
+        k_stage_end<<<1, CTL_THREADS, 0, s>>>(v, stg);
+    }
+    return launch_sparsify(v, true, 0.0, s);
+}
+
+int launch_lookup(const SolverView& v, int n, const double* t, const double* tp, int which, double* out,
+                  cudaStream_t s) {
+    k_lookup<<<(n + 127) / 128, 128, 0, s>>>(v, n, t, tp, which, out);
+    DMFE_CUDA_TRY(cudaGetLastError());
+    return DMFE_OK;
+}
+
+int launch_refresh_replica(const SolverView& v, cudaStream_t s) {
+    if (!v.hist32[0]) return DMFE_OK;
+    k_refresh_replica<<<grid_for((long long)v.cap * v.L, 256), 256, 0, s>>>(v);
+    DMFE_CUDA_TRY(cudaGetLastError());
+    return DMFE_OK;
+}

@@ -1,0 +1,265 @@
+"""Thin ctypes binding of libdmfe.so (include/dmfe.h).
+
+Argument marshalling only: every step of the computation runs in the library's CUDA
+kernels. Loading fails loudly (OSError) if the library has not been built; there is
+no CPU fallback. The functions keep the C names (``dmfe_create`` ...); ``Solver`` wraps
+them for numpy arrays and torch device tensors.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdmfe.so")
+
+DMFE_OK = 0
+DMFE_ERR_ARG = -1
+DMFE_ERR_OOM = -2
+DMFE_ERR_NONFINITE = -3
+DMFE_ERR_STEP_UNDERFLOW = -4
+DMFE_ERR_CAPACITY = -5
+DMFE_ERR_CUDA = -6
+DMFE_ERR_TIMEOUT = -7
+DMFE_ERR_UNSUPPORTED = -8
+DMFE_ERR_IO = -9
+DMFE_FP64 = 0
+DMFE_FP32_COMPENSATED = 1
+DMFE_NS = 10
+
+_d = ctypes.c_double
+_i = ctypes.c_int
+_p = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+class dmfe_params(ctypes.Structure):
+    _fields_ = [("n_terms", _i), ("powers", _ip), ("coefs", _dp), ("T", _d), ("beta0", _d),
+                ("L", _i), ("s", _i), ("grid_t_max", _d), ("alpha", _d), ("delta", _d),
+                ("history_cap", _i), ("dt0", _d), ("dt_min", _d), ("precision", _i),
+                ("sparsify", _i), ("stream", _p)]
+
+
+class dmfe_stats_t(ctypes.Structure):
+    _fields_ = [("t", _d), ("dt", _d), ("mu", _d), ("E", _d), ("last_eps", _d),
+                ("max_eps_sparse", _d), ("steps_accepted", ctypes.c_longlong),
+                ("steps_rejected", ctypes.c_longlong), ("stages", ctypes.c_longlong),
+                ("sparsify_passes", ctypes.c_longlong), ("slices_removed", ctypes.c_longlong),
+                ("forced_removals", ctypes.c_longlong), ("n_slices", _i), ("status", _i),
+                ("L", _i), ("history_cap", _i), ("s", _i), ("precision", _i)]
+
+
+_SIGS = {
+    "dmfe_default_params": (None, [ctypes.POINTER(dmfe_params)]),
+    "dmfe_strerror": (ctypes.c_char_p, [_i]),
+    "dmfe_create": (_i, [ctypes.POINTER(dmfe_params), ctypes.POINTER(_p)]),
+    "dmfe_destroy": (None, [_p]),
+    "dmfe_grid": (_i, [_p, _dp, _dp, _dp]),
+    "dmfe_tables": (_i, [_p, _dp, _dp, _dp]),
+    "dmfe_integrate": (_i, [_p, _d, _d]),
+    "dmfe_step": (_i, [_p, _i, _d, _d, _p]),
+    "dmfe_get_C": (_i, [_p, _i, _dp, _dp, _dp]),
+    "dmfe_get_R": (_i, [_p, _i, _dp, _dp, _dp]),
+    "dmfe_get_row": (_i, [_p, _dp, _dp, _dp, _dp, _dp]),
+    "dmfe_set_history": (_i, [_p, _i, _dp, _dp, _dp, _dp, _dp]),
+    "dmfe_get_history": (_i, [_p, _ip, _dp, _dp, _dp, _dp, _dp]),
+    "dmfe_history_integrals": (_i, [_p, _d, _dp, _dp, _dp, _dp]),
+    "dmfe_history_integrals_dev": (_i, [_p, _d, _p, _p, _p]),
+    "dmfe_rhs": (_i, [_p, _d, _dp, _dp, _dp, _dp, _dp, _dp]),
+    "dmfe_sparsify": (_i, [_p, _d, _ip]),
+    "dmfe_stats": (_i, [_p, ctypes.POINTER(dmfe_stats_t)]),
+    "dmfe_checkpoint": (_i, [_p, ctypes.c_char_p]),
+    "dmfe_restore": (_i, [ctypes.c_char_p, _p, ctypes.POINTER(_p)]),
+    "dmfe_sync": (_i, [_p]),
+}
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libdmfe.so (raises OSError if it is missing) and declare the signatures."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise OSError("libdmfe.so not built at %s (run __graft_entry__.build())" % path)
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class DMFEError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        msg = load().dmfe_strerror(code).decode()
+        super().__init__("%s: %s (%d)" % (where, msg, code))
+
+
+def _check(rc, where):
+    if rc != DMFE_OK:
+        raise DMFEError(rc, where)
+    return rc
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a
+
+
+class Solver:
+    """A dmfe_solver handle. coefs: {power: coefficient} for f(q) = sum c_p q^p."""
+
+    def __init__(self, coefs, T, L, grid_t_max, s=4, beta0=0.0, alpha=0.0, delta=0.0,
+                 history_cap=None, dt0=1e-4, dt_min=1e-12, precision="fp64", sparsify=True,
+                 stream=None):
+        lib = load()
+        self._lib = lib
+        self.h = _p()
+        terms = sorted((int(p), float(c)) for p, c in dict(coefs).items())
+        pw = (ctypes.c_int * len(terms))(*[p for p, _ in terms])
+        cf = (ctypes.c_double * len(terms))(*[c for _, c in terms])
+        prm = dmfe_params()
+        lib.dmfe_default_params(ctypes.byref(prm))
+        prm.n_terms = len(terms)
+        prm.powers = ctypes.cast(pw, _ip)
+        prm.coefs = ctypes.cast(cf, _dp)
+        prm.T, prm.beta0, prm.L, prm.s = T, beta0, L, s
+        prm.grid_t_max, prm.alpha, prm.delta = grid_t_max, alpha, delta
+        prm.history_cap = int(history_cap) if history_cap else L
+        prm.dt0, prm.dt_min = dt0, dt_min
+        prm.precision = DMFE_FP64 if precision == "fp64" else DMFE_FP32_COMPENSATED
+        prm.sparsify = 1 if sparsify else 0
+        prm.stream = stream
+        _check(lib.dmfe_create(ctypes.byref(prm), ctypes.byref(self.h)), "dmfe_create")
+        self._sizes()
+
+    def _sizes(self):
+        st = self.stats()
+        self.L, self.cap = st["L"], st["history_cap"]
+        th, om, nu = (np.empty(self.L) for _ in range(3))
+        _check(self._lib.dmfe_grid(self.h, _ptr(th), _ptr(om), _ptr(nu)), "dmfe_grid")
+        self.theta, self.omega, self.nu = th, om, nu
+
+    @classmethod
+    def restore(cls, path, stream=None):
+        lib = load()
+        obj = cls.__new__(cls)
+        obj._lib = lib
+        obj.h = _p()
+        _check(lib.dmfe_restore(path.encode(), stream, ctypes.byref(obj.h)), "dmfe_restore")
+        obj._sizes()
+        return obj
+
+    def close(self):
+        if self.h:
+            self._lib.dmfe_destroy(self.h)
+            self.h = _p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- calls
+    def integrate(self, t_max, tol, check=False):
+        rc = self._lib.dmfe_integrate(self.h, float(t_max), float(tol))
+        if check:
+            _check(rc, "dmfe_integrate")
+        return rc
+
+    def step(self, nsteps, t_max, tol, stream_ptr=None):
+        """Launch nsteps device-driven trial steps without synchronising."""
+        _check(self._lib.dmfe_step(self.h, int(nsteps), float(t_max), float(tol),
+                                   _p(stream_ptr) if stream_ptr else None), "dmfe_step")
+
+    def tables(self):
+        x = [np.empty((self.L, self.L)) for _ in range(3)]
+        _check(self._lib.dmfe_tables(self.h, *[_ptr(a) for a in x]), "dmfe_tables")
+        return x
+
+    def _two_time(self, fn, t, tp):
+        t, tp = np.broadcast_arrays(np.atleast_1d(np.asarray(t, float)), np.atleast_1d(np.asarray(tp, float)))
+        t, tp = _f64(t.ravel()), _f64(tp.ravel())
+        out = np.empty(t.size)
+        _check(fn(self.h, t.size, _ptr(t), _ptr(tp), _ptr(out)), fn.__name__)
+        return out
+
+    def get_C(self, t, tp):
+        return self._two_time(self._lib.dmfe_get_C, t, tp)
+
+    def get_R(self, t, tp):
+        return self._two_time(self._lib.dmfe_get_R, t, tp)
+
+    def get_row(self):
+        t, mu, E = _d(), _d(), _d()
+        C, R = np.empty(self.L), np.empty(self.L)
+        _check(self._lib.dmfe_get_row(self.h, ctypes.byref(t), _ptr(C), _ptr(R), ctypes.byref(mu),
+                                      ctypes.byref(E)), "dmfe_get_row")
+        return t.value, C, R, mu.value, E.value
+
+    def set_history(self, t, C, dC, R, dR):
+        t = _f64(t)
+        n = t.size
+        arrs = [_f64(a, n * self.L) for a in (C, dC, R, dR)]
+        _check(self._lib.dmfe_set_history(self.h, n, _ptr(t), *[_ptr(a) for a in arrs]), "dmfe_set_history")
+
+    def get_history(self):
+        n = _i()
+        t = np.empty(self.cap)
+        arrs = [np.empty((self.cap, self.L)) for _ in range(4)]
+        _check(self._lib.dmfe_get_history(self.h, ctypes.byref(n), _ptr(t), *[_ptr(a) for a in arrs]),
+               "dmfe_get_history")
+        k = n.value
+        return (t[:k],) + tuple(a[:k] for a in arrs)
+
+    def history_integrals(self, t, C, R):
+        C, R = _f64(C, self.L), _f64(R, self.L)
+        S = np.empty((DMFE_NS, self.L))
+        mu = _d()
+        _check(self._lib.dmfe_history_integrals(self.h, float(t), _ptr(C), _ptr(R), _ptr(S), ctypes.byref(mu)),
+               "dmfe_history_integrals")
+        return S, mu.value
+
+    def history_integrals_dev(self, t, row_dev_ptr, S_dev_ptr, stream_ptr=None):
+        """Device-pointer entry: row_dev [2][L] float64, S_dev [NS][L] float64 (torch data_ptr())."""
+        _check(self._lib.dmfe_history_integrals_dev(self.h, float(t), _p(row_dev_ptr), _p(S_dev_ptr),
+                                                    _p(stream_ptr) if stream_ptr else None),
+               "dmfe_history_integrals_dev")
+
+    def rhs(self, t, C, R):
+        C, R = _f64(C, self.L), _f64(R, self.L)
+        dC, dR = np.empty(self.L), np.empty(self.L)
+        mu, E = _d(), _d()
+        _check(self._lib.dmfe_rhs(self.h, float(t), _ptr(C), _ptr(R), _ptr(dC), _ptr(dR), ctypes.byref(mu),
+                                  ctypes.byref(E)), "dmfe_rhs")
+        return dC, dR, mu.value, E.value
+
+    def sparsify(self, tol):
+        """One pass (Sec. 3.6); returns a boolean mask over the slices before the pass."""
+        n = self.stats()["n_slices"]
+        removed = (ctypes.c_int * self.cap)()
+        _check(self._lib.dmfe_sparsify(self.h, float(tol), ctypes.cast(removed, _ip)), "dmfe_sparsify")
+        return np.array(removed[:n], dtype=bool)
+
+    def stats(self):
+        s = dmfe_stats_t()
+        _check(self._lib.dmfe_stats(self.h, ctypes.byref(s)), "dmfe_stats")
+        return {name: getattr(s, name) for name, _ in dmfe_stats_t._fields_}
+
+    def checkpoint(self, path):
+        _check(self._lib.dmfe_checkpoint(self.h, path.encode()), "dmfe_checkpoint")
+
+    def sync(self):
+        return self._lib.dmfe_sync(self.h)

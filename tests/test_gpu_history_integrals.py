@@ -1,0 +1,105 @@
+"""Parity of the history-integral kernel (b) with the oracle on seeded frozen histories."""
+import numpy as np
+import pytest
+
+from gpu_common import frozen_case, need_gpu
+from oracle import closed_forms as cf
+from oracle import integrals as OI
+from oracle.model import Model
+from paper_2604_06309_gb300.inputs import MIXED_34, PURE_3
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-11, "fp32": 3e-6}
+
+
+def _oracle_S(coefs, T, L, t_max, s, hist, t, C, R, js=None):
+    G = OI.Grid(L, t_max, s)
+    H = OI.History(*hist)
+    return OI.history_integrals(Model(coefs, T), G, H, t, C, R, js=js)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("L,s,n", [(33, 4, 40), (129, 4, 130), (129, 6, 1), (129, 10, 2), (257, 8, 61), (100, 4, 17)])
+def test_frozen_history_at_last_slice(precision, L, s, n):
+    need_gpu()
+    from paper_2604_06309_gb300 import Solver
+    sv = Solver(MIXED_34, 0.5, L, 1e3, s=s, history_cap=max(n, 16), precision=precision)
+    t_last = 300.0 if n > 1 else 0.0
+    hist = frozen_case(sv, 11 + L + n, n, t_last)
+    t = hist[0][-1]
+    if t == 0.0:
+        t = 0.0
+    C, R = hist[1][-1], hist[3][-1]
+    S, mu = sv.history_integrals(t, C, R)
+    Sref = _oracle_S(MIXED_34, 0.5, L, 1e3, s, hist, t, C, R)
+    assert np.max(np.abs(S - Sref)) < TOL[precision]
+    sv.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_stage_beyond_last_slice_uses_quadratic_extension(precision):
+    need_gpu()
+    from paper_2604_06309_gb300 import Solver
+    from paper_2604_06309_gb300.inputs import SyntheticFields
+    L = 129
+    sv = Solver(PURE_3, 0.8, L, 1e3, history_cap=64, precision=precision)
+    hist = frozen_case(sv, 5, 50, 20.0)
+    t = 20.0 + 0.37
+    C, _, R, _ = SyntheticFields(99).rows(t, sv.theta, sv.omega)
+    S, _ = sv.history_integrals(t, C, R)
+    Sref = _oracle_S(PURE_3, 0.8, L, 1e3, 4, hist, t, C, R)
+    assert np.max(np.abs(S - Sref)) < TOL[precision]
+    sv.close()
+
+
+def test_exact_p2_history():
+    need_gpu()
+    from paper_2604_06309_gb300 import Solver
+    L = 129
+    sv = Solver({2: 0.5}, 0.0, L, 100.0, s=6, history_cap=401)
+    times = np.concatenate([[0.0], np.geomspace(1e-3, 5.0, 400)])
+    C, dC, R, dR = cf.p2_history(times, sv.theta, sv.omega)
+    sv.set_history(times, C, dC, R, dR)
+    S, mu = sv.history_integrals(5.0, C[-1], R[-1])
+    Sref = _oracle_S({2: 0.5}, 0.0, L, 100.0, 6, (times, C, dC, R, dR), 5.0, C[-1], R[-1])
+    assert np.max(np.abs(S - Sref)) < 1e-11
+    assert abs(mu - cf.p2_mu(5.0)) < 1e-8
+    sv.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_full_size_sampled_rows(precision):
+    """L = 2049 with 2049 stored slices (the benchmark shape) at the benchmark launch
+    configuration; the oracle evaluates a sample of output rows one by one."""
+    need_gpu()
+    from paper_2604_06309_gb300 import Solver
+    L = 2049
+    sv = Solver(MIXED_34, 0.5, L, 1e5, history_cap=L, precision=precision)
+    hist = frozen_case(sv, 2049, L, 1e5)
+    t = hist[0][-1]
+    C, R = hist[1][-1], hist[3][-1]
+    S, _ = sv.history_integrals(t, C, R)
+    js = [0, 1, 2, 700, 1024, 1500, 2000, 2046, 2047, 2048]
+    Sref = _oracle_S(MIXED_34, 0.5, L, 1e5, 4, hist, t, C, R, js=js)
+    assert np.max(np.abs(S[:, js] - Sref[:, js])) < TOL[precision]
+    assert np.all(np.isfinite(S))
+    sv.close()
+
+
+def test_device_entry_matches_host_entry():
+    torch = need_gpu()
+    from paper_2604_06309_gb300 import Solver
+    L = 257
+    sv = Solver(MIXED_34, 0.5, L, 1e3, history_cap=100)
+    hist = frozen_case(sv, 3, 100, 500.0)
+    t = hist[0][-1]
+    C, R = hist[1][-1], hist[3][-1]
+    S_host, _ = sv.history_integrals(t, C, R)
+    row = torch.tensor(np.concatenate([C, R]), dtype=torch.float64, device="cuda")
+    S_dev = torch.empty((10, L), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    sv.history_integrals_dev(t, row.data_ptr(), S_dev.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize()
+    assert np.array_equal(S_dev.cpu().numpy(), S_host)
+    sv.close()

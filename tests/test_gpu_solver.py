@@ -1,0 +1,204 @@
+"""Parity of the device-driven Dormand-Prince solve (kernels c, d) with the oracle."""
+import os
+
+import numpy as np
+import pytest
+
+from gpu_common import frozen_case, need_gpu
+from oracle import closed_forms as cf
+from oracle import integrals as OI
+from oracle import solver as OS
+from oracle.model import Model
+from paper_2604_06309_gb300.inputs import MIXED_34, PURE_3, geometric_times, synthetic_history
+
+pytestmark = pytest.mark.gpu
+
+
+def _pair(coefs, T, L, t_max_grid, cap, precision="fp64", s=4, **kw):
+    from paper_2604_06309_gb300 import Solver
+    g = Solver(coefs, T, L, t_max_grid, s=s, history_cap=cap, precision=precision, **kw)
+    o = OS.Solver(coefs, T, L=L, grid_t_max=t_max_grid, s=s, history_cap=cap, **kw)
+    return g, o
+
+
+@pytest.mark.parametrize("t", [0.0, 3.7])
+def test_rhs_matches_oracle(t):
+    need_gpu()
+    from paper_2604_06309_gb300 import Solver
+    L = 65
+    sv = Solver(MIXED_34, 0.5, L, 100.0, history_cap=40)
+    if t > 0:
+        hist = frozen_case(sv, 8, 40, 3.5)
+        H = OI.History(*hist)
+    else:
+        H = None
+    from paper_2604_06309_gb300.inputs import SyntheticFields
+    C, _, R, _ = SyntheticFields(4).rows(t, sv.theta, sv.omega)
+    dC, dR, mu, E = sv.rhs(t, C, R)
+    rC, rR, rmu, rE = OI.rhs(Model(MIXED_34, 0.5), OI.Grid(L, 100.0), H, t, C, R)
+    assert max(np.max(np.abs(dC - rC)), np.max(np.abs(dR - rR))) < 1e-11
+    assert abs(mu - rmu) < 1e-13 and abs(E - rE) < 1e-13
+    sv.close()
+
+
+def _compare_runs(g, o, tol_rows=1e-9):
+    tg, Cg, dCg, Rg, dRg = g.get_history()
+    assert len(tg) == o.hist.N
+    assert np.array_equal(tg, o.hist.t)          # identical step decisions => identical times
+    for a, b in ((Cg, o.hist.C), (dCg, o.hist.dC), (Rg, o.hist.R), (dRg, o.hist.dR)):
+        assert np.max(np.abs(a - b)) < tol_rows
+    st = g.stats()
+    assert st["steps_accepted"] == o.stats["steps_accepted"]
+    assert st["steps_rejected"] == o.stats["steps_rejected"]
+    assert st["sparsify_passes"] == o.stats["sparsify_passes"]
+    assert st["slices_removed"] == o.stats["slices_removed"]
+    assert st["forced_removals"] == o.stats["forced_removals"]
+
+
+def test_integrate_fp64_matches_oracle_step_by_step():
+    need_gpu()
+    g, o = _pair(PURE_3, 0.8, 33, 100.0, cap=400)
+    assert g.integrate(1.0, 1e-8) == 0
+    assert o.integrate(1.0, 1e-8) == 0
+    _compare_runs(g, o)
+    t, C, R, mu, E = g.get_row()
+    assert t == 1.0 and abs(E - o.E) < 1e-10 and abs(mu - o.mu) < 1e-10
+    g.close()
+
+
+def test_integrate_with_sparsification_and_rejections_matches_oracle():
+    need_gpu()
+    # a large first step forces rejections; a small store forces sparsification passes
+    g, o = _pair(MIXED_34, 0.5, 33, 100.0, cap=24, dt0=0.3)
+    assert g.integrate(2.0, 1e-8) == 0
+    assert o.integrate(2.0, 1e-8) == 0
+    assert o.stats["steps_rejected"] >= 1 and o.stats["sparsify_passes"] >= 1
+    _compare_runs(g, o)
+    g.close()
+
+
+def test_integrate_fp32_compensated_within_1e6():
+    need_gpu()
+    g, o = _pair(MIXED_34, 0.5, 65, 100.0, cap=128, precision="fp32")
+    assert g.integrate(3.0, 1e-8) == 0
+    assert o.integrate(3.0, 1e-8) == 0
+    t = np.array([3.0, 3.0, 3.0, 2.1, 1.0])
+    tp = np.array([2.9, 1.5, 0.0, 0.7, 0.5])
+    assert np.max(np.abs(g.get_C(t, tp) - o.get_C(t, tp))) < 1e-6
+    assert np.max(np.abs(g.get_R(t, tp) - o.get_R(t, tp))) < 1e-6
+    _, _, _, _, E = g.get_row()
+    assert abs(E - o.E) < 1e-6
+    g.close()
+
+
+def test_p2_energy_against_closed_form():
+    need_gpu()
+    from paper_2604_06309_gb300 import Solver
+    g = Solver({2: 0.5}, 0.0, 65, 100.0, s=6, history_cap=4000)
+    assert g.integrate(5.0, 1e-10) == 0
+    _, _, _, _, E = g.get_row()
+    assert abs(E - cf.p2_E(5.0)) < 1e-7
+    t = np.array([5.0, 5.0, 3.3])
+    tp = np.array([4.9, 0.0, 1.1])
+    assert np.max(np.abs(g.get_C(t, tp) - cf.p2_C(t, tp))) < 3e-6
+    # invariants: C(t,t) = 1, R(t,t^-) = 1, causality, C(t,0) = R(t,0)
+    ts = np.array([0.5, 1.7, 5.0])
+    assert np.max(np.abs(g.get_C(ts, ts) - 1)) < 1e-14
+    assert np.max(np.abs(g.get_R(ts, ts) - 1)) < 1e-14
+    assert np.all(g.get_R(np.array([1.0]), np.array([1.5])) == 0)
+    assert np.max(np.abs(g.get_C(ts, 0 * ts) - g.get_R(ts, 0 * ts))) < 1e-10
+    g.close()
+
+
+def test_two_time_lookup_matches_oracle():
+    need_gpu()
+    from paper_2604_06309_gb300 import Solver
+    L = 129
+    g = Solver(MIXED_34, 0.5, L, 1e3, s=6, history_cap=80)
+    hist = frozen_case(g, 21, 80, 400.0)
+    G = OI.Grid(L, 1e3, 6)
+    H = OI.History(*hist)
+    rng = np.random.default_rng(1)
+    t = rng.uniform(0, 400.0, 300)
+    tp = rng.uniform(0, 400.0, 300)
+    t[:3] = [400.0, 0.0, 250.0]
+    tp[:3] = [400.0, 0.0, 0.0]
+    assert np.max(np.abs(g.get_C(t, tp) - OS.get_two_time(G, H, t, tp, "C"))) < 1e-12
+    assert np.max(np.abs(g.get_R(t, tp) - OS.get_two_time(G, H, t, tp, "R"))) < 1e-12
+    g.close()
+
+
+def test_sparsify_decisions_are_identical():
+    need_gpu()
+    from paper_2604_06309_gb300 import Solver
+    L = 65
+    g = Solver(MIXED_34, 0.5, L, 1e3, history_cap=300)
+    times = np.concatenate([[0.0], np.geomspace(1e-2, 50.0, 120), np.linspace(50.5, 60.0, 179)])
+    C, dC, R, dR = synthetic_history(31, times, g.theta, g.omega)
+    g.set_history(times, C, dC, R, dR)
+    H = OI.History(times, C, dC, R, dR)
+    tol = 1e-8
+    eps = OS.sparsify_residuals(H)
+    cand = eps[1:H.N - 11]
+    # keep the comparison meaningful: no residual sits within rounding of the threshold
+    assert np.min(np.abs(cand - tol / 10) / (tol / 10)) > 1e-9
+    removed = g.sparsify(tol)
+    H2, ran = OS.sparsify_pass(H, tol)
+    assert ran
+    expect = ~np.isin(H.t, H2.t)
+    assert np.array_equal(removed, expect)
+    assert 0 < removed.sum() < H.N
+    tg = g.get_history()[0]
+    assert np.array_equal(tg, H2.t)
+    g.close()
+
+
+def test_checkpoint_restore_continues_bit_identically(tmp_path):
+    need_gpu()
+    from paper_2604_06309_gb300 import Solver
+    a = Solver(MIXED_34, 0.5, 33, 100.0, history_cap=24)
+    b = Solver(MIXED_34, 0.5, 33, 100.0, history_cap=24)
+    assert a.integrate(1.0, 1e-8) == 0
+    path = str(tmp_path / "ck.bin")
+    a.checkpoint(path)
+    a.close()
+    r = Solver.restore(path)
+    assert r.integrate(2.0, 1e-8) == 0
+    assert b.integrate(2.0, 1e-8) == 0
+    for x, y in zip(r.get_history(), b.get_history()):
+        assert np.array_equal(x, y)
+    sr, sb = r.stats(), b.stats()
+    for k in ("steps_accepted", "steps_rejected", "sparsify_passes", "slices_removed", "dt"):
+        assert sr[k] == sb[k]
+    r.close()
+    b.close()
+
+
+def test_failure_statuses_from_the_device():
+    need_gpu()
+    from paper_2604_06309_gb300 import Solver, dmfe
+    # step underflow: dt_min above what the tolerance allows (App. B)
+    g = Solver(PURE_3, 0.8, 33, 10.0, dt0=0.5, dt_min=0.3, history_cap=64)
+    assert g.integrate(1.0, 1e-12) == dmfe.DMFE_ERR_STEP_UNDERFLOW
+    assert g.stats()["status"] == dmfe.DMFE_ERR_STEP_UNDERFLOW
+    g.get_row()  # the last accepted slice stays readable
+    g.close()
+    # NaN injected into a host-staged history row -> non-finite error estimate
+    g = Solver(PURE_3, 0.8, 33, 10.0, history_cap=64)
+    times = geometric_times(10, 1e-3, 0.1)
+    C, dC, R, dR = synthetic_history(2, times, g.theta, g.omega)
+    C[-1, 5] = np.nan
+    g.set_history(times, C, dC, R, dR)
+    assert g.integrate(0.5, 1e-8) == dmfe.DMFE_ERR_NONFINITE
+    g.close()
+    # full store with sparsification off
+    g = Solver(PURE_3, 0.8, 33, 10.0, history_cap=16, sparsify=False)
+    assert g.integrate(1.0, 1e-8) == dmfe.DMFE_ERR_CAPACITY
+    assert g.stats()["n_slices"] == 16
+    g.close()
+    # argument errors are reported before any device work
+    g = Solver(PURE_3, 0.8, 33, 10.0, history_cap=16)
+    assert g.integrate(20.0, 1e-8) == dmfe.DMFE_ERR_ARG
+    with pytest.raises(dmfe.DMFEError):
+        g.get_C([5.0], [1.0])
+    g.close()
