@@ -159,6 +159,7 @@ def test_checkpoint_restore_continues_bit_identically(tmp_path):
     a = Solver(MIXED_34, 0.5, 33, 100.0, history_cap=24)
     b = Solver(MIXED_34, 0.5, 33, 100.0, history_cap=24)
     assert a.integrate(1.0, 1e-8) == 0
+    assert b.integrate(1.0, 1e-8) == 0   # same stop (the last step is shortened to land on t = 1)
     path = str(tmp_path / "ck.bin")
     a.checkpoint(path)
     a.close()
