@@ -178,6 +178,31 @@ int dmfe_restore(const char* path, void* stream, dmfe_solver** out);
 /* Synchronise the solver's stream and return the device status word. */
 int dmfe_sync(dmfe_solver* h);
 
+/* ---- allocation-free entry point -------------------------------------------------
+ * The paper has no counterpart: this serves callers of the library that cannot call
+ * cudaMalloc -- processes whose device memory another framework has reserved up front,
+ * and latency-critical loops that cannot afford the synchronisation an allocation may
+ * imply. Such callers have no dmfe_solver (creating one allocates).
+ *
+ * Computes the same decision as dmfe_sparsify (greedy remove-n-skip-n+1 with tolerance
+ * tol, forced removal of the smallest residual when none qualifies) for a history held
+ * by the caller in device memory: t_dev [n] slice times (t[0] = 0, increasing) and
+ * C_dev, dC_dev, R_dev, dR_dev row-major [n][L]. removed_dev [n] (device) receives 1 for
+ * each slice to remove, else 0. Stream-ordered on `stream` (NULL: the legacy default
+ * stream); it does not synchronise. Nothing is allocated: the residuals go to one
+ * fixed device array of DMFE_NOALLOC_MAX_SLICES doubles that every GPU loading the
+ * library holds until exit. The first call on each device looks up that array's device
+ * address (with the device current); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (every value a call
+ * reads is written earlier in the same call), so calls that overlap on the GPU -- on
+ * different streams, or from different host threads -- race and must be serialised.
+ * Returns DMFE_ERR_ARG for NULL pointers, n < 1, L < 1, tol <= 0 or
+ * n > DMFE_NOALLOC_MAX_SLICES, DMFE_ERR_CUDA if a launch fails. */
+#define DMFE_NOALLOC_MAX_SLICES 16384
+int dmfe_sparsify_select_noalloc(const double* t_dev, const double* C_dev, const double* dC_dev,
+                                 const double* R_dev, const double* dR_dev, int n, int L,
+                                 double tol, int* removed_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,123 @@
+// dmfe_sparsify_select_noalloc: the sparsification decision of dmfe_sparsify for a
+// history that the caller already holds in device memory, computed without allocating
+// anything.
+//
+// Who needs it: code that cannot call cudaMalloc -- a process in which another
+// framework has reserved the device memory up front (an extra cudaMalloc would fail or
+// fragment its pool), or a latency-critical loop that cannot afford the device-wide
+// synchronisation cudaMalloc and cudaFree may imply. Such a caller has no dmfe_solver
+// (creating one allocates), so this entry point takes the history arrays directly.
+//
+// The per-slice residuals need scratch memory beyond the inputs and outputs. It lives in
+// one file-scope device array of fixed size, g_sp_scratch, which every GPU that loads
+// this library holds until the process exits. Host code cannot use the array's name as
+// a device address; the first call on each device looks the address up with
+// cudaGetSymbolAddress (with that device current) and caches it.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "dmfe_internal.h"
+
+namespace {
+
+static __device__ __align__(256) double g_sp_scratch[DMFE_NOALLOC_MAX_SLICES];
+
+constexpr int kMaxDevices = 64;
+double* g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mutex;
+
+// Device address of g_sp_scratch on the current device (looked up once per device).
+int scratch_address(double** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DMFE_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return DMFE_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_sp_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return DMFE_ERR_CUDA;
+        }
+        g_scratch_addr[dev] = static_cast<double*>(p);
+    }
+    *out = g_scratch_addr[dev];
+    return DMFE_OK;
+}
+
+__device__ __forceinline__ double herm_int_na(double y0, double d0, double y1, double d1, double h) {
+    return 0.5 * h * (y0 + y1) + h * h * (d0 - d1) / 12.0;
+}
+
+// eps_sparse(k) for candidates k = 1 .. n-12 (Sec. 3.6), one warp per candidate; the
+// same per-lane order and warp butterfly as the solver's residual kernel.
+__global__ void k_na_residual(const double* __restrict__ t, const double* __restrict__ C,
+                              const double* __restrict__ dC, const double* __restrict__ R,
+                              const double* __restrict__ dR, int n, int L, double* __restrict__ eps) {
+    const int last = n - 12;
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int k = 1 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k <= last; k += nw) {
+        const double h1 = t[k] - t[k - 1], h2 = t[k + 1] - t[k];
+        const size_t a = (size_t)(k - 1) * L, b = (size_t)k * L, c = (size_t)(k + 1) * L;
+        double acc = 0.0;
+        for (int i = lane; i < L; i += 32) {
+            const double wC = herm_int_na(C[a + i], dC[a + i], C[b + i], dC[b + i], h1) +
+                              herm_int_na(C[b + i], dC[b + i], C[c + i], dC[c + i], h2);
+            const double oC = herm_int_na(C[a + i], dC[a + i], C[c + i], dC[c + i], h1 + h2);
+            const double wR = herm_int_na(R[a + i], dR[a + i], R[b + i], dR[b + i], h1) +
+                              herm_int_na(R[b + i], dR[b + i], R[c + i], dR[c + i], h2);
+            const double oR = herm_int_na(R[a + i], dR[a + i], R[c + i], dR[c + i], h1 + h2);
+            acc += fabs(wC - oC) + fabs(wR - oR);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) eps[k] = acc;
+    }
+}
+
+// Greedy selection: remove k if eps(k) < tol/10 and skip k+1; if nothing qualifies,
+// remove the candidate with the smallest residual. Writes removed[0..n).
+__global__ void k_na_select(const double* __restrict__ eps, int n, double tol, int* __restrict__ removed) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int k = 0; k < n; ++k) removed[k] = 0;
+    const int last = n - 12;
+    if (last < 1) return;
+    int count = 0;
+    for (int k = 1; k <= last;) {
+        if (eps[k] < tol / 10.0) {
+            removed[k] = 1;
+            ++count;
+            k += 2;
+        } else {
+            ++k;
+        }
+    }
+    if (count == 0) {
+        int m = 1;
+        for (int k = 2; k <= last; ++k)
+            if (eps[k] < eps[m]) m = k;
+        removed[m] = 1;
+    }
+}
+
+}  // namespace
+
+extern "C" int dmfe_sparsify_select_noalloc(const double* t_dev, const double* C_dev, const double* dC_dev,
+                                            const double* R_dev, const double* dR_dev, int n, int L, double tol,
+                                            int* removed_dev, void* stream) {
+    if (!t_dev || !C_dev || !dC_dev || !R_dev || !dR_dev || !removed_dev) return DMFE_ERR_ARG;
+    if (n < 1 || L < 1 || !(tol > 0.0)) return DMFE_ERR_ARG;
+    if (n > DMFE_NOALLOC_MAX_SLICES) return DMFE_ERR_ARG;  // beyond the fixed scratch array
+    double* eps = nullptr;
+    int rc = scratch_address(&eps);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int warps_per_cta = 8;
+    int ctas = (n + warps_per_cta - 1) / warps_per_cta;
+    ctas = ctas < 1 ? 1 : (ctas > 2048 ? 2048 : ctas);
+    k_na_residual<<<ctas, 32 * warps_per_cta, 0, s>>>(t_dev, C_dev, dC_dev, R_dev, dR_dev, n, L, eps);
+    k_na_select<<<1, 32, 0, s>>>(eps, n, tol, removed_dev);
+    if (cudaGetLastError() != cudaSuccess) return DMFE_ERR_CUDA;
+    return DMFE_OK;
+}

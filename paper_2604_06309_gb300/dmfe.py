@@ -73,6 +73,7 @@ _SIGS = {
     "dmfe_checkpoint": (_i, [_p, ctypes.c_char_p]),
     "dmfe_restore": (_i, [ctypes.c_char_p, _p, ctypes.POINTER(_p)]),
     "dmfe_sync": (_i, [_p]),
+    "dmfe_sparsify_select_noalloc": (_i, [_p, _p, _p, _p, _p, _i, _i, _d, _p, _p]),
 }
 
 _lib = None
