@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "df"])
     ap.add_argument("--L", type=int, default=2049)
     ap.add_argument("--kernel-only", action="store_true",
                     help="only launch the history-integral kernel (for profiler captures)")
@@ -155,6 +155,7 @@ def _run_ours(args, rank, world, dev, stream):
             raise RuntimeError("device status %d while preparing the state" % st0["status"])
         if st0["sparsify_passes"] > 0 or setup_steps >= 40000:
             break
+    chunk = sv.autotune()  # work-unit size of the history-integral kernel, on this state
     t_state, Crow, Rrow, _, _ = sv.get_row()
     row = torch.tensor(np.concatenate([Crow, Rrow]), dtype=torch.float64, device="cuda")
     n_state = st0["n_slices"]
@@ -209,12 +210,13 @@ def _run_ours(args, rank, world, dev, stream):
 
     pairs = L * L
     n0 = n_state
-    bytes_hist = 4 * n0 * L * (8 if args.precision == "fp64" else 4)
-    bytes_tab = 3 * pairs * (8 if args.precision == "fp64" else 4)
+    wide = args.precision in ("fp64", "df")  # FP64 master or double-float replica: 8 B per value
+    bytes_hist = 4 * n0 * L * (8 if wide else 4)
+    bytes_tab = 3 * pairs * (8 if wide else 4)
     bytes_io = 2 * L * 8 + 10 * L * 8
     res = dict(dev_time=dev_time, e2e_time=e2e_time, k_avg=k_avg, clocks=clk, stats=st, stats_after=st2,
                bytes=(bytes_hist, bytes_tab, bytes_io), pairs=pairs, n0=n0, t_state=t_state,
-               setup_steps=setup_steps)
+               setup_steps=setup_steps, chunk=chunk)
     sv.close()
     return res
 
@@ -294,11 +296,12 @@ def main():
     bh, bt, bio = res["bytes"]
     k = res["k_avg"]
     L = args.L
-    if args.precision == "fp64":
+    if args.precision in ("fp64", "df"):
         flops = res["pairs"] * FLOP_PER_PAIR_S4
         fp64_peak = 1250.0  # GFLOP/s, nominal GB300 FP64 (derived peak)
-        roof = {"kernel": "k_hi_f64 (history integrals)", "bound": "alu", "achieved": flops / k / 1e9,
-                "peak": fp64_peak, "unit": "GFLOP/s", "frac": flops / k / 1e9 / fp64_peak, "traffic": None,
+        roof = {"kernel": "k_hi_%s (history integrals)" % ("f64" if args.precision == "fp64" else "df"),
+                "bound": "alu", "achieved": flops / k / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
+                "frac": flops / k / 1e9 / fp64_peak, "traffic": None,
                 "peak_source": "nominal FP64 1.25 TFLOP/s", "algorithmic_bytes": bh + bt + bio,
                 "hbm_frac_of_%s" % src: (bh + bt + bio) / k / 1e9 / hbm, "kernel_ms": k * 1e3}
     else:
@@ -308,7 +311,7 @@ def main():
                 "algorithmic_bytes": bh + bt + bio, "history_bytes": bh, "table_bytes": bt, "kernel_ms": k * 1e3}
     line = {"metric": "RK steps/s", "value": value, "unit": "RK steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dev_time / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32+f64", "df": "f32x2 (double-float)+f64"}[args.precision],
             "data": "synthetic", "config": cfg,
             "e2e": {"value": world * args.steps / e2e_time, "unit": "RK steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 2 * L * 8 + 3 * 8},
@@ -317,7 +320,7 @@ def main():
             "solver": dict({k2: res["stats"][k2] for k2 in ("t", "steps_accepted", "steps_rejected",
                                                              "sparsify_passes", "slices_removed", "forced_removals",
                                                              "n_slices", "dt", "last_eps")},
-                           state_prepared_by_steps=res["setup_steps"])}
+                           state_prepared_by_steps=res["setup_steps"], autotuned_unit=res["chunk"])}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(L)
     print(json.dumps(line))

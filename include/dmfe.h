@@ -45,6 +45,11 @@ extern "C" {
                                      times, theta, mu, the RK error, step control and
                                      the sparsification test stay FP64                 */
 
+#define DMFE_DOUBLE_FLOAT      2  /* interpolation and sums in double-float arithmetic (pairs of
+                                     FP32 numbers, 48-bit significand, ~1e-13 relative) on the
+                                     FP32 pipes over a double-float history replica; FP64 for
+                                     everything else. FP64-class results at FP32-pipe speed */
+
 #define DMFE_NS 10   /* rows of the history-integral output S, see dmfe_history_integrals */
 #define DMFE_MAX_TERMS 16
 #define DMFE_MAX_POWER 24
@@ -64,7 +69,7 @@ typedef struct {
     double        alpha, delta; /* trade-off parameters of Eq. (theta) (default 0, 0)      */
     int           history_cap;  /* stored slices, >= 16 (default L)                        */
     double        dt0, dt_min;  /* initial and minimal step (defaults 1e-4, 1e-12)         */
-    int           precision;    /* DMFE_FP64 or DMFE_FP32_COMPENSATED                      */
+    int           precision;    /* DMFE_FP64, DMFE_FP32_COMPENSATED or DMFE_DOUBLE_FLOAT   */
     int           sparsify;     /* 1: sparsification pass whenever the store is full (default);
                                    0: off (a full store ends the run with DMFE_ERR_CAPACITY) */
     void*         stream;       /* cudaStream_t for all work; NULL: the solver's own stream */
@@ -174,6 +179,13 @@ int dmfe_stats(dmfe_solver* h, dmfe_stats_t* out);
  * a restored solver continues bit-identically. stream as in dmfe_params. */
 int dmfe_checkpoint(dmfe_solver* h, const char* path);
 int dmfe_restore(const char* path, void* stream, dmfe_solver** out);
+
+/* Autotune the work-unit size of the history-integral kernel (summation indices per
+ * unit: the candidates 256, 512, 1024, 2048, 4096 and L) by timing the kernel on the
+ * solver's current history and stage row, and keep the fastest. Results are cached per
+ * (L, history_cap, s, precision) for the process. Changes the summation order of the
+ * sums S (rounding-level differences only). *chunk (may be NULL) receives the choice. */
+int dmfe_autotune(dmfe_solver* h, int* chunk);
 
 /* Synchronise the solver's stream and return the device status word. */
 int dmfe_sync(dmfe_solver* h);

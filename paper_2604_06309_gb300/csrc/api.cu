@@ -6,7 +6,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "dmfe_internal.h"
@@ -75,7 +79,18 @@ void build_poly(const std::vector<int>& pw, const std::vector<double>& cf, Poly&
     for (int m = 0; m < DMFE_MAX_POWER; ++m) {
         P.f1[m] = (float)P.a1[m];
         P.f2[m] = (float)P.a2[m];
+        P.g1[m] = (float)(P.a1[m] - (double)P.f1[m]);
+        P.g2[m] = (float)(P.a2[m] - (double)P.f2[m]);
     }
+}
+
+// Work-unit size of the history-integral kernels (summation indices per unit).
+constexpr int kMinChunk = 256;
+int default_chunk(int precision, int L) {
+    // measured on GB300 at L = 2049 and 4097: the FP32-pipe kernels run best with one
+    // unit per output index; the FP64 kernel with 1024-index units up to L ~ 3000
+    if (precision == DMFE_FP64 && L < 3072) return 1024;
+    return L;
 }
 
 int validate(const dmfe_params* p) {
@@ -91,7 +106,8 @@ int validate(const dmfe_params* p) {
     if (!(p->alpha >= 0.0 && p->alpha <= 1.0) || !(p->delta >= 0.0)) return DMFE_ERR_ARG;
     if (p->history_cap < 16) return DMFE_ERR_ARG;
     if (!(p->dt0 > 0.0) || !(p->dt_min > 0.0)) return DMFE_ERR_ARG;
-    if (p->precision != DMFE_FP64 && p->precision != DMFE_FP32_COMPENSATED) return DMFE_ERR_ARG;
+    if (p->precision != DMFE_FP64 && p->precision != DMFE_FP32_COMPENSATED && p->precision != DMFE_DOUBLE_FLOAT)
+        return DMFE_ERR_ARG;
     if (p->s != 4 && p->s != 6 && p->s != 8 && p->s != 10) return DMFE_ERR_UNSUPPORTED;
     return DMFE_OK;
 }
@@ -140,16 +156,28 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
         TRY(dev_alloc(h, &p, LL * sizeof(double))); v.x1 = (double*)p;
         TRY(dev_alloc(h, &p, LL * sizeof(double))); v.x2 = (double*)p;
         TRY(dev_alloc(h, &p, LL * sizeof(double))); v.x3 = (double*)p;
-    } else {
+    } else if (v.precision == DMFE_FP32_COMPENSATED) {
         TRY(dev_alloc(h, &p, LL * sizeof(uint32_t))); v.p1 = (uint32_t*)p;
         TRY(dev_alloc(h, &p, LL * sizeof(uint32_t))); v.p2 = (uint32_t*)p;
         TRY(dev_alloc(h, &p, LL * sizeof(uint32_t))); v.p3 = (uint32_t*)p;
+    } else {
+        TRY(dev_alloc(h, &p, LL * sizeof(df))); v.q1 = (df*)p;
+        TRY(dev_alloc(h, &p, LL * sizeof(df))); v.q2 = (df*)p;
+        TRY(dev_alloc(h, &p, LL * sizeof(df))); v.q3 = (df*)p;
+        TRY(dev_alloc(h, &p, L * sizeof(df))); v.omega_df = (df*)p;
+        TRY(dev_alloc(h, &p, L * sizeof(df))); v.nu_df = (df*)p;
+        TRY(dev_alloc(h, &p, L * sizeof(dfrow))); v.rowdf = (dfrow*)p;
+        TRY(dev_alloc(h, &p, cap * sizeof(dfslice))); v.slicedf = (dfslice*)p;
+        TRY(dev_alloc(h, &p, L * sizeof(int))); v.cell = (int*)p;
     }
     for (int b = 0; b < 2; ++b) {
         TRY(dev_alloc(h, &p, cap * sizeof(double))); v.ht[b] = (double*)p;
         TRY(dev_alloc(h, &p, (size_t)cap * L * sizeof(dbl4))); v.hist[b] = (dbl4*)p;
-        if (v.precision != DMFE_FP64) {
+        if (v.precision == DMFE_FP32_COMPENSATED) {
             TRY(dev_alloc(h, &p, (size_t)cap * L * sizeof(float4))); v.hist32[b] = (float4*)p;
+        }
+        if (v.precision == DMFE_DOUBLE_FLOAT) {
+            TRY(dev_alloc(h, &p, (size_t)cap * L * sizeof(df8))); v.histdf[b] = (df8*)p;
         }
     }
     TRY(dev_alloc(h, &p, sizeof(DevState))); v.st = (DevState*)p;
@@ -157,6 +185,19 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
     TRY(dev_alloc(h, &p, 7 * 2 * (size_t)L * sizeof(double))); v.k = (double*)p;
     TRY(dev_alloc(h, &p, 2 * L * sizeof(double))); v.ynew = (double*)p;
     TRY(dev_alloc(h, &p, (size_t)DMFE_NS * L * sizeof(double))); v.S = (double*)p;
+    // Partial sums for units of at least kMinChunk summation indices (the smallest chunk
+    // the autotuner or an override may select).
+    TRY(dev_alloc(h, &p, (size_t)(L / kMinChunk > 1 ? L / kMinChunk : 1) * 9 * L * sizeof(double)));
+    v.Spart = (double*)p;
+    TRY(dev_alloc(h, &p, (size_t)L * sizeof(B1Desc))); v.b1 = (B1Desc*)p;
+    if (!v.cell) { TRY(dev_alloc(h, &p, L * sizeof(int))); v.cell = (int*)p; }
+    TRY(dev_alloc(h, &p, (size_t)L * sizeof(int))); v.jcount = (int*)p;
+    DMFE_CUDA_TRY(cudaMemsetAsync(v.jcount, 0, (size_t)L * sizeof(int), h->stream));
+    v.hi_chunk = default_chunk(v.precision, L);
+    if (const char* e = std::getenv("DMFE_HI_CHUNK")) {
+        const int c = std::atoi(e);
+        if (c >= kMinChunk && c % 32 == 0) v.hi_chunk = c;
+    }
     TRY(dev_alloc(h, &p, cap * sizeof(double))); v.eps_sp = (double*)p;
     TRY(dev_alloc(h, &p, cap * sizeof(int))); v.keep = (int*)p;
     TRY(dev_alloc(h, &p, cap * sizeof(int))); v.newidx = (int*)p;
@@ -172,6 +213,15 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
     DMFE_CUDA_TRY(cudaMemcpyAsync((void*)v.nu, h->nu.data(), L * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     DMFE_CUDA_TRY(cudaMemcpyAsync((void*)v.omega32, om32.data(), L * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     DMFE_CUDA_TRY(cudaMemcpyAsync((void*)v.nu32, nu32.data(), L * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    std::vector<df> omdf(L), nudf(L);
+    if (v.precision == DMFE_DOUBLE_FLOAT) {
+        for (int i = 0; i < L; ++i) {
+            omdf[i] = df_from_d(h->omega[i]);
+            nudf[i] = df_from_d(h->nu[i]);
+        }
+        DMFE_CUDA_TRY(cudaMemcpyAsync((void*)v.omega_df, omdf.data(), L * sizeof(df), cudaMemcpyHostToDevice, h->stream));
+        DMFE_CUDA_TRY(cudaMemcpyAsync((void*)v.nu_df, nudf.data(), L * sizeof(df), cudaMemcpyHostToDevice, h->stream));
+    }
     std::memset(h->hstate, 0, sizeof(DevState));
     h->hstate->dt = pin->dt0;
     h->hstate->dt_min = pin->dt_min;
@@ -301,6 +351,15 @@ int dmfe_tables(dmfe_solver* h, double* x1, double* x2, double* x3) {
         for (int q = 0; q < 3; ++q)
             if (outs[q]) DMFE_CUDA_TRY(cudaMemcpyAsync(outs[q], src[q], LL * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    } else if (v.precision == DMFE_DOUBLE_FLOAT) {
+        const df* src[3] = {v.q1, v.q2, v.q3};
+        std::vector<df> tmp(LL);
+        for (int q = 0; q < 3; ++q) {
+            if (!outs[q]) continue;
+            DMFE_CUDA_TRY(cudaMemcpyAsync(tmp.data(), src[q], LL * sizeof(df), cudaMemcpyDeviceToHost, h->stream));
+            DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+            for (size_t k = 0; k < LL; ++k) outs[q][k] = (double)tmp[k].hi + (double)tmp[k].lo;
+        }
     } else {
         const uint32_t* src[3] = {v.p1, v.p2, v.p3};
         std::vector<uint32_t> tmp(LL);
@@ -554,6 +613,88 @@ int dmfe_stats(dmfe_solver* h, dmfe_stats_t* o) {
     o->history_cap = h->v.cap;
     o->s = h->v.s;
     o->precision = h->v.precision;
+    return DMFE_OK;
+}
+
+static std::mutex g_tune_mutex;
+static std::map<std::tuple<int, int, int, int>, int> g_tune_cache;
+
+int dmfe_autotune(dmfe_solver* h, int* chunk_out) {
+    if (!h) return DMFE_ERR_ARG;
+    SolverView& v = h->v;
+    const auto key = std::make_tuple(v.L, v.cap, v.s, v.precision);
+    int best = -1;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) best = it->second;
+    }
+    if (best < 0) {
+        TRY(read_state(h));
+        const int L = v.L;
+        const DevState& s = *h->hstate;
+        // stage row = the last stored slice
+        std::vector<dbl4> row(L);
+        DMFE_CUDA_TRY(cudaMemcpyAsync(row.data(), v.hist[s.active] + (size_t)(s.n - 1) * L, L * sizeof(dbl4),
+                                      cudaMemcpyDeviceToHost, h->stream));
+        DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        std::vector<double> CR(2 * L);
+        for (int i = 0; i < L; ++i) {
+            CR[i] = row[i].x;
+            CR[L + i] = row[i].z;
+        }
+        double* d = h->scratch;
+        DMFE_CUDA_TRY(cudaMemcpyAsync(d, CR.data(), 2 * L * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        std::vector<int> cands;
+        for (int c : {kMinChunk, 512, 1024, 2048, 4096, L}) {
+            const int cc = c >= L ? L : c;
+            if (cc >= kMinChunk || cc == L)
+                if (std::find(cands.begin(), cands.end(), cc) == cands.end()) cands.push_back(cc);
+        }
+        cudaEvent_t e0, e1;
+        DMFE_CUDA_TRY(cudaEventCreate(&e0));
+        DMFE_CUDA_TRY(cudaEventCreate(&e1));
+        float best_ms = 1e30f;
+        const int saved = v.hi_chunk;
+        int rc = DMFE_OK;
+        for (int c : cands) {
+            v.hi_chunk = c;
+            int grid = 0;
+            size_t sm = 0;
+            rc = hi_config(v, &grid, &sm);
+            if (rc) break;
+            float tot = 0.f;
+            for (int it = 0; it < 4 && !rc; ++it) {
+                if (cudaEventRecord(e0, h->stream) != cudaSuccess) rc = DMFE_ERR_CUDA;
+                if (!rc) rc = launch_history_integrals(v, d, s.t, false, v.S, grid, h->stream);
+                if (!rc && cudaEventRecord(e1, h->stream) != cudaSuccess) rc = DMFE_ERR_CUDA;
+                if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = DMFE_ERR_CUDA;
+                float ms = 0.f;
+                if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = DMFE_ERR_CUDA;
+                if (it > 0) tot += ms;  // first launch warms caches
+            }
+            if (rc) break;
+            if (tot < best_ms) {
+                best_ms = tot;
+                best = c;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc) {
+            v.hi_chunk = saved;
+            return rc;
+        }
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = best;
+    }
+    v.hi_chunk = best;
+    TRY(hi_config(v, &h->hi_grid, &h->hi_smem));
+    if (h->step_exec) {  // the captured step holds the old launch configuration
+        cudaGraphExecDestroy(h->step_exec);
+        h->step_exec = nullptr;
+    }
+    if (chunk_out) *chunk_out = best;
     return DMFE_OK;
 }
 

@@ -1,0 +1,74 @@
+// Double-float arithmetic: a value is hi + lo with two FP32 numbers (|lo| <= ulp(hi)/2),
+// a 48-bit significand computed on the FP32 pipes. Error-free transforms after Dekker
+// (1971) and Knuth (TAOCP vol. 2): TwoSum, FastTwoSum, and the FMA form of TwoProduct.
+// The __f*_rn intrinsics keep the compiler from contracting or reassociating them.
+#pragma once
+
+#include <cuda_runtime.h>
+
+struct __align__(8) df {
+    float hi, lo;
+};
+
+// Conversion from FP64 (rounds to the nearest pair).
+__host__ __device__ __forceinline__ df df_from_d(double x) {
+    float h = (float)x;
+    float l = (float)(x - (double)h);
+    return df{h, l};
+}
+
+#if defined(__CUDACC__)
+__device__ __forceinline__ df df_make(float h, float l) { return df{h, l}; }
+
+// a + b = s + e exactly (no precondition on |a|, |b|)
+__device__ __forceinline__ df two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return df{s, e};
+}
+
+// a + b = s + e exactly when |a| >= |b|
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return df{s, e};
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return fast_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+
+__device__ __forceinline__ df df_add_f(df a, float b) {
+    df s = two_sum(a.hi, b);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+    float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return fast_two_sum(p, e);
+}
+
+// a * b + c
+__device__ __forceinline__ df df_fma(df a, df b, df c) { return df_add(df_mul(a, b), c); }
+
+__device__ __forceinline__ bool df_lt(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool df_ge(df a, df b) { return !df_lt(a, b); }
+
+__device__ __forceinline__ double df_to_d(df a) { return (double)a.hi + (double)a.lo; }
+#endif

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "../../include/dmfe.h"
+#include "df64.h"
 
 #define DMFE_CUDA_TRY(call)                                   \
     do {                                                      \
@@ -25,8 +26,33 @@ struct Poly {
     double a0[DMFE_MAX_POWER + 1];       // f(q)   = sum_m a0[m] q^m
     double a1[DMFE_MAX_POWER];           // f'(q)  = sum_m a1[m] q^m
     double a2[DMFE_MAX_POWER];           // f''(q) = sum_m a2[m] q^m
-    float f1[DMFE_MAX_POWER];
+    float f1[DMFE_MAX_POWER];            // FP32 f' (also the hi part of the double-float f')
     float f2[DMFE_MAX_POWER];
+    float g1[DMFE_MAX_POWER];            // lo parts: f' = f1 + g1 as a double-float
+    float g2[DMFE_MAX_POWER];
+};
+
+// Double-float history element and stage-row element (32 bytes each).
+struct __align__(32) df8 {
+    df C, dC, R, dR;
+};
+struct __align__(32) dfrow {
+    df K, D, C, R;
+};
+// B1 time interpolation of output index j for one stage: value at time theta_j t =
+// w0 Y[a0] + w1 dY[a0] + w2 Y[a1] + w3 dY[a1] (a1 < 0: the stage row, w3 = 0).
+struct __align__(16) B1Desc {
+    int a0, a1;
+    double w[4];
+    df wd[4];
+};
+
+// Per-slice constants of one stage for the double-float kernel: complement
+// v_k = (t - t_k)/t, inv_k = t/(t_{k+1} - t_k), h_k = t_{k+1} - t_k.
+struct __align__(8) dfslice {
+    df v, inv;
+    float h;
+    float pad;
 };
 
 template <typename R>
@@ -88,11 +114,24 @@ struct SolverView {
     double* ht[2];        // slice times [cap], two buffers (compaction ping-pong)
     dbl4* hist[2];        // [cap][L] {C, dC, R, dR} FP64 master
     float4* hist32[2];    // [cap][L] FP32 replica (FP32 path)
+    df8* histdf[2];       // [cap][L] double-float replica (double-float path)
+    const df* q1;         // [L*L] double-float fractional index (double-float path)
+    const df* q2;
+    const df* q3;
+    const df* omega_df;   // [L]
+    const df* nu_df;      // [L]
+    dfrow* rowdf;         // [L] stage row prepared for the double-float kernel
+    dfslice* slicedf;     // [cap]
+    int* cell;            // [L] slice of time theta_m t
+    B1Desc* b1;           // [L] per-stage B1 time weights
+    int hi_chunk;         // summation indices per work unit
     DevState* st;
     double* Y;            // [2L] stage row (C then R)
     double* k;            // [7][2L] stage derivatives
     double* ynew;         // [2L] 5th-order solution of the trial step
     double* S;            // [NS][L]
+    double* Spart;        // [parts][9][L] partial sums of the chunks of the i-range
+    int* jcount;          // [L] parts finished per output index (zero between launches)
     double* eps_sp;       // [cap] sparsification residuals
     int* keep;            // [cap]
     int* newidx;          // [cap]
@@ -116,6 +155,12 @@ int launch_sparsify(const SolverView& v, bool from_step, double tol, cudaStream_
 int launch_lookup(const SolverView& v, int n, const double* t, const double* tp, int which,
                   double* out, cudaStream_t s);
 int launch_refresh_replica(const SolverView& v, cudaStream_t s);
+// per-stage preparation for every precision (kernels_df.cu)
+int launch_stage_prep(const SolverView& v, const double* row_dev, double t, bool from_state, cudaStream_t s);
+// double-float path (kernels_df.cu)
+int launch_history_integrals_df(const SolverView& v, const double* row_dev, double t, bool from_state,
+                                double* S_dev, int grid_ctas, cudaStream_t s);
+int hi_config_df(const SolverView& v, int* grid_ctas, size_t* smem);
 
 // ---- host grid (host_grid.cpp) ----
 double host_gamma_from_tmax(double t_max);

@@ -1,0 +1,408 @@
+// History integrals in double-float arithmetic (Secs. 3.3, 3.4, Eq. int).
+//
+// Same quantities, mapping and reduction order as kernels_hi.cu (units of (j, chunk of
+// the i-range), lanes stride over i, fixed butterflies), but every interpolation, product and
+// sum runs in double-float (df64.h): FP64-class accuracy (~1e-13 relative) on the FP32
+// pipes, which on this part issue 64 times the FP64 rate. Inputs are a double-float
+// replica of the history and double-float stencil positions.
+//
+// k_stage_prep does the per-stage FP64 work once, spread over many SMs: the table
+// cell -> slice of time theta_m t, the B1 time weights of every output index, and for
+// this path the stage row {K = f''(C) R, D = f'(C), C, R} and the per-slice
+// complements v_k = (t - t_k)/t with their reciprocal widths.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dmfe_internal.h"
+#include "hi_units.h"
+
+namespace {
+
+constexpr int DF_THREADS = 512;
+constexpr int DF_WARPS = DF_THREADS / 32;
+
+__device__ __forceinline__ int find_slice_g(const double* ht, int n, double tau) {
+    if (n <= 2) return 0;
+    int lo = 0, hi = n - 2;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (ht[mid] <= tau) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Per-stage preparation (all precisions): the cell -> slice table, the B1 time weights of
+// every output index, and for the double-float path the stage row and slice constants.
+__global__ void k_stage_prep(SolverView v, const double* __restrict__ row, double t_arg, int from_state) {
+    const DevState* st = v.st;
+    if (from_state && (st->status != 0 || st->done)) return;
+    const int L = v.L, n = st->n, act = st->active;
+    const double t = from_state ? st->t_stage : t_arg;
+    const double* ht = v.ht[act];
+    const double tl = ht[n - 1];
+    const bool ext = t > tl;
+    const double hx = t - tl;
+    const int tot = L > n ? L : n;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += gridDim.x * blockDim.x) {
+        if (q < L) {
+            const double tau = v.theta[q] * t;
+            const int c = find_slice_g(ht, n, tau);
+            v.cell[q] = c;
+            B1Desc d;
+            if (ext && tau > tl) {
+                const double s = tau - tl, qq = s / hx;
+                d.a0 = n - 1; d.a1 = -1;
+                d.w[0] = 1.0 - qq * qq; d.w[1] = s - s * qq; d.w[2] = qq * qq; d.w[3] = 0.0;
+            } else if (n == 1) {
+                d.a0 = 0; d.a1 = 0;
+                d.w[0] = 1.0; d.w[1] = 0.0; d.w[2] = 0.0; d.w[3] = 0.0;
+            } else {
+                const double hh = ht[c + 1] - ht[c];
+                const double sg = (tau - ht[c]) / hh, om = 1.0 - sg;
+                d.a0 = c; d.a1 = c + 1;
+                d.w[0] = (1.0 + 2.0 * sg) * om * om;
+                d.w[1] = sg * om * om * hh;
+                d.w[2] = sg * sg * (3.0 - 2.0 * sg);
+                d.w[3] = sg * sg * (sg - 1.0) * hh;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) d.wd[k] = df_from_d(d.w[k]);
+            v.b1[q] = d;
+            if (v.rowdf) {
+                const double C = row[q], R = row[L + q];
+                v.rowdf[q] = dfrow{df_from_d(fp2(v.poly, C) * R), df_from_d(fp1(v.poly, C)), df_from_d(C), df_from_d(R)};
+            }
+        }
+        if (q < n && v.slicedf) {
+            const double tk = ht[q];
+            dfslice e;
+            e.v = df_from_d((t - tk) / t);
+            if (q + 1 < n) {
+                const double w = ht[q + 1] - tk;
+                e.inv = df_from_d(t / w);
+                e.h = (float)w;
+            } else {
+                e.inv = df{0.f, 0.f};
+                e.h = 0.f;
+            }
+            e.pad = 0.f;
+            v.slicedf[q] = e;
+        }
+    }
+}
+
+// Lagrange weights on nodes 0..SW-1 at the double-float position u.
+template <int SW>
+__device__ __forceinline__ void lagrange_df(df u, df (&w)[SW]) {
+    df um[SW];
+#pragma unroll
+    for (int k = 0; k < SW; ++k) um[k] = df_add_f(u, -(float)k);
+    df pre[SW], suf[SW];
+    pre[0] = df{1.f, 0.f};
+#pragma unroll
+    for (int k = 1; k < SW; ++k) pre[k] = df_mul(pre[k - 1], um[k - 1]);
+    suf[SW - 1] = df{1.f, 0.f};
+#pragma unroll
+    for (int k = SW - 2; k >= 0; --k) suf[k] = df_mul(suf[k + 1], um[k + 1]);
+#pragma unroll
+    for (int k = 0; k < SW; ++k) {
+        // 1 / prod_{m != k} (k - m) as a double-float constant
+        double c = 1.0;
+#pragma unroll
+        for (int m = 0; m < SW; ++m)
+            if (m != k) c /= (double)(k - m);
+        const float ch = (float)c;
+        const float cl = (float)(c - (double)ch);
+        w[k] = df_mul(df_mul(pre[k], suf[k]), df{ch, cl});
+    }
+}
+
+template <int SW>
+__device__ __forceinline__ int base_of(float xhi, int L) {
+    int b = (int)floorf(xhi) - SW / 2 + 1;
+    b = b < 0 ? 0 : b;
+    return b > L - SW ? L - SW : b;
+}
+
+// Stencil position x (double-float) -> base b and the weights.
+template <int SW>
+__device__ __forceinline__ int stencil_df(df x, int L, df (&w)[SW]) {
+    const int b = base_of<SW>(x.hi, L);
+    // x.hi - b is exact (b is an integer within a few units of x.hi)
+    const df u = fast_two_sum(__fsub_rn(x.hi, (float)b), x.lo);
+    lagrange_df<SW>(u, w);
+    return b;
+}
+
+__device__ __forceinline__ df poly_df(const float* hi, const float* lo, int deg, df q) {
+    df v = df{hi[deg], lo[deg]};
+    for (int m = deg - 1; m >= 0; --m) v = df_fma(v, q, df{hi[m], lo[m]});
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+template <int SW>
+__global__ void __launch_bounds__(DF_THREADS, 1) k_hi_df(SolverView v, double t_arg, int from_state,
+                                                         double* __restrict__ S) {
+    extern __shared__ __align__(32) unsigned char smraw[];
+    const DevState* st = v.st;
+    if (from_state && (st->status != 0 || st->done)) return;
+    const int L = v.L, n = st->n, act = st->active;
+    const double t = from_state ? st->t_stage : t_arg;
+    const df8* __restrict__ H = v.histdf[act];
+    const double* __restrict__ ht = v.ht[act];
+    dfrow* srow = reinterpret_cast<dfrow*>(smraw);                   // [L]
+    df* sv = reinterpret_cast<df*>(srow + L);                         // [cap] v_k
+    df* sinv = sv + v.cap;                                            // [cap] t/(t_{k+1} - t_k)
+    float* sh = reinterpret_cast<float*>(sinv + v.cap);               // [cap] t_{k+1} - t_k
+    uint16_t* scell = reinterpret_cast<uint16_t*>(sh + v.cap);        // [L]
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        srow[i] = v.rowdf[i];
+        scell[i] = (uint16_t)v.cell[i];
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const dfslice e = v.slicedf[i];
+        sv[i] = e.v;
+        sinv[i] = e.inv;
+        sh[i] = e.h;
+    }
+    __syncthreads();
+    const double tl = ht[n - 1];
+    const bool ext = t > tl;
+    const double hx = t - tl;
+    const df vlast = sv[n - 1];
+    const df inv_vlast = df_from_d(ext ? t / hx : 0.0);
+    const df hx_df = df_from_d(hx);
+    const int lane = threadIdx.x & 31;
+    const df* __restrict__ omdf = v.omega_df;
+    const df* __restrict__ nudf = v.nu_df;
+    const float* f1 = v.poly.f1;
+    const float* g1 = v.poly.g1;
+    const float* f2 = v.poly.f2;
+    const float* g2 = v.poly.g2;
+    const int d1 = v.poly.deg1, d2 = v.poly.deg2;
+
+    const int chunk = v.hi_chunk;
+    int ub, ue;
+    hi_unit_block(L, chunk, &ub, &ue);
+    for (int u_ = ub + (threadIdx.x >> 5); u_ < ue; u_ += DF_WARPS) {
+        int j, i0, i1;
+        hi_unit_range(u_, L, chunk, &j, &i0, &i1);
+        // ---- per unit: B1 time weights prepared once per stage
+        const df omj = omdf[j];
+        int a0, a1;
+        df bw0, bw1, bw2, bw3;
+        {
+            const B1Desc d = v.b1[j];
+            a0 = d.a0; a1 = d.a1;
+            bw0 = d.wd[0]; bw1 = d.wd[1]; bw2 = d.wd[2]; bw3 = d.wd[3];
+        }
+        const df* __restrict__ q1r = v.q1 + (size_t)j * L;
+        const df* __restrict__ q2r = v.q2 + (size_t)j * L;
+        const df* __restrict__ q3r = v.q3 + (size_t)j * L;
+        df acc[9];
+#pragma unroll
+        for (int r = 0; r < 9; ++r) acc[r] = df{0.f, 0.f};
+        df c_at_0 = df{0.f, 0.f};
+        for (int i = i0 + lane; i < i1; i += 32) {
+            // ---- B1: on-grid column i at time theta_j t
+            df CB1, RB1;
+            {
+                const df8 h0 = H[(size_t)a0 * L + i];
+                CB1 = df_add(df_mul(bw0, h0.C), df_mul(bw1, h0.dC));
+                RB1 = df_add(df_mul(bw0, h0.R), df_mul(bw1, h0.dR));
+                if (a1 >= 0) {
+                    const df8 h1 = H[(size_t)a1 * L + i];
+                    CB1 = df_add(CB1, df_add(df_mul(bw2, h1.C), df_mul(bw3, h1.dC)));
+                    RB1 = df_add(RB1, df_add(df_mul(bw2, h1.R), df_mul(bw3, h1.dR)));
+                } else {
+                    const dfrow r1 = srow[i];
+                    CB1 = df_add(CB1, df_mul(bw2, r1.C));
+                    RB1 = df_add(RB1, df_mul(bw2, r1.R));
+                }
+            }
+            // ---- A1: current row at phi1
+            df KA1 = {0.f, 0.f}, DA1 = {0.f, 0.f}, CA1 = {0.f, 0.f}, RA1 = {0.f, 0.f};
+            {
+                df w[SW];
+                const int b = stencil_df<SW>(q1r[i], L, w);
+#pragma unroll
+                for (int k = 0; k < SW; ++k) {
+                    const dfrow q = srow[b + k];
+                    KA1 = df_fma(w[k], q.K, KA1);
+                    DA1 = df_fma(w[k], q.D, DA1);
+                    CA1 = df_fma(w[k], q.C, CA1);
+                    RA1 = df_fma(w[k], q.R, RA1);
+                }
+            }
+            // ---- A2: current row at phi2
+            df KA2 = {0.f, 0.f}, RA2 = {0.f, 0.f};
+            const df x2 = q2r[i];
+            {
+                df w[SW];
+                const int b = stencil_df<SW>(x2, L, w);
+#pragma unroll
+                for (int k = 0; k < SW; ++k) {
+                    const dfrow q = srow[b + k];
+                    KA2 = df_fma(w[k], q.K, KA2);
+                    RA2 = df_fma(w[k], q.R, RA2);
+                }
+            }
+            // ---- B2: theta position psi on the slices around phi2 t (complement form)
+            df CB2, RB2;
+            {
+                const df u = df_mul(omj, omdf[i]);  // 1 - phi2 = omega_j omega_i
+                int s0, s1;
+                df tw0, tw1, tw2, tw3;
+                if (ext && df_lt(u, vlast)) {
+                    const df q = df_mul(df_sub(vlast, u), inv_vlast);
+                    const df q2 = df_mul(q, q);
+                    s0 = n - 1; s1 = -1;
+                    tw0 = df_add_f(df_neg(q2), 1.f);
+                    tw1 = df_mul(hx_df, df_sub(q, q2));
+                    tw2 = q2;
+                    tw3 = df{0.f, 0.f};
+                } else if (n == 1) {
+                    s0 = 0; s1 = 0;
+                    tw0 = df{1.f, 0.f}; tw1 = df{0.f, 0.f}; tw2 = df{0.f, 0.f}; tw3 = df{0.f, 0.f};
+                } else {
+                    int k = scell[(int)floorf(x2.hi) < L ? (int)floorf(x2.hi) : L - 1];
+                    while (k < n - 2 && df_ge(sv[k + 1], u)) ++k;
+                    while (k > 0 && df_lt(sv[k], u)) --k;
+                    const df sg = df_mul(df_sub(sv[k], u), sinv[k]);
+                    const float hh = sh[k];
+                    const df om = df_add_f(df_neg(sg), 1.f);
+                    const df om2 = df_mul(om, om), sg2 = df_mul(sg, sg);
+                    s0 = k; s1 = k + 1;
+                    tw0 = df_mul(df_add_f(df_mul_f(sg, 2.f), 1.f), om2);
+                    tw1 = df_mul_f(df_mul(sg, om2), hh);
+                    tw2 = df_mul(sg2, df_add_f(df_mul_f(sg, -2.f), 3.f));
+                    tw3 = df_mul_f(df_mul(sg2, df_add_f(sg, -1.f)), hh);
+                }
+                df w[SW];
+                const int b = stencil_df<SW>(q3r[i], L, w);
+                df c0 = {0.f, 0.f}, dc0 = {0.f, 0.f}, r0 = {0.f, 0.f}, dr0 = {0.f, 0.f};
+                const df8* __restrict__ p0 = H + (size_t)s0 * L + b;
+#pragma unroll
+                for (int k = 0; k < SW; ++k) {
+                    const df8 e = p0[k];
+                    c0 = df_fma(w[k], e.C, c0);
+                    dc0 = df_fma(w[k], e.dC, dc0);
+                    r0 = df_fma(w[k], e.R, r0);
+                    dr0 = df_fma(w[k], e.dR, dr0);
+                }
+                CB2 = df_add(df_mul(tw0, c0), df_mul(tw1, dc0));
+                RB2 = df_add(df_mul(tw0, r0), df_mul(tw1, dr0));
+                df c1 = {0.f, 0.f}, dc1 = {0.f, 0.f}, r1 = {0.f, 0.f}, dr1 = {0.f, 0.f};
+                if (s1 >= 0) {
+                    const df8* __restrict__ p1 = H + (size_t)s1 * L + b;
+#pragma unroll
+                    for (int k = 0; k < SW; ++k) {
+                        const df8 e = p1[k];
+                        c1 = df_fma(w[k], e.C, c1);
+                        dc1 = df_fma(w[k], e.dC, dc1);
+                        r1 = df_fma(w[k], e.R, r1);
+                        dr1 = df_fma(w[k], e.dR, dr1);
+                    }
+                    CB2 = df_add(CB2, df_add(df_mul(tw2, c1), df_mul(tw3, dc1)));
+                    RB2 = df_add(RB2, df_add(df_mul(tw2, r1), df_mul(tw3, dr1)));
+                } else {
+#pragma unroll
+                    for (int k = 0; k < SW; ++k) {
+                        const dfrow e = srow[b + k];
+                        c1 = df_fma(w[k], e.C, c1);
+                        r1 = df_fma(w[k], e.R, r1);
+                    }
+                    CB2 = df_add(CB2, df_mul(tw2, c1));
+                    RB2 = df_add(RB2, df_mul(tw2, r1));
+                }
+            }
+            const df f1a = poly_df(f1, g1, d1, CB1), f2a = poly_df(f2, g2, d2, CB1);
+            const df f1b = poly_df(f1, g1, d1, CB2), f2b = poly_df(f2, g2, d2, CB2);
+            const df nui = nudf[i];
+            const df nRB1 = df_mul(nui, RB1);
+            const df nRA2 = df_mul(nui, RA2);
+            const df nKA2 = df_mul(nui, KA2);
+            acc[0] = df_fma(df_mul(nui, KA1), CB1, acc[0]);
+            acc[1] = df_fma(nKA2, CB2, acc[1]);
+            acc[2] = df_fma(DA1, nRB1, acc[2]);
+            acc[3] = df_fma(nKA2, RB2, acc[3]);
+            acc[4] = df_fma(df_mul(f2a, CA1), nRB1, acc[4]);
+            acc[5] = df_fma(df_mul(nui, f1a), RA1, acc[5]);
+            acc[6] = df_fma(f1b, nRA2, acc[6]);
+            acc[7] = df_fma(df_mul(f2b, RB2), nRA2, acc[7]);
+            acc[8] = df_fma(df_fma(f2a, CB1, f1a), nRB1, acc[8]);
+            if (i == 0) c_at_0 = CB1;
+        }
+        double sums[9];
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+            const df x = df_warp_sum(acc[r]);
+            sums[r] = lane == 0 ? df_to_d(x) : 0.0;
+        }
+        if (lane == 0) hi_finish_unit(sums, df_to_d(c_at_0), u_, L, chunk, v.Spart, v.jcount, S);
+    }
+}
+
+size_t df_smem_bytes(const SolverView& v) {
+    return (size_t)v.L * sizeof(dfrow) + (size_t)v.cap * (2 * sizeof(df) + sizeof(float)) +
+           (size_t)v.L * sizeof(uint16_t) + 16;
+}
+
+void* df_kernel_for(int s) {
+    switch (s) {
+        case 4: return (void*)k_hi_df<4>;
+        case 6: return (void*)k_hi_df<6>;
+        case 8: return (void*)k_hi_df<8>;
+        case 10: return (void*)k_hi_df<10>;
+    }
+    return nullptr;
+}
+
+}  // namespace
+
+int launch_stage_prep(const SolverView& v, const double* row_dev, double t, bool from_state, cudaStream_t s) {
+    const int tot = v.L > v.cap ? v.L : v.cap;
+    k_stage_prep<<<(tot + 127) / 128, 128, 0, s>>>(v, row_dev, t, from_state ? 1 : 0);
+    DMFE_CUDA_TRY(cudaGetLastError());
+    return DMFE_OK;
+}
+
+int hi_config_df(const SolverView& v, int* grid_ctas, size_t* smem) {
+    void* fn = df_kernel_for(v.s);
+    if (!fn) return DMFE_ERR_UNSUPPORTED;
+    if (v.L > 65535) return DMFE_ERR_UNSUPPORTED;
+    const size_t sm = df_smem_bytes(v);
+    int dev = 0, max_optin = 0, nsm = 0;
+    DMFE_CUDA_TRY(cudaGetDevice(&dev));
+    DMFE_CUDA_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    DMFE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (sm > (size_t)max_optin) return DMFE_ERR_UNSUPPORTED;
+    DMFE_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int per_sm = 0;
+    DMFE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, DF_THREADS, sm));
+    if (per_sm < 1) return DMFE_ERR_UNSUPPORTED;
+    const int want = (hi_parts(v.L, v.hi_chunk) * v.L + DF_WARPS - 1) / DF_WARPS;
+    const int cap = nsm * per_sm;
+    *grid_ctas = want < cap ? want : cap;
+    *smem = sm;
+    return DMFE_OK;
+}
+
+int launch_history_integrals_df(const SolverView& v, const double* row_dev, double t, bool from_state,
+                                double* S_dev, int grid_ctas, cudaStream_t s) {
+    void* fn = df_kernel_for(v.s);
+    if (!fn) return DMFE_ERR_UNSUPPORTED;
+    const int fs = from_state ? 1 : 0;
+    int rc = launch_stage_prep(v, row_dev, t, from_state, s);
+    if (rc) return rc;
+    const size_t sm = df_smem_bytes(v);
+    void* args[] = {(void*)&v, (void*)&t, (void*)&fs, (void*)&S_dev};
+    DMFE_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid_ctas), dim3(DF_THREADS), args, sm, s));
+    return DMFE_OK;
+}

@@ -10,10 +10,11 @@
 // and accumulates the nine nu-weighted products S[0..8] of dmfe.h plus S[9] = C(theta_j t, 0).
 // Times in (t_last, t] come from the quadratic through the last slice and the stage row.
 //
-// Mapping: one warp per output index j, lanes stride over i (coalesced table and B1 rows);
-// each lane sums its terms in i order and the warp reduces with a fixed butterfly, so
-// results are deterministic. The slice containing phi2 t is found from a per-stage
-// table cell -> slice (phi2 lies in grid cell floor(x2)) and a short walk.
+// Mapping (hi_units.h): a warp takes a unit (j, chunk of 256 i), lanes stride over
+// i (coalesced table and B1 rows); each lane sums its terms in i order, the warp reduces
+// with a fixed butterfly and the last chunk to finish adds the chunks in a fixed
+// order, so results are deterministic. The slice containing phi2 t is found from a
+// per-stage table cell -> slice (phi2 lies in grid cell floor(x2)) and a short walk.
 //
 // Precision variants:
 //   FP64: every value in FP64, stencil positions from FP64 tables.
@@ -26,10 +27,11 @@
 #include <stdint.h>
 
 #include "dmfe_internal.h"
+#include "hi_units.h"
 
 namespace {
 
-constexpr int HI_THREADS = 256;
+constexpr int HI_THREADS = 512;
 constexpr int HI_WARPS = HI_THREADS / 32;
 
 // Lagrange weights on nodes 0..SW-1 at u: w_k = prod_{m != k} (u - m) / (k - m).
@@ -111,7 +113,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // ------------------------------------------------------------------ FP64 variant
 template <int SW>
-__global__ void __launch_bounds__(HI_THREADS) k_hi_f64(SolverView v, const double* __restrict__ row,
+__global__ void __launch_bounds__(HI_THREADS, 1) k_hi_f64(SolverView v, const double* __restrict__ row,
                                                        double t_arg, int from_state, double* __restrict__ S) {
     extern __shared__ __align__(32) unsigned char smraw[];
     const DevState* st = v.st;
@@ -130,21 +132,29 @@ __global__ void __launch_bounds__(HI_THREADS) k_hi_f64(SolverView v, const doubl
         srow[i] = dbl4{fp2(v.poly, C) * R, fp1(v.poly, C), C, R};
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) sht[i] = ht[i];
-    __syncthreads();
-    for (int m = threadIdx.x; m < L; m += blockDim.x) scell[m] = find_slice(sht, n, v.theta[m] * t);
+    for (int m = threadIdx.x; m < L; m += blockDim.x) scell[m] = v.cell[m];
     __syncthreads();
     const double tl = sht[n - 1];
     const bool ext = t > tl;
     const double hx = t - tl;
     const int lane = threadIdx.x & 31;
-    const int nwarps = gridDim.x * HI_WARPS;
     const double* __restrict__ theta = v.theta;
     const double* __restrict__ omega = v.omega;
     const double* __restrict__ nu = v.nu;
+    const int chunk = v.hi_chunk;
+    int ub, ue;
+    hi_unit_block(L, chunk, &ub, &ue);
 
-    for (int j = blockIdx.x * HI_WARPS + (threadIdx.x >> 5); j < L; j += nwarps) {
+    for (int u = ub + (threadIdx.x >> 5); u < ue; u += HI_WARPS) {
+        int j, i0, i1;
+        hi_unit_range(u, L, chunk, &j, &i0, &i1);
         const double thj = theta[j], omj = omega[j];
-        const TimeW b1 = time_weights_f64(sht, n, ext, tl, hx, thj * t, scell[j]);
+        TimeW b1;
+        {
+            const B1Desc d = v.b1[j];
+            b1.a0 = d.a0; b1.a1 = d.a1;
+            b1.w0 = d.w[0]; b1.w1 = d.w[1]; b1.w2 = d.w[2]; b1.w3 = d.w[3];
+        }
         const double* __restrict__ x1r = v.x1 + (size_t)j * L;
         const double* __restrict__ x2r = v.x2 + (size_t)j * L;
         const double* __restrict__ x3r = v.x3 + (size_t)j * L;
@@ -152,7 +162,7 @@ __global__ void __launch_bounds__(HI_THREADS) k_hi_f64(SolverView v, const doubl
 #pragma unroll
         for (int r = 0; r < 9; ++r) acc[r] = 0.0;
         double c_at_0 = 0.0;
-        for (int i = lane; i < L; i += 32) {
+        for (int i = i0 + lane; i < i1; i += 32) {
             // ---- B1: on-grid column i at time theta_j t
             double CB1, RB1;
             {
@@ -245,12 +255,10 @@ __global__ void __launch_bounds__(HI_THREADS) k_hi_f64(SolverView v, const doubl
             acc[8] += nui * ((f2a * CB1 + f1a) * RB1);
             if (i == 0) c_at_0 = CB1;
         }
+        double sums[9];
 #pragma unroll
-        for (int r = 0; r < 9; ++r) {
-            double s = warp_sum(acc[r]);
-            if (lane == 0) S[(size_t)r * L + j] = s;
-        }
-        if (lane == 0) S[(size_t)9 * L + j] = c_at_0;
+        for (int r = 0; r < 9; ++r) sums[r] = warp_sum(acc[r]);
+        if (lane == 0) hi_finish_unit(sums, c_at_0, u, L, chunk, v.Spart, v.jcount, S);
     }
 }
 
@@ -266,7 +274,7 @@ struct Kahan {
 };
 
 template <int SW>
-__global__ void __launch_bounds__(HI_THREADS) k_hi_f32(SolverView v, const double* __restrict__ row,
+__global__ void __launch_bounds__(HI_THREADS, 1) k_hi_f32(SolverView v, const double* __restrict__ row,
                                                        double t_arg, int from_state, double* __restrict__ S) {
     extern __shared__ __align__(32) unsigned char smraw[];
     const DevState* st = v.st;
@@ -297,8 +305,7 @@ __global__ void __launch_bounds__(HI_THREADS) k_hi_f32(SolverView v, const doubl
             sdt[i] = (float)(tk1 - tk);
         }
     }
-    __syncthreads();
-    for (int m = threadIdx.x; m < L; m += blockDim.x) scell[m] = find_slice(sht, n, v.theta[m] * t);
+    for (int m = threadIdx.x; m < L; m += blockDim.x) scell[m] = v.cell[m];
     __syncthreads();
     const double tl = sht[n - 1];
     const bool ext = t > tl;
@@ -306,16 +313,24 @@ __global__ void __launch_bounds__(HI_THREADS) k_hi_f32(SolverView v, const doubl
     const float vlast = sv[n - 1];
     const float hx32 = (float)hx;
     const int lane = threadIdx.x & 31;
-    const int nwarps = gridDim.x * HI_WARPS;
     const float* __restrict__ om32 = v.omega32;
     const float* __restrict__ nu32 = v.nu32;
     const float fscale = 1.0f / (float)(1u << FIX_FRAC_BITS);
+    const int chunk = v.hi_chunk;
+    int ub, ue;
+    hi_unit_block(L, chunk, &ub, &ue);
 
-    for (int j = blockIdx.x * HI_WARPS + (threadIdx.x >> 5); j < L; j += nwarps) {
-        const double thj = v.theta[j];
+    for (int u = ub + (threadIdx.x >> 5); u < ue; u += HI_WARPS) {
+        int j, i0, i1;
+        hi_unit_range(u, L, chunk, &j, &i0, &i1);
         const float omj = om32[j];
-        const TimeW b1d = time_weights_f64(sht, n, ext, tl, hx, thj * t, scell[j]);
-        const float bw0 = (float)b1d.w0, bw1 = (float)b1d.w1, bw2 = (float)b1d.w2, bw3 = (float)b1d.w3;
+        TimeW b1d;
+        float bw0, bw1, bw2, bw3;
+        {
+            const B1Desc d = v.b1[j];
+            b1d.a0 = d.a0; b1d.a1 = d.a1;
+            bw0 = d.wd[0].hi; bw1 = d.wd[1].hi; bw2 = d.wd[2].hi; bw3 = d.wd[3].hi;
+        }
         const uint32_t* __restrict__ p1r = v.p1 + (size_t)j * L;
         const uint32_t* __restrict__ p2r = v.p2 + (size_t)j * L;
         const uint32_t* __restrict__ p3r = v.p3 + (size_t)j * L;
@@ -323,7 +338,7 @@ __global__ void __launch_bounds__(HI_THREADS) k_hi_f32(SolverView v, const doubl
 #pragma unroll
         for (int r = 0; r < 9; ++r) { acc[r].s = 0.f; acc[r].c = 0.f; }
         float c_at_0 = 0.f;
-        for (int i = lane; i < L; i += 32) {
+        for (int i = i0 + lane; i < i1; i += 32) {
             float CB1, RB1;
             {
                 float4 h0 = H[(size_t)b1d.a0 * L + i];
@@ -430,12 +445,14 @@ __global__ void __launch_bounds__(HI_THREADS) k_hi_f32(SolverView v, const doubl
             acc[8].add(nui * ((f2a * CB1 + f1a) * RB1));
             if (i == 0) c_at_0 = CB1;
         }
+        double sums[9];
 #pragma unroll
         for (int r = 0; r < 9; ++r) {
-            double s = warp_sum((double)acc[r].s - (double)acc[r].c);
-            if (lane == 0) S[(size_t)r * L + j] = s;
+            // the compensated pair (s, -c) reduced as a double-float on the FP32 pipes
+            const df x = df_warp_sum(fast_two_sum(acc[r].s, -acc[r].c));
+            sums[r] = lane == 0 ? df_to_d(x) : 0.0;
         }
-        if (lane == 0) S[(size_t)9 * L + j] = (double)c_at_0;
+        if (lane == 0) hi_finish_unit(sums, (double)c_at_0, u, L, chunk, v.Spart, v.jcount, S);
     }
 }
 
@@ -464,6 +481,7 @@ void* hi_kernel_for(const SolverView& v) {
 }  // namespace
 
 int hi_config(const SolverView& v, int* grid_ctas, size_t* smem) {
+    if (v.precision == DMFE_DOUBLE_FLOAT) return hi_config_df(v, grid_ctas, smem);
     void* fn = hi_kernel_for(v);
     if (!fn) return DMFE_ERR_UNSUPPORTED;
     size_t sm = hi_smem_bytes(v);
@@ -477,7 +495,7 @@ int hi_config(const SolverView& v, int* grid_ctas, size_t* smem) {
     int per_sm = 0;
     DMFE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, HI_THREADS, sm));
     if (per_sm < 1) return DMFE_ERR_UNSUPPORTED;
-    int want = (v.L + HI_WARPS - 1) / HI_WARPS;
+    int want = (hi_parts(v.L, v.hi_chunk) * v.L + HI_WARPS - 1) / HI_WARPS;
     int cap = nsm * per_sm;
     *grid_ctas = want < cap ? want : cap;
     *smem = sm;
@@ -486,8 +504,12 @@ int hi_config(const SolverView& v, int* grid_ctas, size_t* smem) {
 
 int launch_history_integrals(const SolverView& v, const double* row_dev, double t, bool from_state,
                              double* S_dev, int grid_ctas, cudaStream_t s) {
+    if (v.precision == DMFE_DOUBLE_FLOAT)
+        return launch_history_integrals_df(v, row_dev, t, from_state, S_dev, grid_ctas, s);
     void* fn = hi_kernel_for(v);
     if (!fn) return DMFE_ERR_UNSUPPORTED;
+    int rc = launch_stage_prep(v, row_dev, t, from_state, s);
+    if (rc) return rc;
     size_t sm = hi_smem_bytes(v);
     int fs = from_state ? 1 : 0;
     void* args[] = {(void*)&v, (void*)&row_dev, (void*)&t, (void*)&fs, (void*)&S_dev};

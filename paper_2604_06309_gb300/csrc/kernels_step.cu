@@ -64,7 +64,7 @@ __device__ double frac_index_dev(const SolverView& v, double th, double om) {
 }
 
 __global__ void k_tables(SolverView v, double* x1, double* x2, double* x3, uint32_t* p1, uint32_t* p2,
-                         uint32_t* p3) {
+                         uint32_t* p3, df* q1, df* q2, df* q3) {
     const long long LL = (long long)v.L * v.L;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < LL;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -81,6 +81,11 @@ __global__ void k_tables(SolverView v, double* x1, double* x2, double* x3, uint3
         const double b = frac_index_dev(v, ph2, oph2);
         const double c = frac_index_dev(v, ps, ops);
         if (x1) { x1[idx] = a; x2[idx] = b; x3[idx] = c; }
+        if (q1) {
+            q1[idx] = df_from_d(a);
+            q2[idx] = df_from_d(b);
+            q3[idx] = df_from_d(c);
+        }
         if (p1) {
             const double sc = (double)(1u << FIX_FRAC_BITS);
             p1[idx] = (uint32_t)llrint(a * sc);
@@ -175,6 +180,7 @@ __global__ void __launch_bounds__(CTL_THREADS) k_initial(SolverView v) {
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         v.hist[act][i] = dbl4{1.0, dC[i], 1.0, dR[i]};
         if (v.hist32[act]) v.hist32[act][i] = make_float4(1.f, (float)dC[i], 1.f, (float)dR[i]);
+        if (v.histdf[act]) v.histdf[act][i] = df8{df{1.f, 0.f}, df_from_d(dC[i]), df{1.f, 0.f}, df_from_d(dR[i])};
     }
     if (threadIdx.x == 0) {
         v.ht[act][0] = 0.0;
@@ -194,10 +200,12 @@ __device__ void append_slice(const SolverView& v, int act, int slot, double t, c
     const int L = v.L;
     dbl4* H = v.hist[act] + (size_t)slot * L;
     float4* H32 = v.hist32[act] ? v.hist32[act] + (size_t)slot * L : nullptr;
+    df8* HD = v.histdf[act] ? v.histdf[act] + (size_t)slot * L : nullptr;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         const dbl4 e{Y[i], dY[i], Y[L + i], dY[L + i]};
         H[i] = e;
         if (H32) H32[i] = make_float4((float)e.x, (float)e.y, (float)e.z, (float)e.w);
+        if (HD) HD[i] = df8{df_from_d(e.x), df_from_d(e.y), df_from_d(e.z), df_from_d(e.w)};
     }
     if (threadIdx.x == 0) v.ht[act][slot] = t;
 }
@@ -423,6 +431,7 @@ __global__ void k_sp_compact(SolverView v) {
         const size_t dst = (size_t)v.newidx[k] * L + i;
         v.hist[nxt][dst] = v.hist[act][q];
         if (v.hist32[act]) v.hist32[nxt][dst] = v.hist32[act][q];
+        if (v.histdf[act]) v.histdf[nxt][dst] = v.histdf[act][q];
         if (i == 0) v.ht[nxt][v.newidx[k]] = v.ht[act][k];
     }
 }
@@ -500,7 +509,8 @@ __global__ void k_refresh_replica(SolverView v) {
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < tot;
          q += (long long)gridDim.x * blockDim.x) {
         const dbl4 e = v.hist[act][q];
-        v.hist32[act][q] = make_float4((float)e.x, (float)e.y, (float)e.z, (float)e.w);
+        if (v.hist32[act]) v.hist32[act][q] = make_float4((float)e.x, (float)e.y, (float)e.z, (float)e.w);
+        if (v.histdf[act]) v.histdf[act][q] = df8{df_from_d(e.x), df_from_d(e.y), df_from_d(e.z), df_from_d(e.w)};
     }
 }
 
@@ -513,10 +523,9 @@ int grid_for(long long work, int threads) {
 }  // namespace
 
 int launch_tables(const SolverView& v, cudaStream_t s) {
-    const bool f64 = v.precision == DMFE_FP64;
     k_tables<<<grid_for((long long)v.L * v.L, 256), 256, 0, s>>>(
-        v, f64 ? (double*)v.x1 : nullptr, f64 ? (double*)v.x2 : nullptr, f64 ? (double*)v.x3 : nullptr,
-        f64 ? nullptr : (uint32_t*)v.p1, f64 ? nullptr : (uint32_t*)v.p2, f64 ? nullptr : (uint32_t*)v.p3);
+        v, (double*)v.x1, (double*)v.x2, (double*)v.x3, (uint32_t*)v.p1, (uint32_t*)v.p2, (uint32_t*)v.p3,
+        (df*)v.q1, (df*)v.q2, (df*)v.q3);
     DMFE_CUDA_TRY(cudaGetLastError());
     return DMFE_OK;
 }
@@ -570,7 +579,7 @@ int launch_lookup(const SolverView& v, int n, const double* t, const double* tp,
 }
 
 int launch_refresh_replica(const SolverView& v, cudaStream_t s) {
-    if (!v.hist32[0]) return DMFE_OK;
+    if (!v.hist32[0] && !v.histdf[0]) return DMFE_OK;
     k_refresh_replica<<<grid_for((long long)v.cap * v.L, 256), 256, 0, s>>>(v);
     DMFE_CUDA_TRY(cudaGetLastError());
     return DMFE_OK;

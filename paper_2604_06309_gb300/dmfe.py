@@ -26,6 +26,8 @@ DMFE_ERR_UNSUPPORTED = -8
 DMFE_ERR_IO = -9
 DMFE_FP64 = 0
 DMFE_FP32_COMPENSATED = 1
+DMFE_DOUBLE_FLOAT = 2
+PRECISIONS = {"fp64": DMFE_FP64, "fp32": DMFE_FP32_COMPENSATED, "df": DMFE_DOUBLE_FLOAT}
 DMFE_NS = 10
 
 _d = ctypes.c_double
@@ -73,6 +75,7 @@ _SIGS = {
     "dmfe_checkpoint": (_i, [_p, ctypes.c_char_p]),
     "dmfe_restore": (_i, [ctypes.c_char_p, _p, ctypes.POINTER(_p)]),
     "dmfe_sync": (_i, [_p]),
+    "dmfe_autotune": (_i, [_p, _ip]),
     "dmfe_sparsify_select_noalloc": (_i, [_p, _p, _p, _p, _p, _i, _i, _d, _p, _p]),
 }
 
@@ -139,7 +142,7 @@ class Solver:
         prm.grid_t_max, prm.alpha, prm.delta = grid_t_max, alpha, delta
         prm.history_cap = int(history_cap) if history_cap else L
         prm.dt0, prm.dt_min = dt0, dt_min
-        prm.precision = DMFE_FP64 if precision == "fp64" else DMFE_FP32_COMPENSATED
+        prm.precision = PRECISIONS[precision]
         prm.sparsify = 1 if sparsify else 0
         prm.stream = stream
         _check(lib.dmfe_create(ctypes.byref(prm), ctypes.byref(self.h)), "dmfe_create")
@@ -261,6 +264,12 @@ class Solver:
 
     def checkpoint(self, path):
         _check(self._lib.dmfe_checkpoint(self.h, path.encode()), "dmfe_checkpoint")
+
+    def autotune(self):
+        """Pick the fastest work-unit size for this configuration; returns it."""
+        c = _i()
+        _check(self._lib.dmfe_autotune(self.h, ctypes.byref(c)), "dmfe_autotune")
+        return c.value
 
     def sync(self):
         return self._lib.dmfe_sync(self.h)

@@ -25,7 +25,7 @@ def test_grid_and_weights(L, t_max, alpha, delta):
     sv.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "df"])
 @pytest.mark.parametrize("L,t_max,alpha,delta", [(129, 100.0, 0.0, 0.0), (97, 1e4, 0.5, 0.2)])
 def test_stencil_tables(precision, L, t_max, alpha, delta):
     need_gpu()

@@ -10,7 +10,7 @@ from paper_2604_06309_gb300.inputs import MIXED_34, PURE_3
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-11, "fp32": 3e-6}
+TOL = {"fp64": 1e-11, "fp32": 3e-6, "df": 1e-10}
 
 
 def _oracle_S(coefs, T, L, t_max, s, hist, t, C, R, js=None):
@@ -19,7 +19,7 @@ def _oracle_S(coefs, T, L, t_max, s, hist, t, C, R, js=None):
     return OI.history_integrals(Model(coefs, T), G, H, t, C, R, js=js)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "df"])
 @pytest.mark.parametrize("L,s,n", [(33, 4, 40), (129, 4, 130), (129, 6, 1), (129, 10, 2), (257, 8, 61), (100, 4, 17)])
 def test_frozen_history_at_last_slice(precision, L, s, n):
     need_gpu()
@@ -37,7 +37,7 @@ def test_frozen_history_at_last_slice(precision, L, s, n):
     sv.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "df"])
 def test_stage_beyond_last_slice_uses_quadratic_extension(precision):
     need_gpu()
     from paper_2604_06309_gb300 import Solver
@@ -53,22 +53,23 @@ def test_stage_beyond_last_slice_uses_quadratic_extension(precision):
     sv.close()
 
 
-def test_exact_p2_history():
+@pytest.mark.parametrize("precision", ["fp64", "df"])
+def test_exact_p2_history(precision):
     need_gpu()
     from paper_2604_06309_gb300 import Solver
     L = 129
-    sv = Solver({2: 0.5}, 0.0, L, 100.0, s=6, history_cap=401)
+    sv = Solver({2: 0.5}, 0.0, L, 100.0, s=6, history_cap=401, precision=precision)
     times = np.concatenate([[0.0], np.geomspace(1e-3, 5.0, 400)])
     C, dC, R, dR = cf.p2_history(times, sv.theta, sv.omega)
     sv.set_history(times, C, dC, R, dR)
     S, mu = sv.history_integrals(5.0, C[-1], R[-1])
     Sref = _oracle_S({2: 0.5}, 0.0, L, 100.0, 6, (times, C, dC, R, dR), 5.0, C[-1], R[-1])
-    assert np.max(np.abs(S - Sref)) < 1e-11
+    assert np.max(np.abs(S - Sref)) < TOL[precision]
     assert abs(mu - cf.p2_mu(5.0)) < 1e-8
     sv.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "df"])
 def test_full_size_sampled_rows(precision):
     """L = 2049 with 2049 stored slices (the benchmark shape) at the benchmark launch
     configuration; the oracle evaluates a sample of output rows one by one."""
@@ -102,4 +103,21 @@ def test_device_entry_matches_host_entry():
     sv.history_integrals_dev(t, row.data_ptr(), S_dev.data_ptr(), stream.cuda_stream)
     torch.cuda.synchronize()
     assert np.array_equal(S_dev.cpu().numpy(), S_host)
+    sv.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df", "fp32"])
+def test_autotune_keeps_results(precision):
+    """The unit size only changes the summation order: results agree to rounding."""
+    need_gpu()
+    from paper_2604_06309_gb300 import Solver
+    L = 1100
+    sv = Solver(MIXED_34, 0.5, L, 1e4, history_cap=300, precision=precision)
+    hist = frozen_case(sv, 9, 300, 5e3)
+    t = hist[0][-1]
+    S0, _ = sv.history_integrals(t, hist[1][-1], hist[3][-1])
+    chunk = sv.autotune()
+    assert chunk in (256, 512, 1024, L)
+    S1, _ = sv.history_integrals(t, hist[1][-1], hist[3][-1])
+    assert np.max(np.abs(S1 - S0)) < (1e-6 if precision == "fp32" else 1e-12)
     sv.close()

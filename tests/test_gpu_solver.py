@@ -55,9 +55,10 @@ def _compare_runs(g, o, tol_rows=1e-9):
     assert st["forced_removals"] == o.stats["forced_removals"]
 
 
-def test_integrate_fp64_matches_oracle_step_by_step():
+@pytest.mark.parametrize("precision", ["fp64", "df"])
+def test_integrate_fp64_matches_oracle_step_by_step(precision):
     need_gpu()
-    g, o = _pair(PURE_3, 0.8, 33, 100.0, cap=400)
+    g, o = _pair(PURE_3, 0.8, 33, 100.0, cap=400, precision=precision)
     assert g.integrate(1.0, 1e-8) == 0
     assert o.integrate(1.0, 1e-8) == 0
     _compare_runs(g, o)
@@ -66,10 +67,11 @@ def test_integrate_fp64_matches_oracle_step_by_step():
     g.close()
 
 
-def test_integrate_with_sparsification_and_rejections_matches_oracle():
+@pytest.mark.parametrize("precision", ["fp64", "df"])
+def test_integrate_with_sparsification_and_rejections_matches_oracle(precision):
     need_gpu()
     # a large first step forces rejections; a small store forces sparsification passes
-    g, o = _pair(MIXED_34, 0.5, 33, 100.0, cap=24, dt0=0.3)
+    g, o = _pair(MIXED_34, 0.5, 33, 100.0, cap=24, dt0=0.3, precision=precision)
     assert g.integrate(2.0, 1e-8) == 0
     assert o.integrate(2.0, 1e-8) == 0
     assert o.stats["steps_rejected"] >= 1 and o.stats["sparsify_passes"] >= 1
