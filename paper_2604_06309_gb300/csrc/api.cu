@@ -181,7 +181,11 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
         }
     }
     TRY(dev_alloc(h, &p, sizeof(DevState))); v.st = (DevState*)p;
-    TRY(dev_alloc(h, &p, 2 * L * sizeof(double))); v.Y = (double*)p;
+    TRY(dev_alloc(h, &p, 2 * 2 * (size_t)L * sizeof(double))); v.Y = (double*)p;
+    TRY(dev_alloc(h, &p, 2 * (size_t)kMaxPrepBlocks * sizeof(double))); v.mupart = (double*)p;
+    TRY(dev_alloc(h, &p, (size_t)kCtlGrid * sizeof(double))); v.epart = (double*)p;
+    TRY(dev_alloc(h, &p, sizeof(int))); v.ctl_count = (int*)p;
+    DMFE_CUDA_TRY(cudaMemsetAsync(v.ctl_count, 0, sizeof(int), h->stream));
     TRY(dev_alloc(h, &p, 7 * 2 * (size_t)L * sizeof(double))); v.k = (double*)p;
     TRY(dev_alloc(h, &p, 2 * L * sizeof(double))); v.ynew = (double*)p;
     TRY(dev_alloc(h, &p, (size_t)DMFE_NS * L * sizeof(double))); v.S = (double*)p;

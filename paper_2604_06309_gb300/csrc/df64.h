@@ -71,4 +71,34 @@ __device__ __forceinline__ bool df_lt(df a, df b) { return a.hi < b.hi || (a.hi 
 __device__ __forceinline__ bool df_ge(df a, df b) { return !df_lt(a, b); }
 
 __device__ __forceinline__ double df_to_d(df a) { return (double)a.hi + (double)a.lo; }
+
+// Accumulator of double-float products sum_k w_k v_k: the high parts are added exactly
+// (TwoSum), the low parts and the product errors in plain FP32; one renormalisation at
+// the end. Same error bound as repeated df_fma, 12 instead of 18 FP32 operations a term.
+struct dacc {
+    float s, lo;
+};
+
+__device__ __forceinline__ dacc dacc_prod(df w, df v) {
+    const float p = __fmul_rn(w.hi, v.hi);
+    float e = __fmaf_rn(w.hi, v.hi, -p);
+    e = __fmaf_rn(w.hi, v.lo, e);
+    e = __fmaf_rn(w.lo, v.hi, e);
+    return dacc{p, e};
+}
+
+__device__ __forceinline__ void dacc_add(dacc& a, df w, df v) {
+    const dacc t = dacc_prod(w, v);
+    const df s = two_sum(a.s, t.s);
+    a.s = s.hi;
+    a.lo = __fadd_rn(a.lo, __fadd_rn(s.lo, t.lo));
+}
+
+__device__ __forceinline__ void dacc_add_df(dacc& a, df x) {
+    const df s = two_sum(a.s, x.hi);
+    a.s = s.hi;
+    a.lo = __fadd_rn(a.lo, __fadd_rn(s.lo, x.lo));
+}
+
+__device__ __forceinline__ df dacc_get(dacc a) { return fast_two_sum(a.s, a.lo); }
 #endif

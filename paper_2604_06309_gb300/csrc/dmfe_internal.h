@@ -126,7 +126,11 @@ struct SolverView {
     B1Desc* b1;           // [L] per-stage B1 time weights
     int hi_chunk;         // summation indices per work unit
     DevState* st;
-    double* Y;            // [2L] stage row (C then R)
+    double* Y;            // [2][2L] stage rows (C then R), double-buffered: stage stg reads
+                          // Y + (stg & 1) * 2L and writes the other buffer
+    double* mupart;       // [2][kMaxPrepBlocks] per-block partial sums of mu's and E's integrands
+    double* epart;        // [kCtlGrid] per-CTA partial sums of the step error
+    int* ctl_count;       // CTAs finished in the last stage of a step (zero between steps)
     double* k;            // [7][2L] stage derivatives
     double* ynew;         // [2L] 5th-order solution of the trial step
     double* S;            // [NS][L]
@@ -138,6 +142,10 @@ struct SolverView {
 };
 
 static const int FIX_FRAC_BITS = 19;  // x = packed / 2^19
+constexpr int kPrepThreads = 128;     // block size of the per-stage prep kernel
+constexpr int kMaxPrepBlocks = (8192 + kPrepThreads - 1) / kPrepThreads;
+constexpr int kCtlThreads = 256;      // block size of the multi-CTA stage kernels
+constexpr int kCtlGrid = 64;          // their maximal grid
 
 // ---- launchers (defined in the .cu files) ----
 int launch_tables(const SolverView& v, cudaStream_t s);

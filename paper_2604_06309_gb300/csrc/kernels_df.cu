@@ -43,8 +43,15 @@ __global__ void k_stage_prep(SolverView v, const double* __restrict__ row, doubl
     const bool ext = t > tl;
     const double hx = t - tl;
     const int tot = L > n ? L : n;
+    __shared__ double red_m[kPrepThreads], red_e[kPrepThreads];
+    double pm = 0.0, pe = 0.0;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += gridDim.x * blockDim.x) {
         if (q < L) {
+            // integrands of mu and E on the stage row (Sec. 2.1), summed per block below
+            const double Cq = row[q], Rq = row[L + q];
+            const double Dq = fp1(v.poly, Cq);
+            pm += v.nu[q] * (fp2(v.poly, Cq) * Rq * Cq + Dq * Rq);
+            pe += v.nu[q] * (Dq * Rq);
             const double tau = v.theta[q] * t;
             const int c = find_slice_g(ht, n, tau);
             v.cell[q] = c;
@@ -89,9 +96,42 @@ __global__ void k_stage_prep(SolverView v, const double* __restrict__ row, doubl
             v.slicedf[q] = e;
         }
     }
+    // deterministic block reduction: each block owns one fixed range of q
+    red_m[threadIdx.x] = pm;
+    red_e[threadIdx.x] = pe;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            red_m[threadIdx.x] += red_m[threadIdx.x + w];
+            red_e[threadIdx.x] += red_e[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        v.mupart[blockIdx.x] = red_m[0];
+        v.mupart[kMaxPrepBlocks + blockIdx.x] = red_e[0];
+    }
 }
 
 // Lagrange weights on nodes 0..SW-1 at the double-float position u.
+template <int SW>
+__device__ __forceinline__ void lagrange_df(df u, df (&w)[SW]);
+
+// Width 4: w0 = -(u-1)(u-2)(u-3)/6, w1 = u(u-2)(u-3)/2, w2 = -u(u-1)(u-3)/2,
+// w3 = u(u-1)(u-2)/6, with the shared products u(u-1) and (u-2)(u-3).
+template <>
+__device__ __forceinline__ void lagrange_df<4>(df u, df (&w)[4]) {
+    const df u1 = df_add_f(u, -1.f), u2 = df_add_f(u, -2.f), u3 = df_add_f(u, -3.f);
+    const df ab = df_mul(u, u1), cd = df_mul(u2, u3);
+    const df sixth = df{0.16666667163372040f, -4.9670538e-09f};  // 1/6 as a double-float
+    w[0] = df_neg(df_mul(df_mul(u1, cd), sixth));
+    const df h1 = df_mul(u, cd);
+    w[1] = df{h1.hi * 0.5f, h1.lo * 0.5f};
+    const df h2 = df_mul(ab, u3);
+    w[2] = df{h2.hi * -0.5f, h2.lo * -0.5f};
+    w[3] = df_mul(df_mul(ab, u2), sixth);
+}
+
 template <int SW>
 __device__ __forceinline__ void lagrange_df(df u, df (&w)[SW]) {
     df um[SW];
@@ -205,53 +245,65 @@ __global__ void __launch_bounds__(DF_THREADS, 1) k_hi_df(SolverView v, double t_
         const df* __restrict__ q1r = v.q1 + (size_t)j * L;
         const df* __restrict__ q2r = v.q2 + (size_t)j * L;
         const df* __restrict__ q3r = v.q3 + (size_t)j * L;
-        df acc[9];
+        dacc acc[9];
 #pragma unroll
-        for (int r = 0; r < 9; ++r) acc[r] = df{0.f, 0.f};
+        for (int r = 0; r < 9; ++r) acc[r] = dacc{0.f, 0.f};
         df c_at_0 = df{0.f, 0.f};
         for (int i = i0 + lane; i < i1; i += 32) {
             // ---- B1: on-grid column i at time theta_j t
             df CB1, RB1;
             {
                 const df8 h0 = H[(size_t)a0 * L + i];
-                CB1 = df_add(df_mul(bw0, h0.C), df_mul(bw1, h0.dC));
-                RB1 = df_add(df_mul(bw0, h0.R), df_mul(bw1, h0.dR));
+                dacc c = dacc_prod(bw0, h0.C), r = dacc_prod(bw0, h0.R);
+                dacc_add(c, bw1, h0.dC);
+                dacc_add(r, bw1, h0.dR);
                 if (a1 >= 0) {
                     const df8 h1 = H[(size_t)a1 * L + i];
-                    CB1 = df_add(CB1, df_add(df_mul(bw2, h1.C), df_mul(bw3, h1.dC)));
-                    RB1 = df_add(RB1, df_add(df_mul(bw2, h1.R), df_mul(bw3, h1.dR)));
+                    dacc_add(c, bw2, h1.C);
+                    dacc_add(c, bw3, h1.dC);
+                    dacc_add(r, bw2, h1.R);
+                    dacc_add(r, bw3, h1.dR);
                 } else {
                     const dfrow r1 = srow[i];
-                    CB1 = df_add(CB1, df_mul(bw2, r1.C));
-                    RB1 = df_add(RB1, df_mul(bw2, r1.R));
+                    dacc_add(c, bw2, r1.C);
+                    dacc_add(r, bw2, r1.R);
                 }
+                CB1 = dacc_get(c);
+                RB1 = dacc_get(r);
             }
             // ---- A1: current row at phi1
-            df KA1 = {0.f, 0.f}, DA1 = {0.f, 0.f}, CA1 = {0.f, 0.f}, RA1 = {0.f, 0.f};
+            df KA1, DA1, CA1, RA1;
             {
                 df w[SW];
                 const int b = stencil_df<SW>(q1r[i], L, w);
+                const dfrow q0 = srow[b];
+                dacc k = dacc_prod(w[0], q0.K), d = dacc_prod(w[0], q0.D);
+                dacc c = dacc_prod(w[0], q0.C), r = dacc_prod(w[0], q0.R);
 #pragma unroll
-                for (int k = 0; k < SW; ++k) {
-                    const dfrow q = srow[b + k];
-                    KA1 = df_fma(w[k], q.K, KA1);
-                    DA1 = df_fma(w[k], q.D, DA1);
-                    CA1 = df_fma(w[k], q.C, CA1);
-                    RA1 = df_fma(w[k], q.R, RA1);
+                for (int m = 1; m < SW; ++m) {
+                    const dfrow q = srow[b + m];
+                    dacc_add(k, w[m], q.K);
+                    dacc_add(d, w[m], q.D);
+                    dacc_add(c, w[m], q.C);
+                    dacc_add(r, w[m], q.R);
                 }
+                KA1 = dacc_get(k); DA1 = dacc_get(d); CA1 = dacc_get(c); RA1 = dacc_get(r);
             }
             // ---- A2: current row at phi2
-            df KA2 = {0.f, 0.f}, RA2 = {0.f, 0.f};
+            df KA2, RA2;
             const df x2 = q2r[i];
             {
                 df w[SW];
                 const int b = stencil_df<SW>(x2, L, w);
+                const dfrow q0 = srow[b];
+                dacc k = dacc_prod(w[0], q0.K), r = dacc_prod(w[0], q0.R);
 #pragma unroll
-                for (int k = 0; k < SW; ++k) {
-                    const dfrow q = srow[b + k];
-                    KA2 = df_fma(w[k], q.K, KA2);
-                    RA2 = df_fma(w[k], q.R, RA2);
+                for (int m = 1; m < SW; ++m) {
+                    const dfrow q = srow[b + m];
+                    dacc_add(k, w[m], q.K);
+                    dacc_add(r, w[m], q.R);
                 }
+                KA2 = dacc_get(k); RA2 = dacc_get(r);
             }
             // ---- B2: theta position psi on the slices around phi2 t (complement form)
             df CB2, RB2;
@@ -286,41 +338,56 @@ __global__ void __launch_bounds__(DF_THREADS, 1) k_hi_df(SolverView v, double t_
                 }
                 df w[SW];
                 const int b = stencil_df<SW>(q3r[i], L, w);
-                df c0 = {0.f, 0.f}, dc0 = {0.f, 0.f}, r0 = {0.f, 0.f}, dr0 = {0.f, 0.f};
                 const df8* __restrict__ p0 = H + (size_t)s0 * L + b;
+                df c0, dc0, r0, dr0;
+                {
+                    const df8 e0 = p0[0];
+                    dacc ac = dacc_prod(w[0], e0.C), adc = dacc_prod(w[0], e0.dC);
+                    dacc ar = dacc_prod(w[0], e0.R), adr = dacc_prod(w[0], e0.dR);
 #pragma unroll
-                for (int k = 0; k < SW; ++k) {
-                    const df8 e = p0[k];
-                    c0 = df_fma(w[k], e.C, c0);
-                    dc0 = df_fma(w[k], e.dC, dc0);
-                    r0 = df_fma(w[k], e.R, r0);
-                    dr0 = df_fma(w[k], e.dR, dr0);
+                    for (int m = 1; m < SW; ++m) {
+                        const df8 e = p0[m];
+                        dacc_add(ac, w[m], e.C);
+                        dacc_add(adc, w[m], e.dC);
+                        dacc_add(ar, w[m], e.R);
+                        dacc_add(adr, w[m], e.dR);
+                    }
+                    c0 = dacc_get(ac); dc0 = dacc_get(adc); r0 = dacc_get(ar); dr0 = dacc_get(adr);
                 }
-                CB2 = df_add(df_mul(tw0, c0), df_mul(tw1, dc0));
-                RB2 = df_add(df_mul(tw0, r0), df_mul(tw1, dr0));
-                df c1 = {0.f, 0.f}, dc1 = {0.f, 0.f}, r1 = {0.f, 0.f}, dr1 = {0.f, 0.f};
+                dacc tc = dacc_prod(tw0, c0), tr = dacc_prod(tw0, r0);
+                dacc_add(tc, tw1, dc0);
+                dacc_add(tr, tw1, dr0);
                 if (s1 >= 0) {
                     const df8* __restrict__ p1 = H + (size_t)s1 * L + b;
+                    const df8 e0 = p1[0];
+                    dacc ac = dacc_prod(w[0], e0.C), adc = dacc_prod(w[0], e0.dC);
+                    dacc ar = dacc_prod(w[0], e0.R), adr = dacc_prod(w[0], e0.dR);
 #pragma unroll
-                    for (int k = 0; k < SW; ++k) {
-                        const df8 e = p1[k];
-                        c1 = df_fma(w[k], e.C, c1);
-                        dc1 = df_fma(w[k], e.dC, dc1);
-                        r1 = df_fma(w[k], e.R, r1);
-                        dr1 = df_fma(w[k], e.dR, dr1);
+                    for (int m = 1; m < SW; ++m) {
+                        const df8 e = p1[m];
+                        dacc_add(ac, w[m], e.C);
+                        dacc_add(adc, w[m], e.dC);
+                        dacc_add(ar, w[m], e.R);
+                        dacc_add(adr, w[m], e.dR);
                     }
-                    CB2 = df_add(CB2, df_add(df_mul(tw2, c1), df_mul(tw3, dc1)));
-                    RB2 = df_add(RB2, df_add(df_mul(tw2, r1), df_mul(tw3, dr1)));
+                    dacc_add(tc, tw2, dacc_get(ac));
+                    dacc_add(tc, tw3, dacc_get(adc));
+                    dacc_add(tr, tw2, dacc_get(ar));
+                    dacc_add(tr, tw3, dacc_get(adr));
                 } else {
+                    const dfrow e0 = srow[b];
+                    dacc ac = dacc_prod(w[0], e0.C), ar = dacc_prod(w[0], e0.R);
 #pragma unroll
-                    for (int k = 0; k < SW; ++k) {
-                        const dfrow e = srow[b + k];
-                        c1 = df_fma(w[k], e.C, c1);
-                        r1 = df_fma(w[k], e.R, r1);
+                    for (int m = 1; m < SW; ++m) {
+                        const dfrow e = srow[b + m];
+                        dacc_add(ac, w[m], e.C);
+                        dacc_add(ar, w[m], e.R);
                     }
-                    CB2 = df_add(CB2, df_mul(tw2, c1));
-                    RB2 = df_add(RB2, df_mul(tw2, r1));
+                    dacc_add(tc, tw2, dacc_get(ac));
+                    dacc_add(tr, tw2, dacc_get(ar));
                 }
+                CB2 = dacc_get(tc);
+                RB2 = dacc_get(tr);
             }
             const df f1a = poly_df(f1, g1, d1, CB1), f2a = poly_df(f2, g2, d2, CB1);
             const df f1b = poly_df(f1, g1, d1, CB2), f2b = poly_df(f2, g2, d2, CB2);
@@ -328,21 +395,21 @@ __global__ void __launch_bounds__(DF_THREADS, 1) k_hi_df(SolverView v, double t_
             const df nRB1 = df_mul(nui, RB1);
             const df nRA2 = df_mul(nui, RA2);
             const df nKA2 = df_mul(nui, KA2);
-            acc[0] = df_fma(df_mul(nui, KA1), CB1, acc[0]);
-            acc[1] = df_fma(nKA2, CB2, acc[1]);
-            acc[2] = df_fma(DA1, nRB1, acc[2]);
-            acc[3] = df_fma(nKA2, RB2, acc[3]);
-            acc[4] = df_fma(df_mul(f2a, CA1), nRB1, acc[4]);
-            acc[5] = df_fma(df_mul(nui, f1a), RA1, acc[5]);
-            acc[6] = df_fma(f1b, nRA2, acc[6]);
-            acc[7] = df_fma(df_mul(f2b, RB2), nRA2, acc[7]);
-            acc[8] = df_fma(df_fma(f2a, CB1, f1a), nRB1, acc[8]);
+            dacc_add(acc[0], df_mul(nui, KA1), CB1);
+            dacc_add(acc[1], nKA2, CB2);
+            dacc_add(acc[2], DA1, nRB1);
+            dacc_add(acc[3], nKA2, RB2);
+            dacc_add(acc[4], df_mul(f2a, CA1), nRB1);
+            dacc_add(acc[5], df_mul(nui, f1a), RA1);
+            dacc_add(acc[6], f1b, nRA2);
+            dacc_add(acc[7], df_mul(f2b, RB2), nRA2);
+            dacc_add(acc[8], df_fma(f2a, CB1, f1a), nRB1);
             if (i == 0) c_at_0 = CB1;
         }
         double sums[9];
 #pragma unroll
         for (int r = 0; r < 9; ++r) {
-            const df x = df_warp_sum(acc[r]);
+            const df x = df_warp_sum(dacc_get(acc[r]));
             sums[r] = lane == 0 ? df_to_d(x) : 0.0;
         }
         if (lane == 0) hi_finish_unit(sums, df_to_d(c_at_0), u_, L, chunk, v.Spart, v.jcount, S);
@@ -368,7 +435,7 @@ void* df_kernel_for(int s) {
 
 int launch_stage_prep(const SolverView& v, const double* row_dev, double t, bool from_state, cudaStream_t s) {
     const int tot = v.L > v.cap ? v.L : v.cap;
-    k_stage_prep<<<(tot + 127) / 128, 128, 0, s>>>(v, row_dev, t, from_state ? 1 : 0);
+    k_stage_prep<<<(tot + kPrepThreads - 1) / kPrepThreads, kPrepThreads, 0, s>>>(v, row_dev, t, from_state ? 1 : 0);
     DMFE_CUDA_TRY(cudaGetLastError());
     return DMFE_OK;
 }

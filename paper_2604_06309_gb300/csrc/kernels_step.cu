@@ -210,19 +210,6 @@ __device__ void append_slice(const SolverView& v, int act, int slot, double t, c
     if (threadIdx.x == 0) v.ht[act][slot] = t;
 }
 
-// Stage combination Y = y + h sum_{l <= last} A[row][l] k_l, rounded like the plain sum.
-__device__ void combine(const SolverView& v, const dbl4* yrow, double h, int arow, int nk) {
-    const int L = v.L;
-    const int L2 = 2 * L;
-    for (int q = threadIdx.x; q < L2; q += blockDim.x) {
-        const int i = q < L ? q : q - L;
-        const double y = q < L ? yrow[i].x : yrow[i].z;
-        double acc = 0.0;
-        for (int l = 0; l < nk; ++l) acc = __dadd_rn(acc, __dmul_rn(kDP_A[arow][l], v.k[(size_t)l * L2 + q]));
-        v.Y[q] = __dadd_rn(y, __dmul_rn(h, acc));
-    }
-}
-
 __global__ void __launch_bounds__(CTL_THREADS) k_begin_integrate(SolverView v, double t_target, double tol) {
     if (threadIdx.x != 0) return;
     DevState* st = v.st;
@@ -231,33 +218,37 @@ __global__ void __launch_bounds__(CTL_THREADS) k_begin_integrate(SolverView v, d
     st->done = (st->t >= t_target) ? 1 : 0;
 }
 
-// Start of a trial step: h = min(dt, t_target - t), k_1 = stored derivative of the last
-// slice (first-same-as-last), Y_2 = y + h a_21 k_1.
-__global__ void __launch_bounds__(CTL_THREADS) k_step_begin(SolverView v) {
+// Start of a trial step (multi-CTA): h = min(dt, t_target - t), k_1 = stored derivative of
+// the last slice (first-same-as-last), stage-1 row Y_1 = y + h a_10 k_1 into buffer 1.
+__global__ void __launch_bounds__(kCtlThreads) k_step_begin(SolverView v) {
     DevState* st = v.st;
     if (gated(st)) return;
     const int L = v.L;
-    const int act = st->active;
-    const dbl4* yrow = v.hist[act] + (size_t)(st->n - 1) * L;
+    const dbl4* yrow = v.hist[st->active] + (size_t)(st->n - 1) * L;
     const double t = st->t;
     const double h = fmin(st->dt, st->t_target - t);
-    for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        v.k[i] = yrow[i].y;
-        v.k[L + i] = yrow[i].w;
+    double* Y1 = v.Y + 2 * (size_t)L;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < L; j += gridDim.x * blockDim.x) {
+        const dbl4 e = yrow[j];
+        v.k[j] = e.y;
+        v.k[L + j] = e.w;
+        Y1[j] = __dadd_rn(e.x, __dmul_rn(h, __dmul_rn(kDP_A[1][0], e.y)));
+        Y1[L + j] = __dadd_rn(e.z, __dmul_rn(h, __dmul_rn(kDP_A[1][0], e.w)));
     }
-    __syncthreads();
-    combine(v, yrow, h, 1, 1);
-    if (threadIdx.x == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->h = h;
         st->t_stage = __dadd_rn(t, __dmul_rn(kDP_C[1], h));
     }
 }
 
-// End of stage `stg` (1..6): k_stg from the sums S; then either the next stage row or,
-// after the last stage, the error estimate and the step decision of Sec. 3.5.
-__global__ void __launch_bounds__(CTL_THREADS) k_stage_end(SolverView v, int stg) {
-    __shared__ double red[CTL_THREADS];
-    __shared__ int s_append;
+// End of stage stg (1..6), multi-CTA: k_stg from the sums S and the stage row (read from
+// buffer stg & 1); then either the next stage row (written to the other buffer) or,
+// after the last stage, the error estimate, whose per-CTA partials the last CTA to
+// finish adds in a fixed order before taking the step decision of Sec. 3.5 and
+// appending the slice. mu and E come from the per-block partial sums of the prep kernel.
+__global__ void __launch_bounds__(kCtlThreads) k_stage_end(SolverView v, int stg, int prep_blocks) {
+    __shared__ double s_mu, s_E, red[kCtlThreads];
+    __shared__ int s_last, s_append;
     DevState* st = v.st;
     if (gated(st)) return;
     const int L = v.L;
@@ -266,30 +257,81 @@ __global__ void __launch_bounds__(CTL_THREADS) k_stage_end(SolverView v, int stg
     const int n = st->n;
     const dbl4* yrow = v.hist[act] + (size_t)(n - 1) * L;
     const double t = st->t, h = st->h;
-    double mu, E;
-    assemble_core(v, v.Y, v.S, st->t_stage, v.k + (size_t)stg * L2, v.k + (size_t)stg * L2 + L, &mu, &E, red);
+    const double ts = __dadd_rn(t, __dmul_rn(kDP_C[stg], h));  // this stage's time
+    const double* Yc = v.Y + (size_t)(stg & 1) * L2;
+    double* Yn = v.Y + (size_t)((stg + 1) & 1) * L2;
+    const double C0 = Yc[0];
+    if (threadIdx.x == 0) {
+        double sm = 0.0, se = 0.0;
+        for (int b = 0; b < prep_blocks; ++b) {
+            sm += v.mupart[b];
+            se += v.mupart[kMaxPrepBlocks + b];
+        }
+        s_mu = v.T + ts * sm + v.beta0 * fp1(v.poly, C0) * C0;
+        s_E = -ts * se - v.beta0 * fp0(v.poly, C0);
+    }
     __syncthreads();
+    const double mu = s_mu;
+    double* kC = v.k + (size_t)stg * L2;
+    double pe = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < L; j += gridDim.x * blockDim.x) {
+        const double th = v.theta[j], om = v.omega[j];
+        const double C = Yc[j], R = Yc[L + j];
+        const double* sj = v.S + j;
+        const double S0 = sj[0], S1 = sj[L], S2 = sj[2 * L], S3 = sj[3 * L], S4 = sj[4 * L];
+        const double S5 = sj[5 * L], S6 = sj[6 * L], S7 = sj[7 * L], S8 = sj[8 * L], S9 = sj[9 * L];
+        const double d1C = -mu * C + ts * (th * (S0 + S2) + om * S1) + v.beta0 * fp1(v.poly, C0) * S9;
+        const double d1R = -mu * R + ts * om * S3;
+        const double mup = v.T + ts * th * S8 + v.beta0 * fp1(v.poly, S9) * S9;
+        const double d2C = -mup * C + ts * (th * (S4 + S5) + om * S6) + 2.0 * v.T * R +
+                           v.beta0 * fp1(v.poly, S9) * C0;
+        const double d2R = mup * R - ts * om * S7;
+        const bool diag = (j == L - 1);
+        kC[j] = diag ? 0.0 : d1C + th * d2C;
+        kC[L + j] = diag ? 0.0 : d1R + th * d2R;
+        if (stg < 6) {
+            // next stage row Y = y + h sum_{l <= stg} A[stg+1][l] k_l, rounded like the plain sum
+            for (int half = 0; half < 2; ++half) {
+                const int q = j + half * L;
+                double acc = 0.0;
+                for (int l = 0; l <= stg; ++l) acc = __dadd_rn(acc, __dmul_rn(kDP_A[stg + 1][l], v.k[(size_t)l * L2 + q]));
+                const double y = half == 0 ? yrow[j].x : yrow[j].z;
+                Yn[q] = __dadd_rn(y, __dmul_rn(h, acc));
+            }
+        } else {
+            // embedded error estimate h sum_l e_l k_l, 1-norm
+            for (int half = 0; half < 2; ++half) {
+                const int q = j + half * L;
+                double acc = 0.0;
+                for (int l = 0; l < 7; ++l) acc = __dadd_rn(acc, __dmul_rn(kDP_E[l], v.k[(size_t)l * L2 + q]));
+                pe += fabs(__dmul_rn(h, acc));
+            }
+        }
+    }
     if (stg < 6) {
-        combine(v, yrow, h, stg + 1, stg + 1);
-        if (threadIdx.x == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
             st->stages += 1;
             st->t_stage = __dadd_rn(t, __dmul_rn(kDP_C[stg + 1], h));
         }
         return;
     }
-    // eps_RK = sum_i |dC_i| + |dR_i| with the embedded estimate h sum_l e_l k_l
-    double pe = 0.0;
-    for (int q = threadIdx.x; q < L2; q += blockDim.x) {
-        double acc = 0.0;
-        for (int l = 0; l < 7; ++l) acc = __dadd_rn(acc, __dmul_rn(kDP_E[l], v.k[(size_t)l * L2 + q]));
-        pe += fabs(__dmul_rn(h, acc));
-    }
-    const double eps = block_sum(pe, red);
+    const double ep = block_sum(pe, red);
     if (threadIdx.x == 0) {
+        v.epart[blockIdx.x] = ep;
+        __threadfence();
+        s_last = atomicAdd(v.ctl_count, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        double eps = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) eps += __ldcg(&v.epart[b]);
+        *v.ctl_count = 0;
         st->stages += 1;
         st->eps = eps;
-        st->mu = mu;
-        st->E = E;
+        st->mu = s_mu;
+        st->E = s_E;
         s_append = -1;
         const double tol = st->tol;
         if (!isfinite(eps)) {
@@ -318,7 +360,9 @@ __global__ void __launch_bounds__(CTL_THREADS) k_stage_end(SolverView v, int stg
     }
     __syncthreads();
     if (s_append >= 0) {
+        // the 5th-order solution Y_6 sits in buffer 0, its derivative k_7 in k[6]
         append_slice(v, act, s_append, st->t_pending, v.Y, v.k + (size_t)6 * L2);
+        __syncthreads();
         if (threadIdx.x == 0) {
             st->n = s_append + 1;
             st->t = st->t_pending;
@@ -562,11 +606,16 @@ int launch_sparsify(const SolverView& v, bool from_step, double tol, cudaStream_
 // One Dormand-Prince step: begin, six stages of (history integrals, stage end), then the
 // sparsification kernels, which do nothing unless the step left a slice pending.
 int launch_step(const SolverView& v, int grid_ctas, cudaStream_t s) {
-    k_step_begin<<<1, CTL_THREADS, 0, s>>>(v);
+    int g = (v.L + kCtlThreads - 1) / kCtlThreads;
+    g = g < 1 ? 1 : (g > kCtlGrid ? kCtlGrid : g);
+    const int tot = v.L > v.cap ? v.L : v.cap;
+    const int prep_blocks = (tot + kPrepThreads - 1) / kPrepThreads;
+    k_step_begin<<<g, kCtlThreads, 0, s>>>(v);
     for (int stg = 1; stg <= 6; ++stg) {
-        int rc = launch_history_integrals(v, v.Y, 0.0, true, v.S, grid_ctas, s);
+        const double* row = v.Y + (size_t)(stg & 1) * 2 * v.L;
+        int rc = launch_history_integrals(v, row, 0.0, true, v.S, grid_ctas, s);
         if (rc) return rc;
-        k_stage_end<<<1, CTL_THREADS, 0, s>>>(v, stg);
+        k_stage_end<<<g, kCtlThreads, 0, s>>>(v, stg, prep_blocks);
     }
     return launch_sparsify(v, true, 0.0, s);
 }
