@@ -34,11 +34,19 @@ COEFS = {3: 0.25, 4: 0.25}
 T_BATH = 0.5
 GRID_T_MAX = 1e5
 TOL = 1e-8
-# Algorithmic FP64 operations per (i, j) pair of the FP64 kernel at stencil width 4,
-# counted from the source (FMA = 2): interpolation weights 3 x 16, A1 4 x 4 FMA, A2
-# 2 x 4 FMA, B1 2 x 4 FMA, B2 2 x 4 x 4 FMA + 2 x 4 FMA Hermite + 14 time weights,
-# f' and f'' at two points (10 FMA), nine products and sums (27).
-FLOP_PER_PAIR_S4 = 48 + 32 + 16 + 16 + 64 + 16 + 14 + 20 + 27
+# Algorithmic operations per (i, j) pair at stencil width 4, counted from the kernel
+# source (FMA = 2 flops). FP64 kernel: Lagrange weights 3 x 20, A1 32, A2 16, B1 16,
+# B2 (time weights 23, two 4-point stencils of 4 fields 64, Hermite combination 14),
+# f' and f'' at two points for the (3+4) model 20, nine products and sums 30.
+FLOP_PER_PAIR_S4 = 60 + 32 + 16 + 16 + 101 + 20 + 30
+# Double-float kernel, FP32 flops of the double-float arithmetic: weights 3 x 118,
+# B1 110, A1 220, A2 110, B2 713, f' and f'' 210, products and sums 226.
+DF_FP32_FLOP_PER_PAIR_S4 = 354 + 110 + 220 + 110 + 713 + 210 + 226
+# Nominal per-GPU peaks derived from the unit counts and the 2.07 GHz maximum SM clock:
+# FP64 1.25 TFLOP/s (2 FMA lanes per SM); FP32 152 SMs x 128 lanes x 2 x 2.07e9.
+FP64_PEAK_GFLOPS = 1250.0
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
+LAUNCHES_PER_STEP = 24  # step graph (begin, 6 x [prep, integrals, stage end], 4 sparsify) + begin
 
 
 def parse():
@@ -52,6 +60,8 @@ def parse():
     ap.add_argument("--kernel-only", action="store_true",
                     help="only launch the history-integral kernel (for profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the double-float and FP32-compensated variants of the same workload")
     return ap.parse_args()
 
 
@@ -253,6 +263,41 @@ def cpu_baseline(L, rows=512):
                       "scaled to all rows and 6 stages per step" % (rows, L, el)}
 
 
+DTYPES = {"fp64": "f64", "fp32": "f32+f64", "df": "f32x2 (double-float)+f64"}
+VARIANT_NAMES = {"fp64": "fp64", "df": "double_float", "fp32": "fp32_compensated"}
+
+
+def roofline(precision, res):
+    hbm, src = peaks()
+    bh, bt, bio = res["bytes"]
+    k = res["k_avg"]
+    pairs = res["pairs"]
+    if precision == "fp64":
+        ach = pairs * FLOP_PER_PAIR_S4 / k / 1e9
+        return {"kernel": "k_hi_f64 (history integrals)", "bound": "alu", "achieved": ach,
+                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": ach / FP64_PEAK_GFLOPS, "traffic": None,
+                "peak_source": "nominal FP64 (unit counts x clock)", "algorithmic_bytes": bh + bt + bio,
+                "hbm_frac_of_%s" % src: (bh + bt + bio) / k / 1e9 / hbm, "kernel_ms": k * 1e3}
+    if precision == "df":
+        ach = pairs * DF_FP32_FLOP_PER_PAIR_S4 / k / 1e9
+        return {"kernel": "k_hi_df (history integrals)", "bound": "alu", "achieved": ach,
+                "peak": FP32_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": ach / FP32_PEAK_GFLOPS, "traffic": None,
+                "peak_source": "nominal FP32 (unit counts x clock)", "algorithmic_bytes": bh + bt + bio,
+                "fp64_equivalent_gflops": pairs * FLOP_PER_PAIR_S4 / k / 1e9,
+                "hbm_frac_of_%s" % src: (bh + bt + bio) / k / 1e9 / hbm, "kernel_ms": k * 1e3}
+    ach = (bh + bt + bio) / k / 1e9
+    return {"kernel": "k_hi_f32 (history integrals)", "bound": "hbm", "achieved": ach, "peak": hbm,
+            "unit": "GB/s", "frac": ach / hbm, "traffic": None, "peak_source": src,
+            "algorithmic_bytes": bh + bt + bio, "history_bytes": bh, "table_bytes": bt, "kernel_ms": k * 1e3}
+
+
+def solver_info(res):
+    return dict({k2: res["stats"][k2] for k2 in ("t", "steps_accepted", "steps_rejected", "sparsify_passes",
+                                                 "slices_removed", "forced_removals", "n_slices", "dt",
+                                                 "last_eps")},
+                state_prepared_by_steps=res["setup_steps"], autotuned_unit=res["chunk"])
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -292,35 +337,28 @@ def main():
     if rank != 0:
         return
     value = world * args.steps / dev_time
-    hbm, src = peaks()
-    bh, bt, bio = res["bytes"]
-    k = res["k_avg"]
     L = args.L
-    if args.precision in ("fp64", "df"):
-        flops = res["pairs"] * FLOP_PER_PAIR_S4
-        fp64_peak = 1250.0  # GFLOP/s, nominal GB300 FP64 (derived peak)
-        roof = {"kernel": "k_hi_%s (history integrals)" % ("f64" if args.precision == "fp64" else "df"),
-                "bound": "alu", "achieved": flops / k / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
-                "frac": flops / k / 1e9 / fp64_peak, "traffic": None,
-                "peak_source": "nominal FP64 1.25 TFLOP/s", "algorithmic_bytes": bh + bt + bio,
-                "hbm_frac_of_%s" % src: (bh + bt + bio) / k / 1e9 / hbm, "kernel_ms": k * 1e3}
-    else:
-        ach = (bh + bt + bio) / k / 1e9
-        roof = {"kernel": "k_hi_f32 (history integrals)", "bound": "hbm", "achieved": ach, "peak": hbm,
-                "unit": "GB/s", "frac": ach / hbm, "traffic": None, "peak_source": src,
-                "algorithmic_bytes": bh + bt + bio, "history_bytes": bh, "table_bytes": bt, "kernel_ms": k * 1e3}
+    roof = roofline(args.precision, res)
     line = {"metric": "RK steps/s", "value": value, "unit": "RK steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dev_time / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32+f64", "df": "f32x2 (double-float)+f64"}[args.precision],
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision],
             "data": "synthetic", "config": cfg,
             "e2e": {"value": world * args.steps / e2e_time, "unit": "RK steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 2 * L * 8 + 3 * 8},
-            "gpu_launches": args.steps * 18,
-            "roofline": roof, "clocks": res["clocks"],
-            "solver": dict({k2: res["stats"][k2] for k2 in ("t", "steps_accepted", "steps_rejected",
-                                                             "sparsify_passes", "slices_removed", "forced_removals",
-                                                             "n_slices", "dt", "last_eps")},
-                           state_prepared_by_steps=res["setup_steps"], autotuned_unit=res["chunk"])}
+            "gpu_launches": args.steps * LAUNCHES_PER_STEP,
+            "roofline": roof, "clocks": res["clocks"], "solver": solver_info(res)}
+    if not args.no_variants and world == 1:
+        variants = {}
+        for prec in ("df", "fp32", "fp64"):
+            if prec == args.precision:
+                continue
+            a2 = argparse.Namespace(**vars(args))
+            a2.precision = prec
+            r2 = run_ours(a2, rank, world)
+            variants[VARIANT_NAMES[prec]] = {
+                "value": args.steps / r2["dev_time"], "e2e": args.steps / r2["e2e_time"], "unit": "RK steps/s",
+                "dtype": DTYPES[prec], "roofline": roofline(prec, r2), "solver": solver_info(r2)}
+        line["variants"] = variants
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(L)
     print(json.dumps(line))

@@ -190,6 +190,36 @@ int dmfe_autotune(dmfe_solver* h, int* chunk);
 /* Synchronise the solver's stream and return the device status word. */
 int dmfe_sync(dmfe_solver* h);
 
+/* ---- batched and served solves ------------------------------------------------------
+ * A batch runs many independent solves (one per slot) with one CUDA graph per
+ * Dormand-Prince step: each stage is one persistent history-integral launch over the
+ * units of every active slot (the slots may have different L, history caps, f, T and
+ * t_max), plus batched control kernels. Slots read a batch table in device memory, so
+ * slots can be added and removed between steps without re-capturing the graph
+ * (continuous batching). A slot's results are bitwise identical to the same solve run
+ * alone with the same work-unit size. All slots share the batch's precision and stencil
+ * width. Every solve owns its device memory; a slot is a dmfe_solver. */
+typedef struct dmfe_batch dmfe_batch;
+/* max_slots <= 256; max_L, max_cap bound the slots' L and history_cap (they size the
+ * shared-memory tables of the batched kernels). stream as in dmfe_params. */
+int dmfe_batch_create(int max_slots, int max_L, int max_cap, int precision, int s, void* stream,
+                      dmfe_batch** out);
+void dmfe_batch_destroy(dmfe_batch* b);
+/* Admit a solve into a free slot: creates its solver (allocates; synchronous), targets
+ * t_max with tolerance tol. *slot receives the slot. DMFE_ERR_CAPACITY: no free slot;
+ * DMFE_ERR_ARG: parameters outside the batch's bounds or precision/stencil mismatch. */
+int dmfe_batch_add(dmfe_batch* b, const dmfe_params* p, double t_max, double tol, int* slot);
+/* Release a slot (synchronises, frees its solver). */
+int dmfe_batch_remove(dmfe_batch* b, int slot);
+/* The solver of a slot (NULL if free), for dmfe_get_C/R, dmfe_get_row, dmfe_stats. */
+dmfe_solver* dmfe_batch_solver(dmfe_batch* b, int slot);
+/* Launch nsteps batched steps on the batch stream without synchronising. */
+int dmfe_batch_step(dmfe_batch* b, int nsteps);
+/* Synchronise and read every slot: status[k] (0, DMFE_ERR_*, or 1 = reached t_max; -100
+ * for a free slot) and t[k] (arrays of max_slots, may be NULL). Finished and failed slots
+ * stop receiving work. *running receives the number of slots still integrating. */
+int dmfe_batch_poll(dmfe_batch* b, int* status, double* t, int* running);
+
 /* ---- allocation-free entry point -------------------------------------------------
  * The paper has no counterpart: this serves callers of the library that cannot call
  * cudaMalloc -- processes whose device memory another framework has reserved up front,

@@ -283,6 +283,14 @@ double last_time(dmfe_solver* h) { return h->hstate->t; }
 
 }  // namespace
 
+const SolverView& solver_view(const dmfe_solver* h) { return h->v; }
+
+int solver_read_state(dmfe_solver* h, DevState* out) {
+    TRY(read_state(h));
+    *out = *h->hstate;
+    return DMFE_OK;
+}
+
 extern "C" {
 
 void dmfe_default_params(dmfe_params* p) {

@@ -1,0 +1,224 @@
+// Batched solves: a table of slots in device memory, one captured graph per batched
+// Dormand-Prince step (launch_batch_step), admission and release of slots between steps.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "dmfe_internal.h"
+#include "hi_units.h"
+
+struct dmfe_batch {
+    int max_slots = 0, max_L = 0, max_cap = 0, precision = 0, s = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<dmfe_solver*> slots;
+    std::vector<int> finished;  // 1: done or failed (no more work)
+    BatchTable* h_table = nullptr;  // pinned
+    BatchTable* d_table = nullptr;
+    bool dirty = true;
+    cudaGraphExec_t exec = nullptr;
+    int hi_grid = 0;
+    size_t hi_smem = 0;
+    DevState* h_state = nullptr;  // pinned, one per slot
+};
+
+namespace {
+
+#define TRYB(x)                \
+    do {                       \
+        int rc_ = (x);         \
+        if (rc_) return rc_;   \
+    } while (0)
+
+void rebuild_table(dmfe_batch* b) {
+    BatchTable& t = *b->h_table;
+    int count = 0;
+    for (int k = 0; k < b->max_slots; ++k)
+        if (b->slots[k]) count = k + 1;
+    t.count = count;
+    long long off = 0;
+    for (int k = 0; k < b->max_slots; ++k) {
+        t.uoff[k] = off;
+        dmfe_solver* h = b->slots[k];
+        t.active[k] = h ? 1 : 0;
+        if (h) {
+            const SolverView& v = solver_view(h);
+            t.views[k] = v;
+            if (!b->finished[k]) off += (long long)hi_parts(v.L, v.hi_chunk) * v.L;
+        }
+    }
+    t.uoff[b->max_slots] = off;
+    for (int k = count; k <= b->max_slots && k > 0; ++k) t.uoff[k] = off;
+    b->dirty = true;
+}
+
+int upload_table(dmfe_batch* b) {
+    if (!b->dirty) return DMFE_OK;
+    DMFE_CUDA_TRY(cudaMemcpyAsync(b->d_table, b->h_table, sizeof(BatchTable), cudaMemcpyHostToDevice, b->stream));
+    b->dirty = false;
+    return DMFE_OK;
+}
+
+int build_graph(dmfe_batch* b) {
+    if (b->exec) return DMFE_OK;
+    cudaGraph_t g = nullptr;
+    DMFE_CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = launch_batch_step(b->d_table, b->precision, b->s, b->max_L, b->max_cap, b->max_slots,
+                                     b->hi_grid, b->hi_smem, b->cap_stream);
+    const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+    if (rc || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc ? rc : DMFE_ERR_CUDA;
+    }
+    const cudaError_t e2 = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+        b->exec = nullptr;
+        cudaGetLastError();
+        return DMFE_ERR_CUDA;
+    }
+    return DMFE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dmfe_batch_create(int max_slots, int max_L, int max_cap, int precision, int s, void* stream,
+                      dmfe_batch** out) {
+    if (!out) return DMFE_ERR_ARG;
+    *out = nullptr;
+    if (max_slots < 1 || max_slots > kMaxSlots || max_L < 16 || max_L > 8192 || max_cap < 16) return DMFE_ERR_ARG;
+    if (precision != DMFE_FP64 && precision != DMFE_FP32_COMPENSATED && precision != DMFE_DOUBLE_FLOAT)
+        return DMFE_ERR_ARG;
+    dmfe_batch* b = new (std::nothrow) dmfe_batch();
+    if (!b) return DMFE_ERR_OOM;
+    b->max_slots = max_slots;
+    b->max_L = max_L;
+    b->max_cap = max_cap;
+    b->precision = precision;
+    b->s = s;
+    b->slots.assign(max_slots, nullptr);
+    b->finished.assign(max_slots, 0);
+    int rc = batch_hi_config(precision, s, max_L, max_cap, &b->hi_grid, &b->hi_smem);
+    if (!rc) {
+        if (stream) {
+            b->stream = (cudaStream_t)stream;
+        } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess) {
+            b->own_stream = true;
+        } else {
+            rc = DMFE_ERR_CUDA;
+        }
+    }
+    if (!rc && cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) rc = DMFE_ERR_CUDA;
+    if (!rc && cudaMallocHost((void**)&b->h_table, sizeof(BatchTable)) != cudaSuccess) rc = DMFE_ERR_OOM;
+    if (!rc && cudaMallocHost((void**)&b->h_state, sizeof(DevState) * max_slots) != cudaSuccess) rc = DMFE_ERR_OOM;
+    if (!rc && cudaMalloc((void**)&b->d_table, sizeof(BatchTable)) != cudaSuccess) rc = DMFE_ERR_OOM;
+    if (rc) {
+        cudaGetLastError();
+        dmfe_batch_destroy(b);
+        return rc;
+    }
+    std::memset(b->h_table, 0, sizeof(BatchTable));
+    rebuild_table(b);
+    *out = b;
+    return DMFE_OK;
+}
+
+void dmfe_batch_destroy(dmfe_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (dmfe_solver* h : b->slots)
+        if (h) dmfe_destroy(h);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->d_table) cudaFree(b->d_table);
+    if (b->h_table) cudaFreeHost(b->h_table);
+    if (b->h_state) cudaFreeHost(b->h_state);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+int dmfe_batch_add(dmfe_batch* b, const dmfe_params* p, double t_max, double tol, int* slot) {
+    if (!b || !p) return DMFE_ERR_ARG;
+    const int cap = p->history_cap ? p->history_cap : p->L;
+    if (p->precision != b->precision || p->s != b->s || p->L > b->max_L || cap > b->max_cap) return DMFE_ERR_ARG;
+    if (!(tol > 0.0) || !(t_max <= p->grid_t_max * (1.0 + 1e-12))) return DMFE_ERR_ARG;
+    int k = 0;
+    while (k < b->max_slots && b->slots[k]) ++k;
+    if (k == b->max_slots) return DMFE_ERR_CAPACITY;
+    dmfe_params q = *p;
+    q.stream = b->stream;
+    dmfe_solver* h = nullptr;
+    TRYB(dmfe_create(&q, &h));
+    const int rc = launch_begin_integrate(solver_view(h), t_max, tol, b->stream);
+    if (rc) {
+        dmfe_destroy(h);
+        return rc;
+    }
+    b->slots[k] = h;
+    b->finished[k] = 0;
+    rebuild_table(b);
+    if (slot) *slot = k;
+    return DMFE_OK;
+}
+
+int dmfe_batch_remove(dmfe_batch* b, int slot) {
+    if (!b || slot < 0 || slot >= b->max_slots || !b->slots[slot]) return DMFE_ERR_ARG;
+    DMFE_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    dmfe_destroy(b->slots[slot]);
+    b->slots[slot] = nullptr;
+    b->finished[slot] = 0;
+    rebuild_table(b);
+    return DMFE_OK;
+}
+
+dmfe_solver* dmfe_batch_solver(dmfe_batch* b, int slot) {
+    if (!b || slot < 0 || slot >= b->max_slots) return nullptr;
+    return b->slots[slot];
+}
+
+int dmfe_batch_step(dmfe_batch* b, int nsteps) {
+    if (!b || nsteps < 0) return DMFE_ERR_ARG;
+    TRYB(upload_table(b));
+    TRYB(build_graph(b));
+    for (int it = 0; it < nsteps; ++it) DMFE_CUDA_TRY(cudaGraphLaunch(b->exec, b->stream));
+    return DMFE_OK;
+}
+
+int dmfe_batch_poll(dmfe_batch* b, int* status, double* t, int* running) {
+    if (!b) return DMFE_ERR_ARG;
+    for (int k = 0; k < b->max_slots; ++k)
+        if (b->slots[k])
+            DMFE_CUDA_TRY(cudaMemcpyAsync(&b->h_state[k], solver_view(b->slots[k]).st, sizeof(DevState),
+                                          cudaMemcpyDeviceToHost, b->stream));
+    DMFE_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    int run = 0;
+    bool changed = false;
+    for (int k = 0; k < b->max_slots; ++k) {
+        int st = -100;
+        double tk = 0.0;
+        if (b->slots[k]) {
+            const DevState& d = b->h_state[k];
+            tk = d.t;
+            st = d.status ? d.status : (d.done ? 1 : 0);
+            const int fin = st != 0;
+            if (fin != b->finished[k]) {
+                b->finished[k] = fin;
+                changed = true;
+            }
+            if (!fin) ++run;
+        }
+        if (status) status[k] = st;
+        if (t) t[k] = tk;
+    }
+    if (changed) rebuild_table(b);
+    if (running) *running = run;
+    return DMFE_OK;
+}
+
+}  // extern "C"

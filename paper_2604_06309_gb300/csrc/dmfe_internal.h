@@ -141,6 +141,17 @@ struct SolverView {
     int* newidx;          // [cap]
 };
 
+// Batch table (device memory): the slots of a batch, read by the batched kernels of one
+// captured step graph; the host rewrites it between graph launches when slots change.
+constexpr int kMaxSlots = 256;
+struct BatchTable {
+    int count;                      // slots 0 .. count-1 are examined
+    int pad;
+    long long uoff[kMaxSlots + 1];  // history-integral unit offsets (0 units: idle slot)
+    int active[kMaxSlots];          // 1: slot holds a solver
+    SolverView views[kMaxSlots];
+};
+
 static const int FIX_FRAC_BITS = 19;  // x = packed / 2^19
 constexpr int kPrepThreads = 128;     // block size of the per-stage prep kernel
 constexpr int kMaxPrepBlocks = (8192 + kPrepThreads - 1) / kPrepThreads;
@@ -169,6 +180,19 @@ int launch_stage_prep(const SolverView& v, const double* row_dev, double t, bool
 int launch_history_integrals_df(const SolverView& v, const double* row_dev, double t, bool from_state,
                                 double* S_dev, int grid_ctas, cudaStream_t s);
 int hi_config_df(const SolverView& v, int* grid_ctas, size_t* smem);
+
+// ---- batched execution (batch.cu and the kernel files) ----
+int batch_hi_config(int precision, int sw, int max_L, int max_cap, int* grid_ctas, size_t* smem);
+int batch_hi_config_df(int sw, int max_L, int max_cap, int* grid_ctas, size_t* smem);
+int launch_batch_hi(const BatchTable* bt, int precision, int sw, int stg, int grid, size_t smem, cudaStream_t s);
+int launch_batch_hi_df(const BatchTable* bt, int sw, int stg, int grid, size_t smem, cudaStream_t s);
+int launch_batch_prep(const BatchTable* bt, int stg, int max_tot, int slots, cudaStream_t s);
+int launch_batch_step(const BatchTable* bt, int precision, int sw, int max_L, int max_cap, int slots,
+                      int hi_grid, size_t hi_smem, cudaStream_t s);
+// accessors of a solver's internals (api.cu)
+struct dmfe_solver;
+const SolverView& solver_view(const dmfe_solver* h);
+int solver_read_state(dmfe_solver* h, DevState* out);
 
 // ---- host grid (host_grid.cpp) ----
 double host_gamma_from_tmax(double t_max);

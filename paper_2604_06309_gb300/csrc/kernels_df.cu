@@ -33,7 +33,8 @@ __device__ __forceinline__ int find_slice_g(const double* ht, int n, double tau)
 
 // Per-stage preparation (all precisions): the cell -> slice table, the B1 time weights of
 // every output index, and for the double-float path the stage row and slice constants.
-__global__ void k_stage_prep(SolverView v, const double* __restrict__ row, double t_arg, int from_state) {
+__device__ __forceinline__ void stage_prep_body(const SolverView& v, const double* __restrict__ row, double t_arg,
+                                                int from_state) {
     const DevState* st = v.st;
     if (from_state && (st->status != 0 || st->done)) return;
     const int L = v.L, n = st->n, act = st->active;
@@ -187,8 +188,8 @@ __device__ __forceinline__ double warp_sum_d(double x) {
 }
 
 template <int SW>
-__global__ void __launch_bounds__(DF_THREADS, 1) k_hi_df(SolverView v, double t_arg, int from_state,
-                                                         double* __restrict__ S) {
+__device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, int from_state, double* __restrict__ S,
+                                           int ub, int ue) {
     extern __shared__ __align__(32) unsigned char smraw[];
     const DevState* st = v.st;
     if (from_state && (st->status != 0 || st->done)) return;
@@ -228,8 +229,6 @@ __global__ void __launch_bounds__(DF_THREADS, 1) k_hi_df(SolverView v, double t_
     const int d1 = v.poly.deg1, d2 = v.poly.deg2;
 
     const int chunk = v.hi_chunk;
-    int ub, ue;
-    hi_unit_block(L, chunk, &ub, &ue);
     for (int u_ = ub + (threadIdx.x >> 5); u_ < ue; u_ += DF_WARPS) {
         int j, i0, i1;
         hi_unit_range(u_, L, chunk, &j, &i0, &i1);
@@ -416,6 +415,44 @@ __global__ void __launch_bounds__(DF_THREADS, 1) k_hi_df(SolverView v, double t_
     }
 }
 
+__global__ void k_stage_prep(SolverView v, const double* __restrict__ row, double t_arg, int from_state) {
+    stage_prep_body(v, row, t_arg, from_state);
+}
+
+template <int SW>
+__global__ void __launch_bounds__(DF_THREADS, 1) k_hi_df(SolverView v, double t_arg, int from_state,
+                                                         double* __restrict__ S) {
+    int ub, ue;
+    hi_unit_block(v.L, v.hi_chunk, &ub, &ue);
+    hi_df_body<SW>(v, t_arg, from_state, S, ub, ue);
+}
+
+// Batched versions (see kernels_hi.cu): prep over (element block, slot), integrals over
+// the concatenated unit space of the batch table.
+__global__ void k_batch_prep(const BatchTable* __restrict__ bt, int stg) {
+    const int k = blockIdx.y;
+    if (k >= bt->count || !bt->active[k]) return;
+    const SolverView& v = bt->views[k];
+    stage_prep_body(v, v.Y + (size_t)(stg & 1) * 2 * v.L, 0.0, 1);
+}
+
+template <int SW>
+__global__ void __launch_bounds__(DF_THREADS, 1) k_batch_hi_df(const BatchTable* __restrict__ bt, int stg) {
+    const long long U = bt->uoff[bt->count];
+    const long long gb = U * blockIdx.x / gridDim.x, ge = U * (blockIdx.x + 1) / gridDim.x;
+    int k = 0;
+    while (k < bt->count && bt->uoff[k + 1] <= gb) ++k;
+    for (; k < bt->count && bt->uoff[k] < ge; ++k) {
+        const long long o = bt->uoff[k];
+        const int lb = (int)((gb > o ? gb : o) - o);
+        const int le = (int)((ge < bt->uoff[k + 1] ? ge : bt->uoff[k + 1]) - o);
+        if (le <= lb) continue;
+        const SolverView& v = bt->views[k];
+        __syncthreads();  // the previous slot's shared-memory tables are no longer read
+        hi_df_body<SW>(v, 0.0, 1, v.S, lb, le);
+    }
+}
+
 size_t df_smem_bytes(const SolverView& v) {
     return (size_t)v.L * sizeof(dfrow) + (size_t)v.cap * (2 * sizeof(df) + sizeof(float)) +
            (size_t)v.L * sizeof(uint16_t) + 16;
@@ -471,5 +508,52 @@ int launch_history_integrals_df(const SolverView& v, const double* row_dev, doub
     const size_t sm = df_smem_bytes(v);
     void* args[] = {(void*)&v, (void*)&t, (void*)&fs, (void*)&S_dev};
     DMFE_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid_ctas), dim3(DF_THREADS), args, sm, s));
+    return DMFE_OK;
+}
+
+int batch_hi_config_df(int sw, int max_L, int max_cap, int* grid_ctas, size_t* smem) {
+    SolverView v{};
+    v.L = max_L;
+    v.cap = max_cap;
+    v.s = sw;
+    void* fn = nullptr;
+    switch (sw) {
+        case 4: fn = (void*)k_batch_hi_df<4>; break;
+        case 6: fn = (void*)k_batch_hi_df<6>; break;
+        case 8: fn = (void*)k_batch_hi_df<8>; break;
+        case 10: fn = (void*)k_batch_hi_df<10>; break;
+        default: return DMFE_ERR_UNSUPPORTED;
+    }
+    if (max_L > 65535) return DMFE_ERR_UNSUPPORTED;
+    const size_t sm = df_smem_bytes(v);
+    int dev = 0, max_optin = 0, nsm = 0;
+    DMFE_CUDA_TRY(cudaGetDevice(&dev));
+    DMFE_CUDA_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    DMFE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (sm > (size_t)max_optin) return DMFE_ERR_UNSUPPORTED;
+    DMFE_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int per_sm = 0;
+    DMFE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, DF_THREADS, sm));
+    if (per_sm < 1) return DMFE_ERR_UNSUPPORTED;
+    *grid_ctas = nsm * per_sm;
+    *smem = sm;
+    return DMFE_OK;
+}
+
+int launch_batch_hi_df(const BatchTable* bt, int sw, int stg, int grid, size_t smem, cudaStream_t s) {
+    switch (sw) {
+        case 4: k_batch_hi_df<4><<<grid, DF_THREADS, smem, s>>>(bt, stg); break;
+        case 6: k_batch_hi_df<6><<<grid, DF_THREADS, smem, s>>>(bt, stg); break;
+        case 8: k_batch_hi_df<8><<<grid, DF_THREADS, smem, s>>>(bt, stg); break;
+        case 10: k_batch_hi_df<10><<<grid, DF_THREADS, smem, s>>>(bt, stg); break;
+        default: return DMFE_ERR_UNSUPPORTED;
+    }
+    DMFE_CUDA_TRY(cudaGetLastError());
+    return DMFE_OK;
+}
+
+int launch_batch_prep(const BatchTable* bt, int stg, int max_tot, int slots, cudaStream_t s) {
+    k_batch_prep<<<dim3((max_tot + kPrepThreads - 1) / kPrepThreads, slots), kPrepThreads, 0, s>>>(bt, stg);
+    DMFE_CUDA_TRY(cudaGetLastError());
     return DMFE_OK;
 }

@@ -112,9 +112,11 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // ------------------------------------------------------------------ FP64 variant
+// Body shared by the single-instance and batched kernels: processes units [ub, ue) of
+// solver v with the warps of this CTA (shared memory is reloaded for v).
 template <int SW>
-__global__ void __launch_bounds__(HI_THREADS, 1) k_hi_f64(SolverView v, const double* __restrict__ row,
-                                                       double t_arg, int from_state, double* __restrict__ S) {
+__device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* __restrict__ row, double t_arg,
+                                            int from_state, double* __restrict__ S, int ub, int ue) {
     extern __shared__ __align__(32) unsigned char smraw[];
     const DevState* st = v.st;
     if (from_state && (st->status != 0 || st->done)) return;
@@ -142,8 +144,6 @@ __global__ void __launch_bounds__(HI_THREADS, 1) k_hi_f64(SolverView v, const do
     const double* __restrict__ omega = v.omega;
     const double* __restrict__ nu = v.nu;
     const int chunk = v.hi_chunk;
-    int ub, ue;
-    hi_unit_block(L, chunk, &ub, &ue);
 
     for (int u = ub + (threadIdx.x >> 5); u < ue; u += HI_WARPS) {
         int j, i0, i1;
@@ -274,8 +274,8 @@ struct Kahan {
 };
 
 template <int SW>
-__global__ void __launch_bounds__(HI_THREADS, 1) k_hi_f32(SolverView v, const double* __restrict__ row,
-                                                       double t_arg, int from_state, double* __restrict__ S) {
+__device__ __forceinline__ void hi_f32_body(const SolverView& v, const double* __restrict__ row, double t_arg,
+                                            int from_state, double* __restrict__ S, int ub, int ue) {
     extern __shared__ __align__(32) unsigned char smraw[];
     const DevState* st = v.st;
     if (from_state && (st->status != 0 || st->done)) return;
@@ -317,8 +317,6 @@ __global__ void __launch_bounds__(HI_THREADS, 1) k_hi_f32(SolverView v, const do
     const float* __restrict__ nu32 = v.nu32;
     const float fscale = 1.0f / (float)(1u << FIX_FRAC_BITS);
     const int chunk = v.hi_chunk;
-    int ub, ue;
-    hi_unit_block(L, chunk, &ub, &ue);
 
     for (int u = ub + (threadIdx.x >> 5); u < ue; u += HI_WARPS) {
         int j, i0, i1;
@@ -456,6 +454,43 @@ __global__ void __launch_bounds__(HI_THREADS, 1) k_hi_f32(SolverView v, const do
     }
 }
 
+template <int SW>
+__global__ void __launch_bounds__(HI_THREADS, 1) k_hi_f64(SolverView v, const double* __restrict__ row,
+                                                       double t_arg, int from_state, double* __restrict__ S) {
+    int ub, ue;
+    hi_unit_block(v.L, v.hi_chunk, &ub, &ue);
+    hi_f64_body<SW>(v, row, t_arg, from_state, S, ub, ue);
+}
+
+template <int SW>
+__global__ void __launch_bounds__(HI_THREADS, 1) k_hi_f32(SolverView v, const double* __restrict__ row,
+                                                       double t_arg, int from_state, double* __restrict__ S) {
+    int ub, ue;
+    hi_unit_block(v.L, v.hi_chunk, &ub, &ue);
+    hi_f32_body<SW>(v, row, t_arg, from_state, S, ub, ue);
+}
+
+// Batched: one persistent launch per stage over the units of every slot of the batch
+// table; each CTA takes a contiguous range of the concatenated unit space.
+template <int SW, int PREC>
+__global__ void __launch_bounds__(HI_THREADS, 1) k_batch_hi(const BatchTable* __restrict__ bt, int stg) {
+    const long long U = bt->uoff[bt->count];
+    const long long gb = U * blockIdx.x / gridDim.x, ge = U * (blockIdx.x + 1) / gridDim.x;
+    int k = 0;
+    while (k < bt->count && bt->uoff[k + 1] <= gb) ++k;
+    for (; k < bt->count && bt->uoff[k] < ge; ++k) {
+        const long long o = bt->uoff[k];
+        const int lb = (int)((gb > o ? gb : o) - o);
+        const int le = (int)((ge < bt->uoff[k + 1] ? ge : bt->uoff[k + 1]) - o);
+        if (le <= lb) continue;
+        const SolverView& v = bt->views[k];
+        const double* row = v.Y + (size_t)(stg & 1) * 2 * v.L;
+        __syncthreads();  // the previous slot's shared-memory tables are no longer read
+        if (PREC == DMFE_FP64) hi_f64_body<SW>(v, row, 0.0, 1, v.S, lb, le);
+        else hi_f32_body<SW>(v, row, 0.0, 1, v.S, lb, le);
+    }
+}
+
 size_t hi_smem_bytes(const SolverView& v) {
     if (v.precision == DMFE_FP64)
         return (size_t)v.L * sizeof(dbl4) + (size_t)v.cap * sizeof(double) + (size_t)v.L * sizeof(int);
@@ -514,5 +549,54 @@ int launch_history_integrals(const SolverView& v, const double* row_dev, double 
     int fs = from_state ? 1 : 0;
     void* args[] = {(void*)&v, (void*)&row_dev, (void*)&t, (void*)&fs, (void*)&S_dev};
     DMFE_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid_ctas), dim3(HI_THREADS), args, sm, s));
+    return DMFE_OK;
+}
+
+// ---- batched launchers
+int batch_hi_config(int precision, int sw, int max_L, int max_cap, int* grid_ctas, size_t* smem) {
+    if (precision == DMFE_DOUBLE_FLOAT) return batch_hi_config_df(sw, max_L, max_cap, grid_ctas, smem);
+    SolverView v{};
+    v.L = max_L;
+    v.cap = max_cap;
+    v.precision = precision;
+    v.s = sw;
+    const size_t sm = hi_smem_bytes(v);
+    void* fn = nullptr;
+    switch (sw) {
+        case 4: fn = precision == DMFE_FP64 ? (void*)k_batch_hi<4, DMFE_FP64> : (void*)k_batch_hi<4, DMFE_FP32_COMPENSATED>; break;
+        case 6: fn = precision == DMFE_FP64 ? (void*)k_batch_hi<6, DMFE_FP64> : (void*)k_batch_hi<6, DMFE_FP32_COMPENSATED>; break;
+        case 8: fn = precision == DMFE_FP64 ? (void*)k_batch_hi<8, DMFE_FP64> : (void*)k_batch_hi<8, DMFE_FP32_COMPENSATED>; break;
+        case 10: fn = precision == DMFE_FP64 ? (void*)k_batch_hi<10, DMFE_FP64> : (void*)k_batch_hi<10, DMFE_FP32_COMPENSATED>; break;
+        default: return DMFE_ERR_UNSUPPORTED;
+    }
+    int dev = 0, max_optin = 0, nsm = 0;
+    DMFE_CUDA_TRY(cudaGetDevice(&dev));
+    DMFE_CUDA_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    DMFE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (sm > (size_t)max_optin) return DMFE_ERR_UNSUPPORTED;
+    DMFE_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int per_sm = 0;
+    DMFE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, HI_THREADS, sm));
+    if (per_sm < 1) return DMFE_ERR_UNSUPPORTED;
+    *grid_ctas = nsm * per_sm;
+    *smem = sm;
+    return DMFE_OK;
+}
+
+int launch_batch_hi(const BatchTable* bt, int precision, int sw, int stg, int grid, size_t smem, cudaStream_t s) {
+    if (precision == DMFE_DOUBLE_FLOAT) return launch_batch_hi_df(bt, sw, stg, grid, smem, s);
+    const bool f64 = precision == DMFE_FP64;
+    switch (sw) {
+        case 4: if (f64) k_batch_hi<4, DMFE_FP64><<<grid, HI_THREADS, smem, s>>>(bt, stg);
+                else k_batch_hi<4, DMFE_FP32_COMPENSATED><<<grid, HI_THREADS, smem, s>>>(bt, stg); break;
+        case 6: if (f64) k_batch_hi<6, DMFE_FP64><<<grid, HI_THREADS, smem, s>>>(bt, stg);
+                else k_batch_hi<6, DMFE_FP32_COMPENSATED><<<grid, HI_THREADS, smem, s>>>(bt, stg); break;
+        case 8: if (f64) k_batch_hi<8, DMFE_FP64><<<grid, HI_THREADS, smem, s>>>(bt, stg);
+                else k_batch_hi<8, DMFE_FP32_COMPENSATED><<<grid, HI_THREADS, smem, s>>>(bt, stg); break;
+        case 10: if (f64) k_batch_hi<10, DMFE_FP64><<<grid, HI_THREADS, smem, s>>>(bt, stg);
+                 else k_batch_hi<10, DMFE_FP32_COMPENSATED><<<grid, HI_THREADS, smem, s>>>(bt, stg); break;
+        default: return DMFE_ERR_UNSUPPORTED;
+    }
+    DMFE_CUDA_TRY(cudaGetLastError());
     return DMFE_OK;
 }

@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(CTL_THREADS) k_begin_integrate(SolverView v, d
 
 // Start of a trial step (multi-CTA): h = min(dt, t_target - t), k_1 = stored derivative of
 // the last slice (first-same-as-last), stage-1 row Y_1 = y + h a_10 k_1 into buffer 1.
-__global__ void __launch_bounds__(kCtlThreads) k_step_begin(SolverView v) {
+__device__ __forceinline__ void step_begin_body(const SolverView& v, int cta, int ncta) {
     DevState* st = v.st;
     if (gated(st)) return;
     const int L = v.L;
@@ -228,14 +228,14 @@ __global__ void __launch_bounds__(kCtlThreads) k_step_begin(SolverView v) {
     const double t = st->t;
     const double h = fmin(st->dt, st->t_target - t);
     double* Y1 = v.Y + 2 * (size_t)L;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < L; j += gridDim.x * blockDim.x) {
+    for (int j = cta * blockDim.x + threadIdx.x; j < L; j += ncta * blockDim.x) {
         const dbl4 e = yrow[j];
         v.k[j] = e.y;
         v.k[L + j] = e.w;
         Y1[j] = __dadd_rn(e.x, __dmul_rn(h, __dmul_rn(kDP_A[1][0], e.y)));
         Y1[L + j] = __dadd_rn(e.z, __dmul_rn(h, __dmul_rn(kDP_A[1][0], e.w)));
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (cta == 0 && threadIdx.x == 0) {
         st->h = h;
         st->t_stage = __dadd_rn(t, __dmul_rn(kDP_C[1], h));
     }
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(kCtlThreads) k_step_begin(SolverView v) {
 // after the last stage, the error estimate, whose per-CTA partials the last CTA to
 // finish adds in a fixed order before taking the step decision of Sec. 3.5 and
 // appending the slice. mu and E come from the per-block partial sums of the prep kernel.
-__global__ void __launch_bounds__(kCtlThreads) k_stage_end(SolverView v, int stg, int prep_blocks) {
+__device__ __forceinline__ void stage_end_body(const SolverView& v, int stg, int prep_blocks, int cta, int ncta) {
     __shared__ double s_mu, s_E, red[kCtlThreads];
     __shared__ int s_last, s_append;
     DevState* st = v.st;
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kCtlThreads) k_stage_end(SolverView v, int stg
     const double mu = s_mu;
     double* kC = v.k + (size_t)stg * L2;
     double pe = 0.0;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < L; j += gridDim.x * blockDim.x) {
+    for (int j = cta * blockDim.x + threadIdx.x; j < L; j += ncta * blockDim.x) {
         const double th = v.theta[j], om = v.omega[j];
         const double C = Yc[j], R = Yc[L + j];
         const double* sj = v.S + j;
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kCtlThreads) k_stage_end(SolverView v, int stg
         }
     }
     if (stg < 6) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (cta == 0 && threadIdx.x == 0) {
             st->stages += 1;
             st->t_stage = __dadd_rn(t, __dmul_rn(kDP_C[stg + 1], h));
         }
@@ -317,16 +317,16 @@ __global__ void __launch_bounds__(kCtlThreads) k_stage_end(SolverView v, int stg
     }
     const double ep = block_sum(pe, red);
     if (threadIdx.x == 0) {
-        v.epart[blockIdx.x] = ep;
+        v.epart[cta] = ep;
         __threadfence();
-        s_last = atomicAdd(v.ctl_count, 1) == (int)gridDim.x - 1;
+        s_last = atomicAdd(v.ctl_count, 1) == ncta - 1;
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
     if (threadIdx.x == 0) {
         double eps = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) eps += __ldcg(&v.epart[b]);
+        for (int b = 0; b < ncta; ++b) eps += __ldcg(&v.epart[b]);
         *v.ctl_count = 0;
         st->stages += 1;
         st->eps = eps;
@@ -371,6 +371,35 @@ __global__ void __launch_bounds__(kCtlThreads) k_stage_end(SolverView v, int stg
     }
 }
 
+__device__ __forceinline__ int ctl_grid(int L) {
+    const int g = (L + kCtlThreads - 1) / kCtlThreads;
+    return g < 1 ? 1 : (g > kCtlGrid ? kCtlGrid : g);
+}
+
+__global__ void __launch_bounds__(kCtlThreads) k_step_begin(SolverView v) { step_begin_body(v, blockIdx.x, gridDim.x); }
+
+__global__ void __launch_bounds__(kCtlThreads) k_stage_end(SolverView v, int stg, int prep_blocks) {
+    stage_end_body(v, stg, prep_blocks, blockIdx.x, gridDim.x);
+}
+
+// Batched wrappers: blockIdx.y is the slot; each slot keeps its own CTA partition.
+__global__ void __launch_bounds__(kCtlThreads) k_batch_step_begin(const BatchTable* __restrict__ bt) {
+    const int k = blockIdx.y;
+    if (k >= bt->count || !bt->active[k]) return;
+    const SolverView& v = bt->views[k];
+    const int g = ctl_grid(v.L);
+    if ((int)blockIdx.x < g) step_begin_body(v, blockIdx.x, g);
+}
+
+__global__ void __launch_bounds__(kCtlThreads) k_batch_stage_end(const BatchTable* __restrict__ bt, int stg) {
+    const int k = blockIdx.y;
+    if (k >= bt->count || !bt->active[k]) return;
+    const SolverView& v = bt->views[k];
+    const int g = ctl_grid(v.L);
+    const int tot = v.L > v.cap ? v.L : v.cap;
+    if ((int)blockIdx.x < g) stage_end_body(v, stg, (tot + kPrepThreads - 1) / kPrepThreads, blockIdx.x, g);
+}
+
 // ---------------------------------------------------------------- sparsification
 __device__ __forceinline__ double herm_int(double y0, double d0, double y1, double d1, double h) {
     return 0.5 * h * (y0 + y1) + h * h * (d0 - d1) / 12.0;
@@ -381,7 +410,7 @@ __device__ __forceinline__ bool sp_active(const DevState* st, int from_step) {
 }
 
 // eps_sparse(n) for candidates n = 1 .. N-12: one warp per candidate.
-__global__ void k_sp_residual(SolverView v, int from_step) {
+__device__ __forceinline__ void sp_residual_body(const SolverView& v, int from_step, int cta, int ncta) {
     const DevState* st = v.st;
     if (!sp_active(st, from_step)) return;
     const int L = v.L;
@@ -391,8 +420,8 @@ __global__ void k_sp_residual(SolverView v, int from_step) {
     const dbl4* H = v.hist[act];
     const double* ht = v.ht[act];
     const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x * (blockDim.x >> 5);
-    for (int n = 1 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); n <= last; n += nw) {
+    const int nw = ncta * (blockDim.x >> 5);
+    for (int n = 1 + cta * (blockDim.x >> 5) + (threadIdx.x >> 5); n <= last; n += nw) {
         const double h1 = ht[n] - ht[n - 1], h2 = ht[n + 1] - ht[n];
         const dbl4* a = H + (size_t)(n - 1) * L;
         const dbl4* b = H + (size_t)n * L;
@@ -415,7 +444,7 @@ __global__ void k_sp_residual(SolverView v, int from_step) {
 // Greedy scan of Sec. 3.6 (remove n if eps < tol/10, then skip n+1), forced removal of the
 // smallest residual when nothing qualifies, and the compaction map. Single thread: the
 // scan is sequential by definition and runs once per pass.
-__global__ void k_sp_select(SolverView v, int from_step, double tol_arg) {
+__device__ __forceinline__ void sp_select_body(const SolverView& v, int from_step, double tol_arg) {
     DevState* st = v.st;
     if (!sp_active(st, from_step) || threadIdx.x != 0) return;
     const int N = st->n;
@@ -461,15 +490,14 @@ __global__ void k_sp_select(SolverView v, int from_step, double tol_arg) {
     st->sp_ran = 1;
 }
 
-__global__ void k_sp_compact(SolverView v) {
+__device__ __forceinline__ void sp_compact_body(const SolverView& v, int cta, int ncta) {
     const DevState* st = v.st;
     if (!st->sp_ran) return;
     const int L = v.L;
     const int N = st->n;
     const int act = st->active, nxt = 1 - act;
     const long long tot = (long long)N * L;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < tot;
-         q += (long long)gridDim.x * blockDim.x) {
+    for (long long q = cta * (long long)blockDim.x + threadIdx.x; q < tot; q += (long long)ncta * blockDim.x) {
         const int k = (int)(q / L), i = (int)(q % L);
         if (!v.keep[k]) continue;
         const size_t dst = (size_t)v.newidx[k] * L + i;
@@ -480,7 +508,7 @@ __global__ void k_sp_compact(SolverView v) {
     }
 }
 
-__global__ void __launch_bounds__(CTL_THREADS) k_sp_finish(SolverView v) {
+__device__ __forceinline__ void sp_finish_body(const SolverView& v) {
     DevState* st = v.st;
     if (!st->sp_ran) return;
     __syncthreads();
@@ -500,6 +528,32 @@ __global__ void __launch_bounds__(CTL_THREADS) k_sp_finish(SolverView v) {
             if (st->t >= st->t_target) st->done = 1;
         }
     }
+}
+
+__global__ void k_sp_residual(SolverView v, int from_step) { sp_residual_body(v, from_step, blockIdx.x, gridDim.x); }
+__global__ void k_sp_select(SolverView v, int from_step, double tol_arg) { sp_select_body(v, from_step, tol_arg); }
+__global__ void k_sp_compact(SolverView v) { sp_compact_body(v, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(CTL_THREADS) k_sp_finish(SolverView v) { sp_finish_body(v); }
+
+__global__ void k_batch_sp_residual(const BatchTable* __restrict__ bt) {
+    const int k = blockIdx.y;
+    if (k >= bt->count || !bt->active[k]) return;
+    sp_residual_body(bt->views[k], 1, blockIdx.x, gridDim.x);
+}
+__global__ void k_batch_sp_select(const BatchTable* __restrict__ bt) {
+    const int k = blockIdx.x;
+    if (k >= bt->count || !bt->active[k]) return;
+    sp_select_body(bt->views[k], 1, 0.0);
+}
+__global__ void k_batch_sp_compact(const BatchTable* __restrict__ bt) {
+    const int k = blockIdx.y;
+    if (k >= bt->count || !bt->active[k]) return;
+    sp_compact_body(bt->views[k], blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(CTL_THREADS) k_batch_sp_finish(const BatchTable* __restrict__ bt) {
+    const int k = blockIdx.x;
+    if (k >= bt->count || !bt->active[k]) return;
+    sp_finish_body(bt->views[k]);
 }
 
 // ---------------------------------------------------------------- lookups
@@ -630,6 +684,29 @@ int launch_lookup(const SolverView& v, int n, const double* t, const double* tp,
 int launch_refresh_replica(const SolverView& v, cudaStream_t s) {
     if (!v.hist32[0] && !v.histdf[0]) return DMFE_OK;
     k_refresh_replica<<<grid_for((long long)v.cap * v.L, 256), 256, 0, s>>>(v);
+    DMFE_CUDA_TRY(cudaGetLastError());
+    return DMFE_OK;
+}
+
+// One batched Dormand-Prince step over every active slot of the batch table: the same
+// kernels as launch_step, with blockIdx.y (or blockIdx.x for per-slot kernels) the slot.
+int launch_batch_step(const BatchTable* bt, int precision, int sw, int max_L, int max_cap, int slots,
+                      int hi_grid, size_t hi_smem, cudaStream_t s) {
+    int g = (max_L + kCtlThreads - 1) / kCtlThreads;
+    g = g < 1 ? 1 : (g > kCtlGrid ? kCtlGrid : g);
+    const int max_tot = max_L > max_cap ? max_L : max_cap;
+    k_batch_step_begin<<<dim3(g, slots), kCtlThreads, 0, s>>>(bt);
+    for (int stg = 1; stg <= 6; ++stg) {
+        int rc = launch_batch_prep(bt, stg, max_tot, slots, s);
+        if (rc) return rc;
+        rc = launch_batch_hi(bt, precision, sw, stg, hi_grid, hi_smem, s);
+        if (rc) return rc;
+        k_batch_stage_end<<<dim3(g, slots), kCtlThreads, 0, s>>>(bt, stg);
+    }
+    k_batch_sp_residual<<<dim3((max_cap + 7) / 8, slots), 256, 0, s>>>(bt);
+    k_batch_sp_select<<<slots, 32, 0, s>>>(bt);
+    k_batch_sp_compact<<<dim3(64, slots), 256, 0, s>>>(bt);
+    k_batch_sp_finish<<<slots, CTL_THREADS, 0, s>>>(bt);
     DMFE_CUDA_TRY(cudaGetLastError());
     return DMFE_OK;
 }

@@ -76,6 +76,13 @@ _SIGS = {
     "dmfe_restore": (_i, [ctypes.c_char_p, _p, ctypes.POINTER(_p)]),
     "dmfe_sync": (_i, [_p]),
     "dmfe_autotune": (_i, [_p, _ip]),
+    "dmfe_batch_create": (_i, [_i, _i, _i, _i, _i, _p, ctypes.POINTER(_p)]),
+    "dmfe_batch_destroy": (None, [_p]),
+    "dmfe_batch_add": (_i, [_p, ctypes.POINTER(dmfe_params), _d, _d, _ip]),
+    "dmfe_batch_remove": (_i, [_p, _i]),
+    "dmfe_batch_solver": (_p, [_p, _i]),
+    "dmfe_batch_step": (_i, [_p, _i]),
+    "dmfe_batch_poll": (_i, [_p, _ip, _dp, _ip]),
     "dmfe_sparsify_select_noalloc": (_i, [_p, _p, _p, _p, _p, _i, _i, _d, _p, _p]),
 }
 
@@ -121,6 +128,88 @@ def _f64(a, n=None):
     return a
 
 
+def make_params(coefs, T, L, grid_t_max, s=4, beta0=0.0, alpha=0.0, delta=0.0, history_cap=None, dt0=1e-4,
+                dt_min=1e-12, precision="fp64", sparsify=True, stream=None):
+    """A dmfe_params structure; the returned tuple keeps the coefficient arrays alive."""
+    lib = load()
+    terms = sorted((int(p), float(c)) for p, c in dict(coefs).items())
+    pw = (ctypes.c_int * len(terms))(*[p for p, _ in terms])
+    cf = (ctypes.c_double * len(terms))(*[c for _, c in terms])
+    prm = dmfe_params()
+    lib.dmfe_default_params(ctypes.byref(prm))
+    prm.n_terms = len(terms)
+    prm.powers = ctypes.cast(pw, _ip)
+    prm.coefs = ctypes.cast(cf, _dp)
+    prm.T, prm.beta0, prm.L, prm.s = T, beta0, L, s
+    prm.grid_t_max, prm.alpha, prm.delta = grid_t_max, alpha, delta
+    prm.history_cap = int(history_cap) if history_cap else L
+    prm.dt0, prm.dt_min = dt0, dt_min
+    prm.precision = PRECISIONS[precision]
+    prm.sparsify = 1 if sparsify else 0
+    prm.stream = stream
+    return prm, (pw, cf)
+
+
+class Batch:
+    """A dmfe_batch: many independent solves stepped together (continuous batching)."""
+
+    def __init__(self, max_slots, max_L, max_cap, precision="fp64", s=4, stream=None):
+        self._lib = load()
+        self.h = _p()
+        self.max_slots = max_slots
+        _check(self._lib.dmfe_batch_create(max_slots, max_L, max_cap, PRECISIONS[precision], s, stream,
+                                           ctypes.byref(self.h)), "dmfe_batch_create")
+        self.precision, self.s = precision, s
+
+    def add(self, coefs, T, L, grid_t_max, t_max, tol, **kw):
+        prm, keep = make_params(coefs, T, L, grid_t_max, s=self.s, precision=self.precision, **kw)
+        slot = _i()
+        _check(self._lib.dmfe_batch_add(self.h, ctypes.byref(prm), float(t_max), float(tol), ctypes.byref(slot)),
+               "dmfe_batch_add")
+        return slot.value
+
+    def remove(self, slot):
+        _check(self._lib.dmfe_batch_remove(self.h, int(slot)), "dmfe_batch_remove")
+
+    def solver(self, slot):
+        """Non-owning Solver view of a slot (valid until the slot is removed)."""
+        h = self._lib.dmfe_batch_solver(self.h, int(slot))
+        if not h:
+            raise ValueError("slot %d is free" % slot)
+        return Solver._from_handle(h, owned=False)
+
+    def step(self, nsteps):
+        _check(self._lib.dmfe_batch_step(self.h, int(nsteps)), "dmfe_batch_step")
+
+    def poll(self):
+        """(status[max_slots], t[max_slots], running): status 0 running, 1 done, < 0 error, -100 free."""
+        st = (ctypes.c_int * self.max_slots)()
+        tt = np.empty(self.max_slots)
+        run = _i()
+        _check(self._lib.dmfe_batch_poll(self.h, ctypes.cast(st, _ip), _ptr(tt), ctypes.byref(run)),
+               "dmfe_batch_poll")
+        return np.array(st[:], dtype=int), tt, run.value
+
+    def run(self, poll_every=16):
+        """Step until no slot is running."""
+        while True:
+            self.step(poll_every)
+            _, _, running = self.poll()
+            if running == 0:
+                return
+
+    def close(self):
+        if self.h:
+            self._lib.dmfe_batch_destroy(self.h)
+            self.h = _p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Solver:
     """A dmfe_solver handle. coefs: {power: coefficient} for f(q) = sum c_p q^p."""
 
@@ -130,21 +219,10 @@ class Solver:
         lib = load()
         self._lib = lib
         self.h = _p()
-        terms = sorted((int(p), float(c)) for p, c in dict(coefs).items())
-        pw = (ctypes.c_int * len(terms))(*[p for p, _ in terms])
-        cf = (ctypes.c_double * len(terms))(*[c for _, c in terms])
-        prm = dmfe_params()
-        lib.dmfe_default_params(ctypes.byref(prm))
-        prm.n_terms = len(terms)
-        prm.powers = ctypes.cast(pw, _ip)
-        prm.coefs = ctypes.cast(cf, _dp)
-        prm.T, prm.beta0, prm.L, prm.s = T, beta0, L, s
-        prm.grid_t_max, prm.alpha, prm.delta = grid_t_max, alpha, delta
-        prm.history_cap = int(history_cap) if history_cap else L
-        prm.dt0, prm.dt_min = dt0, dt_min
-        prm.precision = PRECISIONS[precision]
-        prm.sparsify = 1 if sparsify else 0
-        prm.stream = stream
+        self._owned = True
+        prm, keep = make_params(coefs, T, L, grid_t_max, s=s, beta0=beta0, alpha=alpha, delta=delta,
+                                history_cap=history_cap, dt0=dt0, dt_min=dt_min, precision=precision,
+                                sparsify=sparsify, stream=stream)
         _check(lib.dmfe_create(ctypes.byref(prm), ctypes.byref(self.h)), "dmfe_create")
         self._sizes()
 
@@ -154,6 +232,15 @@ class Solver:
         th, om, nu = (np.empty(self.L) for _ in range(3))
         _check(self._lib.dmfe_grid(self.h, _ptr(th), _ptr(om), _ptr(nu)), "dmfe_grid")
         self.theta, self.omega, self.nu = th, om, nu
+
+    @classmethod
+    def _from_handle(cls, h, owned):
+        obj = cls.__new__(cls)
+        obj._lib = load()
+        obj.h = _p(h)
+        obj._owned = owned
+        obj._sizes()
+        return obj
 
     @classmethod
     def restore(cls, path, stream=None):
@@ -166,9 +253,9 @@ class Solver:
         return obj
 
     def close(self):
-        if self.h:
+        if self.h and getattr(self, "_owned", True):
             self._lib.dmfe_destroy(self.h)
-            self.h = _p()
+        self.h = _p()
 
     def __del__(self):
         try:
