@@ -60,6 +60,12 @@ def parse():
     ap.add_argument("--kernel-only", action="store_true",
                     help="only launch the history-integral kernel (for profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="step", choices=["step", "batch", "serve"],
+                    help="step: the headline configuration; batch: 256 independent solves stepped "
+                         "together; serve: Poisson-arrival requests with continuous batching")
+    ap.add_argument("--window", type=float, default=30.0, help="seconds of batched or served work")
+    ap.add_argument("--slots", type=int, default=256)
+    ap.add_argument("--batch-max-L", type=int, default=4097, help="largest grid of the batch mix")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the double-float and FP32-compensated variants of the same workload")
     return ap.parse_args()
@@ -298,6 +304,143 @@ def solver_info(res):
                 state_prepared_by_steps=res["setup_steps"], autotuned_unit=res["chunk"])
 
 
+BATCH_LS = (129, 257, 513, 1025, 2049, 4097)
+
+
+def batch_requests(n, seed=20260406, Ls=BATCH_LS, tmax_range=(1e3, 1e6)):
+    """Seeded parameter sweep: T ~ U[0.3, 1], lambda ~ U[0, 1], L = cap ~ U(Ls), t_max log-uniform."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        T = rng.uniform(0.3, 1.0)
+        lam = rng.uniform(0.0, 1.0)
+        L = int(rng.choice(Ls))
+        tmax = float(np.exp(rng.uniform(np.log(tmax_range[0]), np.log(tmax_range[1]))))
+        out.append({"coefs": {3: 0.5 * lam, 4: 0.5 * (1.0 - lam)}, "T": T, "L": L, "t_max": tmax})
+    return out
+
+
+def run_batch(args):
+    """Config 4: all requests in one batch, stepped for a fixed wall-clock window."""
+    import torch
+    from paper_2604_06309_gb300 import Batch, Solver
+    reqs = batch_requests(args.slots, Ls=tuple(L for L in BATCH_LS if L <= args.batch_max_L))
+    maxL = max(r["L"] for r in reqs)
+    stream = torch.cuda.Stream()
+    res = {}
+    with torch.cuda.stream(stream):
+        b = Batch(args.slots, maxL, maxL, precision=args.precision, stream=stream.cuda_stream)
+        t0 = time.perf_counter()
+        for r in reqs:
+            b.add(r["coefs"], r["T"], r["L"], r["t_max"], r["t_max"], TOL, history_cap=r["L"])
+        admit_s = time.perf_counter() - t0
+        b.step(2)  # warm-up (graph capture, first touches)
+        b.poll()
+        st0 = [b.solver(k).stats() for k in range(len(reqs))]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+        e0.record(stream)
+        tw = time.perf_counter()
+        nsteps = 0
+        while time.perf_counter() - tw < args.window:
+            b.step(1)
+            nsteps += 1
+            if nsteps % 4 == 0:
+                b.poll()
+        e1.record(stream)
+        e1.synchronize()
+        clk = clocks.stop()
+        dev_s = e0.elapsed_time(e1) * 1e-3
+        status, tcur, running = b.poll()
+        st1 = [b.solver(k).stats() for k in range(len(reqs))]
+        stages = sum(a["stages"] - z["stages"] for a, z in zip(st1, st0))
+        pairs = sum((a["stages"] - z["stages"]) * r["L"] ** 2 for a, z, r in zip(st1, st0, reqs))
+        completed = int(sum(1 for x in status[:len(reqs)] if x == 1))
+        failed = int(sum(1 for x in status[:len(reqs)] if -100 < x < 0))
+        res = {"batched_steps": nsteps, "device_s": dev_s, "instance_stages_per_s": stages / dev_s,
+               "pair_evals_per_s": pairs / dev_s, "completed": completed, "failed": failed,
+               "completed_solves_per_s": completed / dev_s, "admission_s": admit_s, "clocks": clk,
+               "max_t_reached": float(np.max(tcur[:len(reqs)]))}
+        b.close()
+        # one at a time on the same GPU, FP64: stage time of a single solve per grid size
+        single = {}
+        for L in sorted(set(r["L"] for r in reqs)):
+            sv = Solver(MIX_FOR_SINGLE, 0.5, L, 1e5, history_cap=L, precision="fp64", stream=stream.cuda_stream)
+            sv.step(3, 1e5, TOL, stream.cuda_stream)
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            sv.step(8, 1e5, TOL, stream.cuda_stream)
+            a1.record(stream)
+            a1.synchronize()
+            single[L] = a0.elapsed_time(a1) * 1e-3 / (8 * 6)
+            sv.close()
+        t_single = sum(single[r["L"]] for r in reqs)          # seconds for one stage of every solve
+        res["single_fp64_instance_stages_per_s"] = len(reqs) / t_single
+        res["gain_vs_single_fp64"] = res["instance_stages_per_s"] / res["single_fp64_instance_stages_per_s"]
+        res["single_fp64_stage_ms"] = {str(L): 1e3 * v for L, v in single.items()}
+    return res
+
+
+MIX_FOR_SINGLE = {3: 0.25, 4: 0.25}
+SERVE_LS = (65, 129, 257)
+
+
+def run_serving(args, rate=20.0, seed=20260406):
+    """Config 5 scaled so that a few-minute run reaches a steady state: Poisson arrivals of
+    (3+4)-spin requests (T~U[0.3,1], lambda~U[0,1], L~U{65,129,257}, t_max~logU[10,100]),
+    admitted by device footprint into a continuously stepped batch."""
+    import torch
+    from paper_2604_06309_gb300 import Server, footprint
+    rng = np.random.default_rng(seed)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.5 * free)
+    srv = Server(args.slots, max(SERVE_LS), max(SERVE_LS), precision=args.precision, hbm_budget=budget,
+                 steps_per_round=4)
+    reqs = batch_requests(100000, seed=seed + 1, Ls=SERVE_LS, tmax_range=(10.0, 100.0))
+    t0 = time.perf_counter()
+    next_arrival = rng.exponential(1.0 / rate)
+    submitted, results, peak_bytes, samples = 0, [], 0, []
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    while True:
+        now = time.perf_counter() - t0
+        if now >= args.window:
+            break
+        while next_arrival <= now and submitted < len(reqs):
+            r = reqs[submitted]
+            srv.submit(r["coefs"], r["T"], r["L"], r["t_max"], r["t_max"], TOL, history_cap=r["L"])
+            submitted += 1
+            next_arrival += rng.exponential(1.0 / rate)
+        results += srv.poll()
+        st = srv.stats()
+        peak_bytes = max(peak_bytes, st["bytes_in_use"])
+        samples.append((now, st["running"], st["queued"]))
+        time.sleep(0.002)
+    clk = clocks.stop()
+    st = srv.stats()
+    results += srv.poll()
+    srv.stop()
+    ok = [r for r in results if r["status"] == 0]
+    lat = np.array([r["done_s"] - r["submit_s"] for r in ok]) if ok else np.array([np.nan])
+    wait = np.array([r["admit_s"] - r["submit_s"] for r in ok]) if ok else np.array([np.nan])
+    second_half = [r for r in ok if r["done_s"] > args.window / 2]
+    return {"metric": "served solves/s", "value": len(ok) / args.window, "unit": "solves/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": DTYPES[args.precision], "data": "synthetic",
+            "config": {"workload": "Poisson arrivals %.0f req/s of (3+4)-spin solves, T~U[0.3,1], lambda~U[0,1], "
+                                   "L=cap~U{%s}, t_max~logU[10,100], tol 1e-8, seed %d, continuous batching"
+                                   % (rate, ",".join(map(str, SERVE_LS)), seed),
+                       "window_s": args.window, "max_slots": args.slots, "hbm_budget_bytes": budget},
+            "serve": {"submitted": submitted, "completed": len(ok), "failed": st["failed"],
+                      "queued_at_end": st["queued"], "running_at_end": st["running"],
+                      "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                      "p50_queue_wait_s": float(np.percentile(wait, 50)),
+                      "solves_per_s_second_half": len(second_half) / (args.window / 2),
+                      "mean_running": float(np.mean([x[1] for x in samples])) if samples else 0.0,
+                      "peak_hbm_bytes": peak_bytes, "hbm_utilisation_of_total": peak_bytes / total,
+                      "batched_steps": st["batched_steps"]},
+            "clocks": clk}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -321,6 +464,20 @@ def main():
         print(json.dumps(line))
         return
 
+    if args.workload == "batch":
+        r = run_batch(args)
+        line = {"metric": "instance-stages/s", "value": r["instance_stages_per_s"], "unit": "instance-stages/s",
+                "n_gpus": 1, "higher_is_better": True, "dtype": DTYPES[args.precision], "data": "synthetic",
+                "config": {"workload": "%d independent (3+4)-spin solves, T~U[0.3,1], lambda~U[0,1], L=cap~U{%s}, "
+                                       "t_max~logU[1e3,1e6], tol 1e-8, seed 20260406, one persistent launch per "
+                                       "stage, graph per batched step" % (args.slots, ",".join(map(str, BATCH_LS))),
+                           "window_s": args.window},
+                "batch": r}
+        print(json.dumps(line))
+        return
+    if args.workload == "serve":
+        print(json.dumps(run_serving(args)))
+        return
     import torch
     if world > 1:
         torch.distributed.init_process_group("nccl")

@@ -220,6 +220,40 @@ int dmfe_batch_step(dmfe_batch* b, int nsteps);
  * stop receiving work. *running receives the number of slots still integrating. */
 int dmfe_batch_poll(dmfe_batch* b, int* status, double* t, int* running);
 
+/* Device bytes a solver with these parameters allocates (dmfe_create), rounded up the way
+ * large device allocations are; used for admission by footprint. 0 on invalid input. */
+unsigned long long dmfe_footprint(const dmfe_params* p);
+
+/* A serving loop over a batch (continuous batching): a host worker thread admits queued
+ * requests first-in first-out into free slots while the summed footprint stays within
+ * hbm_budget bytes, steps the batch steps_per_round steps at a time, and retires every
+ * solve that reaches its t_max or fails, recording its latency. */
+typedef struct dmfe_server dmfe_server;
+typedef struct {
+    long long id;
+    int       status;                  /* 0: reached t_max; < 0: DMFE_ERR_* of the solve    */
+    int       slot;
+    double    t_final, E, mu;          /* last slice: time, energy, Lagrange multiplier     */
+    double    submit_s, admit_s, done_s; /* seconds since the server started               */
+    long long steps_accepted, steps_rejected;
+} dmfe_result;
+typedef struct {
+    long long submitted, admitted, completed, failed;
+    int       queued, running;
+    unsigned long long bytes_in_use, hbm_budget;
+    long long batched_steps;
+} dmfe_server_stats_t;
+int dmfe_server_start(int max_slots, int max_L, int max_cap, int precision, int s,
+                      unsigned long long hbm_budget, int steps_per_round, dmfe_server** out);
+/* Queue a request (parameters copied; thread-safe). *id receives its id. DMFE_ERR_ARG if
+ * it can never be admitted (bounds, precision, footprint above the budget). */
+int dmfe_server_submit(dmfe_server* srv, const dmfe_params* p, double t_max, double tol, long long* id);
+/* Move up to max_out finished results into out (thread-safe); *n receives the count. */
+int dmfe_server_poll(dmfe_server* srv, dmfe_result* out, int max_out, int* n);
+int dmfe_server_stats(dmfe_server* srv, dmfe_server_stats_t* out);
+/* Stop the worker (running solves are abandoned) and free everything. */
+int dmfe_server_stop(dmfe_server* srv);
+
 /* ---- allocation-free entry point -------------------------------------------------
  * The paper has no counterpart: this serves callers of the library that cannot call
  * cudaMalloc -- processes whose device memory another framework has reserved up front,

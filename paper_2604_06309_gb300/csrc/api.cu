@@ -323,6 +323,43 @@ const char* dmfe_strerror(int code) {
     return "unknown error";
 }
 
+// Mirrors the allocations of create_impl (keep the two in step).
+unsigned long long dmfe_footprint(const dmfe_params* pin) {
+    if (!pin) return 0;
+    dmfe_params p = *pin;
+    if (p.history_cap == 0) p.history_cap = p.L;
+    if (validate(&p)) return 0;
+    const unsigned long long L = p.L, cap = p.history_cap, LL = L * L;
+    unsigned long long tot = 0;
+    auto add = [&tot](unsigned long long b) {
+        const unsigned long long g = b >= (2ull << 20) ? (2ull << 20) : 512ull;
+        tot += (b + g - 1) / g * g;
+    };
+    for (int k = 0; k < 3; ++k) add(L * 8);
+    add(L * 4); add(L * 4);
+    if (p.precision == DMFE_FP64) {
+        for (int k = 0; k < 3; ++k) add(LL * 8);
+    } else if (p.precision == DMFE_FP32_COMPENSATED) {
+        for (int k = 0; k < 3; ++k) add(LL * 4);
+    } else {
+        for (int k = 0; k < 3; ++k) add(LL * sizeof(df));
+        add(L * sizeof(df)); add(L * sizeof(df)); add(L * sizeof(dfrow)); add(cap * sizeof(dfslice)); add(L * 4);
+    }
+    for (int b = 0; b < 2; ++b) {
+        add(cap * 8);
+        add(cap * L * sizeof(dbl4));
+        if (p.precision == DMFE_FP32_COMPENSATED) add(cap * L * sizeof(float4));
+        if (p.precision == DMFE_DOUBLE_FLOAT) add(cap * L * sizeof(df8));
+    }
+    add(sizeof(DevState)); add(4 * L * 8);
+    add(2ull * kMaxPrepBlocks * 8); add(kCtlGrid * 8); add(4);
+    add(14 * L * 8); add(2 * L * 8); add(DMFE_NS * L * 8);
+    add((L / kMinChunk > 1 ? L / kMinChunk : 1) * 9 * L * 8); add(L * sizeof(B1Desc));
+    if (p.precision != DMFE_DOUBLE_FLOAT) add(L * 4);
+    add(L * 4); add(cap * 8); add(cap * 4); add(cap * 4); add((4 * L + 16) * 8);
+    return tot;
+}
+
 int dmfe_create(const dmfe_params* pin, dmfe_solver** out) {
     if (!out) return DMFE_ERR_ARG;
     *out = nullptr;

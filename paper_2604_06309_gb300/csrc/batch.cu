@@ -39,19 +39,27 @@ void rebuild_table(dmfe_batch* b) {
     for (int k = 0; k < b->max_slots; ++k)
         if (b->slots[k]) count = k + 1;
     t.count = count;
-    long long off = 0;
+    long long off = 0, woff = 0;
     for (int k = 0; k < b->max_slots; ++k) {
         t.uoff[k] = off;
+        t.woff[k] = woff;
         dmfe_solver* h = b->slots[k];
         t.active[k] = h ? 1 : 0;
         if (h) {
             const SolverView& v = solver_view(h);
             t.views[k] = v;
-            if (!b->finished[k]) off += (long long)hi_parts(v.L, v.hi_chunk) * v.L;
+            if (!b->finished[k]) {
+                off += (long long)hi_parts(v.L, v.hi_chunk) * v.L;
+                woff += (long long)v.L * v.L;
+            }
         }
     }
     t.uoff[b->max_slots] = off;
-    for (int k = count; k <= b->max_slots && k > 0; ++k) t.uoff[k] = off;
+    t.woff[b->max_slots] = woff;
+    for (int k = count; k <= b->max_slots && k > 0; ++k) {
+        t.uoff[k] = off;
+        t.woff[k] = woff;
+    }
     b->dirty = true;
 }
 

@@ -148,6 +148,7 @@ struct BatchTable {
     int count;                      // slots 0 .. count-1 are examined
     int pad;
     long long uoff[kMaxSlots + 1];  // history-integral unit offsets (0 units: idle slot)
+    long long woff[kMaxSlots + 1];  // work (pair) offsets: CTAs split the batch by work
     int active[kMaxSlots];          // 1: slot holds a solver
     SolverView views[kMaxSlots];
 };

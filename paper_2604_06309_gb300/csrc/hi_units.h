@@ -62,3 +62,31 @@ __device__ __forceinline__ void hi_finish_unit(const double (&sums)[9], double c
         jcount[j] = 0;
     }
 }
+
+// Copy a slot's view into shared memory (the batched kernels read it for every pair;
+// from shared memory those reads are broadcasts instead of global loads).
+__device__ __forceinline__ void load_view(SolverView& dst, const SolverView& src) {
+    static_assert(sizeof(SolverView) % 4 == 0, "view size");
+    const int* s = reinterpret_cast<const int*>(&src);
+    int* d = reinterpret_cast<int*>(&dst);
+    for (int q = threadIdx.x; q < (int)(sizeof(SolverView) / 4); q += blockDim.x) d[q] = s[q];
+}
+
+// Work-balanced share of a batch for this CTA: the pairs of all slots are split evenly
+// over the CTAs and each slot's share is mapped to its units in proportion (a slot's
+// units carry nearly equal work). Calls f(k, lb, le) for every slot k with units [lb, le).
+template <typename F>
+__device__ __forceinline__ void batch_for_my_units(const BatchTable* bt, F&& f) {
+    const long long W = bt->woff[bt->count];
+    const long long g0 = W * blockIdx.x / gridDim.x, g1 = W * (blockIdx.x + 1) / gridDim.x;
+    int k = 0;
+    while (k < bt->count && bt->woff[k + 1] <= g0) ++k;
+    for (; k < bt->count && bt->woff[k] < g1; ++k) {
+        const long long o = bt->woff[k], Wk = bt->woff[k + 1] - o;
+        if (Wk <= 0) continue;
+        const long long Uk = bt->uoff[k + 1] - bt->uoff[k];
+        const long long a = (g0 > o ? g0 : o) - o, e = (g1 < o + Wk ? g1 : o + Wk) - o;
+        const int lb = (int)(a * Uk / Wk), le = (int)(e * Uk / Wk);
+        if (le > lb) f(k, lb, le);
+    }
+}

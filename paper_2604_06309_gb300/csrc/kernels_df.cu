@@ -438,19 +438,13 @@ __global__ void k_batch_prep(const BatchTable* __restrict__ bt, int stg) {
 
 template <int SW>
 __global__ void __launch_bounds__(DF_THREADS, 1) k_batch_hi_df(const BatchTable* __restrict__ bt, int stg) {
-    const long long U = bt->uoff[bt->count];
-    const long long gb = U * blockIdx.x / gridDim.x, ge = U * (blockIdx.x + 1) / gridDim.x;
-    int k = 0;
-    while (k < bt->count && bt->uoff[k + 1] <= gb) ++k;
-    for (; k < bt->count && bt->uoff[k] < ge; ++k) {
-        const long long o = bt->uoff[k];
-        const int lb = (int)((gb > o ? gb : o) - o);
-        const int le = (int)((ge < bt->uoff[k + 1] ? ge : bt->uoff[k + 1]) - o);
-        if (le <= lb) continue;
-        const SolverView& v = bt->views[k];
-        __syncthreads();  // the previous slot's shared-memory tables are no longer read
-        hi_df_body<SW>(v, 0.0, 1, v.S, lb, le);
-    }
+    __shared__ __align__(16) SolverView sview;
+    batch_for_my_units(bt, [&](int k, int lb, int le) {
+        __syncthreads();  // the previous slot's shared-memory data are no longer read
+        load_view(sview, bt->views[k]);
+        __syncthreads();
+        hi_df_body<SW>(sview, 0.0, 1, sview.S, lb, le);
+    });
 }
 
 size_t df_smem_bytes(const SolverView& v) {

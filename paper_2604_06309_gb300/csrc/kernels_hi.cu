@@ -471,24 +471,19 @@ __global__ void __launch_bounds__(HI_THREADS, 1) k_hi_f32(SolverView v, const do
 }
 
 // Batched: one persistent launch per stage over the units of every slot of the batch
-// table; each CTA takes a contiguous range of the concatenated unit space.
+// table; each CTA takes an equal share of the batch's pairs (batch_for_my_units).
 template <int SW, int PREC>
 __global__ void __launch_bounds__(HI_THREADS, 1) k_batch_hi(const BatchTable* __restrict__ bt, int stg) {
-    const long long U = bt->uoff[bt->count];
-    const long long gb = U * blockIdx.x / gridDim.x, ge = U * (blockIdx.x + 1) / gridDim.x;
-    int k = 0;
-    while (k < bt->count && bt->uoff[k + 1] <= gb) ++k;
-    for (; k < bt->count && bt->uoff[k] < ge; ++k) {
-        const long long o = bt->uoff[k];
-        const int lb = (int)((gb > o ? gb : o) - o);
-        const int le = (int)((ge < bt->uoff[k + 1] ? ge : bt->uoff[k + 1]) - o);
-        if (le <= lb) continue;
-        const SolverView& v = bt->views[k];
+    __shared__ __align__(16) SolverView sview;
+    batch_for_my_units(bt, [&](int k, int lb, int le) {
+        __syncthreads();  // the previous slot's shared-memory data are no longer read
+        load_view(sview, bt->views[k]);
+        __syncthreads();
+        const SolverView& v = sview;
         const double* row = v.Y + (size_t)(stg & 1) * 2 * v.L;
-        __syncthreads();  // the previous slot's shared-memory tables are no longer read
         if (PREC == DMFE_FP64) hi_f64_body<SW>(v, row, 0.0, 1, v.S, lb, le);
         else hi_f32_body<SW>(v, row, 0.0, 1, v.S, lb, le);
-    }
+    });
 }
 
 size_t hi_smem_bytes(const SolverView& v) {

@@ -53,6 +53,19 @@ class dmfe_stats_t(ctypes.Structure):
                 ("L", _i), ("history_cap", _i), ("s", _i), ("precision", _i)]
 
 
+class dmfe_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("status", _i), ("slot", _i), ("t_final", _d), ("E", _d), ("mu", _d),
+                ("submit_s", _d), ("admit_s", _d), ("done_s", _d), ("steps_accepted", ctypes.c_longlong),
+                ("steps_rejected", ctypes.c_longlong)]
+
+
+class dmfe_server_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("admitted", ctypes.c_longlong),
+                ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong), ("queued", _i), ("running", _i),
+                ("bytes_in_use", ctypes.c_ulonglong), ("hbm_budget", ctypes.c_ulonglong),
+                ("batched_steps", ctypes.c_longlong)]
+
+
 _SIGS = {
     "dmfe_default_params": (None, [ctypes.POINTER(dmfe_params)]),
     "dmfe_strerror": (ctypes.c_char_p, [_i]),
@@ -83,6 +96,12 @@ _SIGS = {
     "dmfe_batch_solver": (_p, [_p, _i]),
     "dmfe_batch_step": (_i, [_p, _i]),
     "dmfe_batch_poll": (_i, [_p, _ip, _dp, _ip]),
+    "dmfe_footprint": (ctypes.c_ulonglong, [ctypes.POINTER(dmfe_params)]),
+    "dmfe_server_start": (_i, [_i, _i, _i, _i, _i, ctypes.c_ulonglong, _i, ctypes.POINTER(_p)]),
+    "dmfe_server_submit": (_i, [_p, ctypes.POINTER(dmfe_params), _d, _d, ctypes.POINTER(ctypes.c_longlong)]),
+    "dmfe_server_poll": (_i, [_p, ctypes.POINTER(dmfe_result), _i, _ip]),
+    "dmfe_server_stats": (_i, [_p, ctypes.POINTER(dmfe_server_stats_t)]),
+    "dmfe_server_stop": (_i, [_p]),
     "dmfe_sparsify_select_noalloc": (_i, [_p, _p, _p, _p, _p, _i, _i, _d, _p, _p]),
 }
 
@@ -206,6 +225,56 @@ class Batch:
     def __del__(self):
         try:
             self.close()
+        except Exception:
+            pass
+
+
+def footprint(coefs, T, L, grid_t_max, **kw):
+    """Device bytes a solver with these parameters allocates."""
+    prm, keep = make_params(coefs, T, L, grid_t_max, **kw)
+    return int(load().dmfe_footprint(ctypes.byref(prm)))
+
+
+class Server:
+    """dmfe_server: requests admitted by device-memory footprint into a continuously
+    stepped batch by a native worker thread."""
+
+    def __init__(self, max_slots, max_L, max_cap, precision="fp64", s=4, hbm_budget=None, steps_per_round=4):
+        self._lib = load()
+        self.h = _p()
+        self.precision, self.s = precision, s
+        if hbm_budget is None:
+            hbm_budget = 64 << 30
+        _check(self._lib.dmfe_server_start(max_slots, max_L, max_cap, PRECISIONS[precision], s, int(hbm_budget),
+                                           steps_per_round, ctypes.byref(self.h)), "dmfe_server_start")
+
+    def submit(self, coefs, T, L, grid_t_max, t_max, tol, **kw):
+        prm, keep = make_params(coefs, T, L, grid_t_max, s=self.s, precision=self.precision, **kw)
+        rid = ctypes.c_longlong()
+        _check(self._lib.dmfe_server_submit(self.h, ctypes.byref(prm), float(t_max), float(tol), ctypes.byref(rid)),
+               "dmfe_server_submit")
+        return rid.value
+
+    def poll(self, max_out=1024):
+        buf = (dmfe_result * max_out)()
+        n = _i()
+        _check(self._lib.dmfe_server_poll(self.h, buf, max_out, ctypes.byref(n)), "dmfe_server_poll")
+        return [{f: getattr(buf[k], f) for f, _ in dmfe_result._fields_} for k in range(n.value)]
+
+    def stats(self):
+        st = dmfe_server_stats_t()
+        _check(self._lib.dmfe_server_stats(self.h, ctypes.byref(st)), "dmfe_server_stats")
+        return {f: getattr(st, f) for f, _ in dmfe_server_stats_t._fields_}
+
+    def stop(self):
+        if self.h:
+            rc = self._lib.dmfe_server_stop(self.h)
+            self.h = _p()
+            _check(rc, "dmfe_server_stop")
+
+    def __del__(self):
+        try:
+            self.stop()
         except Exception:
             pass
 

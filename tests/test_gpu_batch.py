@@ -81,3 +81,82 @@ def test_continuous_batching_admits_and_releases_between_steps():
         for x, y in zip(results[case[2]], ref):
             assert np.array_equal(x, y)
     b.close()
+
+
+def _wait_results(srv, n, timeout=120.0):
+    import time
+    res = {}
+    t0 = time.time()
+    while len(res) < n and time.time() - t0 < timeout:
+        for r in srv.poll():
+            res[r["id"]] = r
+        time.sleep(0.005)
+    return res
+
+
+def test_server_results_equal_solo_runs():
+    need_gpu()
+    from paper_2604_06309_gb300 import Server, Solver
+    tol = 1e-8
+    srv = Server(4, 129, 64, precision="df", hbm_budget=8 << 30, steps_per_round=4)
+    ids = {}
+    for c in CASES:
+        f, T, L, cap, gtm, tmax = c
+        ids[srv.submit(f, T, L, gtm, tmax, tol, history_cap=cap)] = c
+    res = _wait_results(srv, len(CASES))
+    st = srv.stats()
+    srv.stop()
+    assert len(res) == len(CASES) and st["completed"] == len(CASES) and st["failed"] == 0
+    for rid, c in ids.items():
+        f, T, L, cap, gtm, tmax = c
+        sv = Solver(f, T, L, gtm, history_cap=cap, precision="df")
+        assert sv.integrate(tmax, tol) == 0
+        t, _, _, mu, E = sv.get_row()
+        r = res[rid]
+        assert r["status"] == 0 and r["t_final"] == t and r["E"] == E and r["mu"] == mu
+        assert r["submit_s"] <= r["admit_s"] <= r["done_s"]
+        sv.close()
+
+
+def test_server_admission_respects_the_footprint_budget():
+    need_gpu()
+    import time
+    from paper_2604_06309_gb300 import Server, footprint
+    c = CASES[2]
+    f, T, L, cap, gtm, tmax = c
+    one = footprint(f, T, L, gtm, history_cap=cap, precision="fp64")
+    srv = Server(4, 129, 64, precision="fp64", hbm_budget=int(1.5 * one), steps_per_round=2)
+    ids = [srv.submit(f, T, L, gtm, tmax, 1e-8, history_cap=cap) for _ in range(3)]
+    seen = 0
+    res = {}
+    t0 = time.time()
+    while len(res) < 3 and time.time() - t0 < 120:
+        st = srv.stats()
+        seen = max(seen, st["running"])
+        assert st["bytes_in_use"] <= int(1.5 * one)
+        for r in srv.poll():
+            res[r["id"]] = r
+        time.sleep(0.002)
+    srv.stop()
+    assert len(res) == 3 and seen == 1
+    # later requests waited for the earlier ones
+    order = sorted(res.values(), key=lambda r: r["admit_s"])
+    assert order[1]["admit_s"] >= order[0]["done_s"] - 1e-3
+    with pytest.raises(Exception):
+        Server(1, 129, 64, hbm_budget=one // 2).submit(f, T, L, gtm, tmax, 1e-8, history_cap=cap)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "df"])
+def test_footprint_covers_the_allocations(precision):
+    torch = need_gpu()
+    from paper_2604_06309_gb300 import Solver, footprint
+    L, cap = 1025, 600
+    est = footprint(MIXED_34, 0.5, L, 1e4, history_cap=cap, precision=precision)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    sv = Solver(MIXED_34, 0.5, L, 1e4, history_cap=cap, precision=precision)
+    free1, _ = torch.cuda.mem_get_info()
+    used = free0 - free1
+    sv.close()
+    assert used <= est * 1.02 + (8 << 20)
+    assert est <= used * 1.25 + (64 << 20)
