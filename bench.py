@@ -35,13 +35,14 @@ T_BATH = 0.5
 GRID_T_MAX = 1e5
 TOL = 1e-8
 # Algorithmic operations per (i, j) pair at stencil width 4, counted from the kernel
-# source (FMA = 2 flops). FP64 kernel: Lagrange weights 3 x 20, A1 32, A2 16, B1 16,
-# B2 (time weights 23, two 4-point stencils of 4 fields 64, Hermite combination 14),
-# f' and f'' at two points for the (3+4) model 20, nine products and sums 30.
-FLOP_PER_PAIR_S4 = 60 + 32 + 16 + 16 + 101 + 20 + 30
-# Double-float kernel, FP32 flops of the double-float arithmetic: weights 3 x 118,
-# B1 110, A1 220, A2 110, B2 713, f' and f'' 210, products and sums 226.
-DF_FP32_FLOP_PER_PAIR_S4 = 354 + 110 + 220 + 110 + 713 + 210 + 226
+# source (FMA = 2 flops). The Lagrange weights of the three stencils are read from the
+# per-grid tables, not computed per pair. FP64 kernel: A1 32, A2 16, B1 16, B2 (time
+# weights 23, two 4-point stencils of 4 fields 64, Hermite combination 14), f' and f''
+# at two points for the (3+4) model 20, nine products and sums 30.
+FLOP_PER_PAIR_S4 = 32 + 16 + 16 + 101 + 20 + 30
+# Double-float kernel, FP32 flops of the double-float arithmetic: B1 110, A1 220, A2 110,
+# B2 713, f' and f'' 210, products and sums 226.
+DF_FP32_FLOP_PER_PAIR_S4 = 110 + 220 + 110 + 713 + 210 + 226
 # Nominal per-GPU peaks derived from the unit counts and the 2.07 GHz maximum SM clock:
 # FP64 1.25 TFLOP/s (2 FMA lanes per SM); FP32 152 SMs x 128 lanes x 2 x 2.07e9.
 FP64_PEAK_GFLOPS = 1250.0
@@ -228,7 +229,8 @@ def _run_ours(args, rank, world, dev, stream):
     n0 = n_state
     wide = args.precision in ("fp64", "df")  # FP64 master or double-float replica: 8 B per value
     bytes_hist = 4 * n0 * L * (8 if wide else 4)
-    bytes_tab = 3 * pairs * (8 if wide else 4)
+    # stencil entries: {base, 4 weights} of 40 B (FP64 and double-float), packed 4 B positions (FP32)
+    bytes_tab = 3 * pairs * (40 if wide else 4)
     bytes_io = 2 * L * 8 + 10 * L * 8
     res = dict(dev_time=dev_time, e2e_time=e2e_time, k_avg=k_avg, clocks=clk, stats=st, stats_after=st2,
                bytes=(bytes_hist, bytes_tab, bytes_io), pairs=pairs, n0=n0, t_state=t_state,

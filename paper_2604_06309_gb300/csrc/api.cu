@@ -152,18 +152,19 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
     TRY(dev_alloc(h, &p, L * sizeof(double))); v.nu = (double*)p;
     TRY(dev_alloc(h, &p, L * sizeof(float))); v.omega32 = (float*)p;
     TRY(dev_alloc(h, &p, L * sizeof(float))); v.nu32 = (float*)p;
+    const size_t wts = 8 + 8 * (size_t)pin->s;  // bytes per stencil entry
     if (v.precision == DMFE_FP64) {
-        TRY(dev_alloc(h, &p, LL * sizeof(double))); v.x1 = (double*)p;
-        TRY(dev_alloc(h, &p, LL * sizeof(double))); v.x2 = (double*)p;
-        TRY(dev_alloc(h, &p, LL * sizeof(double))); v.x3 = (double*)p;
+        TRY(dev_alloc(h, &p, LL * wts)); v.wt1 = (unsigned char*)p;
+        TRY(dev_alloc(h, &p, LL * wts)); v.wt2 = (unsigned char*)p;
+        TRY(dev_alloc(h, &p, LL * wts)); v.wt3 = (unsigned char*)p;
     } else if (v.precision == DMFE_FP32_COMPENSATED) {
         TRY(dev_alloc(h, &p, LL * sizeof(uint32_t))); v.p1 = (uint32_t*)p;
         TRY(dev_alloc(h, &p, LL * sizeof(uint32_t))); v.p2 = (uint32_t*)p;
         TRY(dev_alloc(h, &p, LL * sizeof(uint32_t))); v.p3 = (uint32_t*)p;
     } else {
-        TRY(dev_alloc(h, &p, LL * sizeof(df))); v.q1 = (df*)p;
-        TRY(dev_alloc(h, &p, LL * sizeof(df))); v.q2 = (df*)p;
-        TRY(dev_alloc(h, &p, LL * sizeof(df))); v.q3 = (df*)p;
+        TRY(dev_alloc(h, &p, LL * wts)); v.wt1 = (unsigned char*)p;
+        TRY(dev_alloc(h, &p, LL * wts)); v.wt2 = (unsigned char*)p;
+        TRY(dev_alloc(h, &p, LL * wts)); v.wt3 = (unsigned char*)p;
         TRY(dev_alloc(h, &p, L * sizeof(df))); v.omega_df = (df*)p;
         TRY(dev_alloc(h, &p, L * sizeof(df))); v.nu_df = (df*)p;
         TRY(dev_alloc(h, &p, L * sizeof(dfrow))); v.rowdf = (dfrow*)p;
@@ -337,12 +338,13 @@ unsigned long long dmfe_footprint(const dmfe_params* pin) {
     };
     for (int k = 0; k < 3; ++k) add(L * 8);
     add(L * 4); add(L * 4);
+    const unsigned long long wts = 8 + 8 * (unsigned long long)p.s;
     if (p.precision == DMFE_FP64) {
-        for (int k = 0; k < 3; ++k) add(LL * 8);
+        for (int k = 0; k < 3; ++k) add(LL * wts);
     } else if (p.precision == DMFE_FP32_COMPENSATED) {
         for (int k = 0; k < 3; ++k) add(LL * 4);
     } else {
-        for (int k = 0; k < 3; ++k) add(LL * sizeof(df));
+        for (int k = 0; k < 3; ++k) add(LL * wts);
         add(L * sizeof(df)); add(L * sizeof(df)); add(L * sizeof(dfrow)); add(cap * sizeof(dfslice)); add(L * 4);
     }
     for (int b = 0; b < 2; ++b) {
@@ -393,33 +395,25 @@ int dmfe_grid(dmfe_solver* h, double* theta, double* omega, double* nu) {
 int dmfe_tables(dmfe_solver* h, double* x1, double* x2, double* x3) {
     if (!h) return DMFE_ERR_ARG;
     const size_t LL = (size_t)h->v.L * h->v.L;
-    const SolverView& v = h->v;
+    // positions are recomputed on demand by the table kernel into temporary buffers
+    SolverView v = h->v;
+    v.p1 = v.p2 = v.p3 = nullptr;
+    v.q1 = v.q2 = v.q3 = nullptr;
+    v.wt1 = v.wt2 = v.wt3 = nullptr;
+    double* buf = nullptr;
+    DMFE_CUDA_TRY(cudaMallocAsync((void**)&buf, 3 * LL * sizeof(double), h->stream));
+    v.x1 = buf;
+    v.x2 = buf + LL;
+    v.x3 = buf + 2 * LL;
+    int rc = launch_tables(v, h->stream);
     double* outs[3] = {x1, x2, x3};
-    if (v.precision == DMFE_FP64) {
-        const double* src[3] = {v.x1, v.x2, v.x3};
-        for (int q = 0; q < 3; ++q)
-            if (outs[q]) DMFE_CUDA_TRY(cudaMemcpyAsync(outs[q], src[q], LL * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-        DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    } else if (v.precision == DMFE_DOUBLE_FLOAT) {
-        const df* src[3] = {v.q1, v.q2, v.q3};
-        std::vector<df> tmp(LL);
-        for (int q = 0; q < 3; ++q) {
-            if (!outs[q]) continue;
-            DMFE_CUDA_TRY(cudaMemcpyAsync(tmp.data(), src[q], LL * sizeof(df), cudaMemcpyDeviceToHost, h->stream));
-            DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
-            for (size_t k = 0; k < LL; ++k) outs[q][k] = (double)tmp[k].hi + (double)tmp[k].lo;
-        }
-    } else {
-        const uint32_t* src[3] = {v.p1, v.p2, v.p3};
-        std::vector<uint32_t> tmp(LL);
-        for (int q = 0; q < 3; ++q) {
-            if (!outs[q]) continue;
-            DMFE_CUDA_TRY(cudaMemcpyAsync(tmp.data(), src[q], LL * sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
-            DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
-            for (size_t k = 0; k < LL; ++k) outs[q][k] = tmp[k] / (double)(1u << FIX_FRAC_BITS);
-        }
-    }
-    return DMFE_OK;
+    for (int q = 0; q < 3 && !rc; ++q)
+        if (outs[q] && cudaMemcpyAsync(outs[q], buf + q * LL, LL * sizeof(double), cudaMemcpyDeviceToHost,
+                                       h->stream) != cudaSuccess)
+            rc = DMFE_ERR_CUDA;
+    cudaFreeAsync(buf, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = DMFE_ERR_CUDA;
+    return rc;
 }
 
 int dmfe_integrate(dmfe_solver* h, double t_max, double tol) {

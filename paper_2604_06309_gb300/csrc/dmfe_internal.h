@@ -105,9 +105,12 @@ struct SolverView {
     const double* nu;     // [L]
     const float* omega32; // [L]
     const float* nu32;    // [L]
-    const double* x1;     // [L*L] FP64 fractional index (FP64 path)
+    const double* x1;     // [L*L] FP64 fractional index (only while dmfe_tables runs)
     const double* x2;
     const double* x3;
+    const unsigned char* wt1;  // [L*L] stencil entries {int base, pad, s weights} of
+    const unsigned char* wt2;  //   8 + 8 s bytes: FP64 weights (FP64 path) or double-float
+    const unsigned char* wt3;  //   weights (double-float path), for phi1, phi2, psi
     const uint32_t* p1;   // [L*L] fixed-point index, 19 fraction bits (FP32 path)
     const uint32_t* p2;
     const uint32_t* p3;

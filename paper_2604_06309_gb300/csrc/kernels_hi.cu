@@ -68,11 +68,13 @@ struct TimeW {
     double w0, w1, w2, w3;
 };
 
+// sinv (may be NULL) holds 1/(t_{k+1} - t_k); inv_hx = 1/hx.
 __device__ __forceinline__ TimeW time_weights_f64(const double* sht, int n, bool ext, double tl,
-                                                  double hx, double tau, int hint) {
+                                                  double hx, double tau, int hint,
+                                                  const double* sinv = nullptr, double inv_hx = 0.0) {
     TimeW r;
     if (ext && tau > tl) {
-        double s = tau - tl, q = s / hx;
+        double s = tau - tl, q = sinv ? s * inv_hx : s / hx;
         r.a0 = n - 1; r.a1 = -1;
         r.w0 = 1.0 - q * q; r.w1 = s - s * q; r.w2 = q * q; r.w3 = 0.0;
     } else if (n == 1) {
@@ -83,7 +85,7 @@ __device__ __forceinline__ TimeW time_weights_f64(const double* sht, int n, bool
         while (k < n - 2 && sht[k + 1] <= tau) ++k;
         while (k > 0 && sht[k] > tau) --k;
         double hh = sht[k + 1] - sht[k];
-        double sg = (tau - sht[k]) / hh;
+        double sg = sinv ? (tau - sht[k]) * sinv[k] : (tau - sht[k]) / hh;
         double om = 1.0 - sg;
         r.a0 = k; r.a1 = k + 1;
         r.w0 = (1.0 + 2.0 * sg) * om * om;
@@ -128,17 +130,22 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
     const double* __restrict__ ht = v.ht[act];
     dbl4* srow = reinterpret_cast<dbl4*>(smraw);            // [L] {K, D, C, R}
     double* sht = reinterpret_cast<double*>(srow + L);              // [cap]
-    int* scell = reinterpret_cast<int*>(sht + v.cap);               // [L]
+    double* sinvh = sht + v.cap;                                    // [cap] 1/(t_{k+1} - t_k)
+    int* scell = reinterpret_cast<int*>(sinvh + v.cap);             // [L]
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         double C = row[i], R = row[L + i];
         srow[i] = dbl4{fp2(v.poly, C) * R, fp1(v.poly, C), C, R};
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) sht[i] = ht[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        sht[i] = ht[i];
+        sinvh[i] = i + 1 < n ? 1.0 / (ht[i + 1] - ht[i]) : 0.0;
+    }
     for (int m = threadIdx.x; m < L; m += blockDim.x) scell[m] = v.cell[m];
     __syncthreads();
     const double tl = sht[n - 1];
     const bool ext = t > tl;
     const double hx = t - tl;
+    const double inv_hx = ext ? 1.0 / hx : 0.0;
     const int lane = threadIdx.x & 31;
     const double* __restrict__ theta = v.theta;
     const double* __restrict__ omega = v.omega;
@@ -155,9 +162,10 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
             b1.a0 = d.a0; b1.a1 = d.a1;
             b1.w0 = d.w[0]; b1.w1 = d.w[1]; b1.w2 = d.w[2]; b1.w3 = d.w[3];
         }
-        const double* __restrict__ x1r = v.x1 + (size_t)j * L;
-        const double* __restrict__ x2r = v.x2 + (size_t)j * L;
-        const double* __restrict__ x3r = v.x3 + (size_t)j * L;
+        constexpr size_t WTS = 8 + 8 * SW;  // bytes per stencil entry
+        const unsigned char* __restrict__ w1r = v.wt1 + (size_t)j * L * WTS;
+        const unsigned char* __restrict__ w2r = v.wt2 + (size_t)j * L * WTS;
+        const unsigned char* __restrict__ w3r = v.wt3 + (size_t)j * L * WTS;
         double acc[9];
 #pragma unroll
         for (int r = 0; r < 9; ++r) acc[r] = 0.0;
@@ -182,10 +190,11 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
             // ---- A1: current row at phi1
             double KA1 = 0, DA1 = 0, CA1 = 0, RA1 = 0;
             {
-                double x = x1r[i];
-                int b = stencil_base<SW>((int)floor(x), L);
+                const unsigned char* e = w1r + (size_t)i * WTS;
+                const int b = *reinterpret_cast<const int*>(e);
                 double w[SW];
-                lagrange<SW>(x - b, w);
+#pragma unroll
+                for (int k = 0; k < SW; ++k) w[k] = reinterpret_cast<const double*>(e + 8)[k];
 #pragma unroll
                 for (int k = 0; k < SW; ++k) {
                     dbl4 q = srow[b + k];
@@ -194,11 +203,14 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
             }
             // ---- A2: current row at phi2
             double KA2 = 0, RA2 = 0;
-            double x2 = x2r[i];
+            int base2;
             {
-                int b = stencil_base<SW>((int)floor(x2), L);
+                const unsigned char* e = w2r + (size_t)i * WTS;
+                const int b = *reinterpret_cast<const int*>(e);
+                base2 = b;
                 double w[SW];
-                lagrange<SW>(x2 - b, w);
+#pragma unroll
+                for (int k = 0; k < SW; ++k) w[k] = reinterpret_cast<const double*>(e + 8)[k];
 #pragma unroll
                 for (int k = 0; k < SW; ++k) {
                     dbl4 q = srow[b + k];
@@ -210,13 +222,15 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
             {
                 const double thi = theta[i];
                 const double tau2 = (thj + omj * thi) * t;
-                int cell = (int)floor(x2);
+                int cell = base2 + SW / 2 - 1;  // the grid cell of phi2 (a hint; the walk corrects)
+                cell = cell < 0 ? 0 : (cell > L - 1 ? L - 1 : cell);
                 const int h0 = scell[cell];
-                const TimeW b2 = time_weights_f64(sht, n, ext, tl, hx, tau2, h0);
-                double x3 = x3r[i];
-                int b = stencil_base<SW>((int)floor(x3), L);
+                const TimeW b2 = time_weights_f64(sht, n, ext, tl, hx, tau2, h0, sinvh, inv_hx);
+                const unsigned char* e = w3r + (size_t)i * WTS;
+                const int b = *reinterpret_cast<const int*>(e);
                 double w[SW];
-                lagrange<SW>(x3 - b, w);
+#pragma unroll
+                for (int k = 0; k < SW; ++k) w[k] = reinterpret_cast<const double*>(e + 8)[k];
                 double c0 = 0, dc0 = 0, r0 = 0, dr0 = 0, c1 = 0, dc1 = 0, r1 = 0, dr1 = 0;
                 const dbl4* __restrict__ s0 = H + (size_t)b2.a0 * L + b;
 #pragma unroll
@@ -488,7 +502,7 @@ __global__ void __launch_bounds__(HI_THREADS, 1) k_batch_hi(const BatchTable* __
 
 size_t hi_smem_bytes(const SolverView& v) {
     if (v.precision == DMFE_FP64)
-        return (size_t)v.L * sizeof(dbl4) + (size_t)v.cap * sizeof(double) + (size_t)v.L * sizeof(int);
+        return (size_t)v.L * sizeof(dbl4) + (size_t)v.cap * 2 * sizeof(double) + (size_t)v.L * sizeof(int);
     return (size_t)v.L * sizeof(float4) + (size_t)v.cap * (sizeof(double) + 3 * sizeof(float)) +
            (size_t)v.L * sizeof(int);
 }
