@@ -1,7 +1,20 @@
-"""Adaptive Dormand-Prince driver, step control, rollback and sparsification.
+"""Adaptive Runge-Kutta driver, step control, rollback and sparsification.
 
 Secs. 3.1 (the step recipe), 3.5 (adaptive ODE solver) and 3.6 (selective history
 reduction). Readings where the paper is silent:
+
+* Integrators (Sec. 3.5): Dormand-Prince 5(4) at early times, then the ten-stage
+  fourth-order strong-stability-preserving method SSPRK(10,4) of Ketcheson (2008).
+  Its Butcher form is generated here from the published low-storage recurrence
+  (five Euler substeps of h/6, the register combination 1/25, 9/25 and 15, -5, four
+  more substeps, final update with h/10). The paper names no embedded estimate for
+  it; the one used here is the third-order weight vector of minimal 2-norm on the
+  same ten stages whose last weight is zero (exactly third order, all weights >= 0).
+* Switch (Sec. 3.5): the spectrum of the Jacobian lies on the negative real axis
+  within radius 4 sqrt(f''(1)). After an accepted Dormand-Prince step whose new
+  controller step dt reaches beta_DP / (4 sqrt(f''(1))), with beta_DP the length of
+  the real stability interval of Dormand-Prince 5, the method becomes SSPRK(10,4)
+  and dt is halved. There is no switch back (a rollback keeps the current method).
 
 * Step rule (Sec. 3.5): eps_RK = sum_i |dC_i| + |dR_i| from the embedded 4th-order
   estimate. eps_RK > 2 tol: reject, revert the last min(10, N-1) stored slices and
@@ -18,8 +31,10 @@ reduction). Readings where the paper is silent:
   the store is full; if it frees nothing, the candidate with the smallest
   eps_sparse is removed and counted as forced.
 
-Pins: tests/test_oracle_solver.py (DP5 order and error-estimate order on scalar
-ODEs, the p = 2 energy against the closed form, f = 0 exact solution, agreement
+Pins: tests/test_oracle_solver.py (DP5 and SSPRK(10,4) order and error-estimate
+order on scalar ODEs, exact order conditions of the generated tableau, the
+low-storage recurrence reproduced step by step, the DP5 stability polynomial and
+its real stability interval by direct one-step amplification, the p = 2 energy against the closed form, f = 0 exact solution, agreement
 with the brute-force uniform-grid solver, equilibrium FDT above T_d, the Hermite
 integral identity and cubic slices being removed by sparsification).
 """
@@ -46,6 +61,135 @@ DP_B4 = np.array([5179 / 57600, 0.0, 7571 / 16695, 393 / 640, -92097 / 339200, 1
 DP_E = DP_B5 - DP_B4
 
 OK, ERR_STEP_UNDERFLOW, ERR_CAPACITY, ERR_NONFINITE = 0, -4, -5, -3
+
+
+class RKMethod:
+    """Explicit Runge-Kutta pair in first-same-as-last form.
+
+    Stage 0 is f at the start of the step (the stored derivative). Stages 1..n are
+    evaluated at t + c[st] h on Y_st = y + h sum_{l < st} A[st][l] k_l; row A[n] is
+    the propagating weight vector b, so Y_n is the new solution and k_n = f(t + h,
+    Y_n) its derivative. The error estimate is h sum_l E[l] k_l over l = 0..n.
+    """
+
+    def __init__(self, name, c, A, E):
+        self.name = name
+        self.n = len(A) - 1
+        self.c = np.asarray(c, dtype=float)
+        self.A = [[float(a) for a in row] for row in A]
+        self.E = np.asarray(E, dtype=float)
+
+
+def ssprk104_exact():
+    """SSPRK(10,4) Butcher coefficients (exact fractions) from its low-storage form.
+
+    Returns (c, A, b, bhat) for the ten method stages (0-based, stage 0 at the step
+    start), with bhat the embedded third-order weights described in the module
+    docstring. Each register holds its coefficients on (y, h k_0, ..., h k_9).
+    """
+    from fractions import Fraction as Fr
+    ns = 10
+    one = [Fr(1)] + [Fr(0)] * ns
+
+    def axpy(a, x, b_, y):
+        return [a * xi + b_ * yi for xi, yi in zip(x, y)]
+
+    rows = []
+    q1, q2 = list(one), list(one)
+
+    def euler(q, weight):
+        st = len(rows)
+        rows.append(q)
+        q = list(q)
+        q[1 + st] += weight
+        return q
+
+    for _ in range(5):
+        q1 = euler(q1, Fr(1, 6))
+    q2 = axpy(Fr(1, 25), q2, Fr(9, 25), q1)
+    q1 = axpy(Fr(15), q2, Fr(-5), q1)
+    for _ in range(4):
+        q1 = euler(q1, Fr(1, 6))
+    # final update u = q2 + 3/5 q1 + h/10 f(q1)
+    rows.append(q1)
+    new = axpy(Fr(1), q2, Fr(3, 5), q1)
+    new[1 + 9] += Fr(1, 10)
+    A = [[r[1 + l] for l in range(st)] for st, r in enumerate(rows)]
+    c = [sum(a) for a in A]
+    b = [new[1 + l] for l in range(ns)]
+    assert all(r[0] == 1 for r in rows) and new[0] == 1
+    bhat = [Fr(3, 20), Fr(1, 12), Fr(7, 120), Fr(3, 40), Fr(2, 15), Fr(7, 120), Fr(3, 40), Fr(2, 15),
+            Fr(7, 30), Fr(0)]
+    return c, A, b, bhat
+
+
+def _ssprk104():
+    c, A, b, bhat = ssprk104_exact()
+    rows = [list(r) for r in A] + [list(b)]
+    cc = list(c) + [1]
+    E = [bi - bh for bi, bh in zip(b, bhat)] + [0]
+    return RKMethod("ssprk104", [float(x) for x in cc], rows, [float(x) for x in E])
+
+
+DP5 = RKMethod("dp5", DP_C, DP_A, DP_E)
+SSPRK104 = _ssprk104()
+METHODS = {"dp5": DP5, "ssprk104": SSPRK104}
+
+
+def stability_coefficients(method):
+    """gamma_k with R(z) = 1 + sum_k gamma_k z^k, gamma_k = b^T A^{k-1} 1 (stages 0..n-1)."""
+    n = method.n
+    A = np.zeros((n, n))
+    for st in range(n):
+        A[st, :st] = method.A[st][:st] if st > 0 else []
+    b = np.asarray(method.A[n][:n], dtype=float)
+    g, v = [1.0], np.ones(n)
+    for _ in range(n):
+        g.append(float(b @ v))
+        v = A @ v
+    return np.array(g)
+
+
+def real_stability_boundary(method):
+    """Largest x with |R(-y)| <= 1 for all y in [0, x] (scan, then bisection)."""
+    g = stability_coefficients(method)
+    R = lambda y: abs(np.polyval(g[::-1], -y))
+    y, dy = 0.0, 1e-3
+    while R(y + dy) <= 1.0 + 1e-14:
+        y += dy
+        if y > 1e3:
+            return np.inf
+    lo, hi = y, y + dy
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if R(mid) <= 1.0:
+            lo = mid
+        else:
+            hi = mid
+    return lo
+
+
+DP5_REAL_STABILITY = real_stability_boundary(DP5)
+
+
+def switch_dt_auto(model):
+    """dt at which Dormand-Prince 5 meets its stability limit (Sec. 3.5): the
+    Jacobian's spectral radius is at most 4 sqrt(f''(1)); inf if f''(1) <= 0."""
+    fpp1 = float(model.fpp(1.0))
+    if fpp1 <= 0.0:
+        return np.inf
+    return DP5_REAL_STABILITY / (4.0 * np.sqrt(fpp1))
+
+
+def rk_step(method, f, t, y, h, k0):
+    """One step of an RKMethod; returns (y_new, err, ks) with ks[n] = f(t + h, y_new)."""
+    ks = [k0]
+    yk = y
+    for st in range(1, method.n + 1):
+        yk = y + h * sum(method.A[st][l] * ks[l] for l in range(st))
+        ks.append(f(t + method.c[st] * h, yk))
+    err = h * sum(method.E[l] * ks[l] for l in range(method.n + 1))
+    return yk, err, ks
 
 
 def dp5_step(f, t, y, h, k1):
@@ -116,7 +260,11 @@ class Solver:
     """Plain FP64 solver state: grid, model, history and step control."""
 
     def __init__(self, coefs, T, L, grid_t_max, s=4, beta0=0.0, alpha=0.0, delta=0.0,
-                 history_cap=None, dt0=1e-4, dt_min=1e-12, sparsify=True):
+                 history_cap=None, dt0=1e-4, dt_min=1e-12, sparsify=True, integrator="auto",
+                 switch_dt=0.0):
+        """integrator: "dp5" (Dormand-Prince throughout), "ssprk104" (SSPRK(10,4)
+        throughout) or "auto" (Dormand-Prince, then SSPRK(10,4) once dt reaches
+        switch_dt; switch_dt = 0 takes the stability estimate switch_dt_auto)."""
         from .model import Model
         self.model = Model(coefs, T, beta0)
         self.grid = Grid(L, grid_t_max, s, alpha, delta)
@@ -126,6 +274,13 @@ class Solver:
         self.dt = float(dt0)
         self.dt_min = float(dt_min)
         self.sparsify = sparsify
+        if integrator not in ("dp5", "ssprk104", "auto"):
+            raise ValueError("integrator must be dp5, ssprk104 or auto")
+        self.integrator = integrator
+        self.method = SSPRK104 if integrator == "ssprk104" else DP5
+        self.switch_dt = (switch_dt_auto(self.model) if switch_dt == 0.0 else float(switch_dt)) \
+            if integrator == "auto" else np.inf
+        self.t_switch = None
         ones = np.ones(L)
         dC0, dR0, mu0, E0 = rhs(self.model, self.grid, None, 0.0, ones, ones)
         self.hist = History([0.0], ones[None, :], dC0[None, :], ones[None, :], dR0[None, :])
@@ -145,12 +300,15 @@ class Solver:
         return np.concatenate([dC, dR])
 
     def step(self, h):
-        """Trial step of size h from the last slice; returns (y_new, k7, eps_RK)."""
-        L = self.grid.L
+        """Trial step of size h from the last slice with the current method; returns
+        (y_new, derivative at y_new, eps_RK)."""
         y = np.concatenate([self.hist.C[-1], self.hist.R[-1]])
-        k1 = np.concatenate([self.hist.dC[-1], self.hist.dR[-1]])
-        y_new, err, ks = dp5_step(self._f, self.t, y, h, k1)
-        return y_new, ks[6], float(np.sum(np.abs(err)))
+        k0 = np.concatenate([self.hist.dC[-1], self.hist.dR[-1]])
+        if self.method is DP5:
+            y_new, err, ks = dp5_step(self._f, self.t, y, h, k0)
+        else:
+            y_new, err, ks = rk_step(self.method, self._f, self.t, y, h, k0)
+        return y_new, ks[-1], float(np.sum(np.abs(err)))
 
     def integrate(self, t_max, tol):
         """Advance to t_max (Secs. 3.1, 3.5, 3.6); returns a status code."""
@@ -182,6 +340,10 @@ class Solver:
                     self.dt *= 0.9
                 elif eps < 0.5 * tol:
                     self.dt *= 1.01
+                if self.method is DP5 and self.dt >= self.switch_dt:
+                    self.method = SSPRK104
+                    self.dt *= 0.5
+                    self.t_switch = t1
             if self.dt < self.dt_min:
                 return ERR_STEP_UNDERFLOW
         C, R = self.hist.C[-1], self.hist.R[-1]
