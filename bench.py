@@ -48,6 +48,11 @@ DF_FP32_FLOP_PER_PAIR_S4 = 110 + 220 + 110 + 713 + 210 + 226
 FP64_PEAK_GFLOPS = 1250.0
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 LAUNCHES_PER_STEP = 24  # step graph (begin, 6 x [prep, integrals, stage end], 4 sparsify) + begin
+# Lengths of the real stability intervals (|R(-x)| <= 1 on [0, x]) of Dormand-Prince 5
+# and SSPRK(10,4); with the Jacobian bound 4 sqrt(f''(1)) of Sec. 3.5 they give the
+# largest stable steps.
+DP5_REAL_STABILITY = 3.3066
+SSPRK104_REAL_STABILITY = 13.917
 
 
 def parse():
@@ -67,6 +72,8 @@ def parse():
     ap.add_argument("--window", type=float, default=30.0, help="seconds of batched or served work")
     ap.add_argument("--slots", type=int, default=256)
     ap.add_argument("--batch-max-L", type=int, default=4097, help="largest grid of the batch mix")
+    ap.add_argument("--integrator", default="auto", choices=["auto", "dp5", "ssprk104"],
+                    help="integrator of the step workload (auto: Dormand-Prince, SSPRK(10,4) after the switch)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the double-float and FP32-compensated variants of the same workload")
     return ap.parse_args()
@@ -147,7 +154,7 @@ def _run_ours(args, rank, world, dev, stream):
     L = args.L
     n0, times = workload(L)
     sv = Solver(COEFS, T_BATH, L, GRID_T_MAX, s=4, history_cap=L, precision=args.precision,
-                stream=stream.cuda_stream)
+                stream=stream.cuda_stream, integrator=getattr(args, "integrator", "auto"))
     S = torch.empty((10, L), dtype=torch.float64, device="cuda")
     flush = torch.empty(int(256 * 2 ** 20), dtype=torch.uint8, device="cuda")
 
@@ -517,6 +524,19 @@ def main():
             variants[VARIANT_NAMES[prec]] = {
                 "value": args.steps / r2["dev_time"], "e2e": args.steps / r2["e2e_time"], "unit": "RK steps/s",
                 "dtype": DTYPES[prec], "roofline": roofline(prec, r2), "solver": solver_info(r2)}
+        # the late-time integrator on the same workload: ten stages per step, a real
+        # stability interval of 13.9 instead of 3.31 (Sec. 3.5)
+        a3 = argparse.Namespace(**vars(args))
+        a3.integrator = "ssprk104"
+        r3 = run_ours(a3, rank, world)
+        ssp = args.steps / r3["dev_time"]
+        rho = 4.0 * np.sqrt(sum(c * p * (p - 1) for p, c in COEFS.items()))
+        variants["ssprk104_" + VARIANT_NAMES[args.precision]] = {
+            "value": ssp, "e2e": args.steps / r3["e2e_time"], "unit": "RK steps/s", "dtype": DTYPES[args.precision],
+            "stage_evals_per_s": 10 * ssp, "gpu_launches_per_step": 35,
+            "simulated_time_per_s_at_stability_limit": ssp * SSPRK104_REAL_STABILITY / rho,
+            "dp5_simulated_time_per_s_at_stability_limit": value * DP5_REAL_STABILITY / rho,
+            "roofline": roofline(args.precision, r3), "solver": solver_info(r3)}
         line["variants"] = variants
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(L)

@@ -5,8 +5,9 @@
  *
  * Fields are stored on the grid (t_n, theta_i t_n): Cf(t, theta) = C(t, theta t),
  * Rf(t, theta) = R(t, theta t) (Sec. 3.1). theta_i, i = 0..L-1, is the fixed grid of
- * Eq. (theta) (Sec. 3.2); t_n are the slices accepted by the adaptive Dormand-Prince
- * integrator (Sec. 3.5), thinned by sparsification (Sec. 3.6).
+ * Eq. (theta) (Sec. 3.2); t_n are the slices accepted by the adaptive Runge-Kutta
+ * integrator (Dormand-Prince 5(4), then SSPRK(10,4); Sec. 3.5), thinned by
+ * sparsification (Sec. 3.6).
  *
  * Conventions for every entry point:
  *  - Return value: DMFE_OK (0) or a negative DMFE_ERR_* code; dmfe_strerror maps it
@@ -50,6 +51,12 @@ extern "C" {
                                      FP32 pipes over a double-float history replica; FP64 for
                                      everything else. FP64-class results at FP32-pipe speed */
 
+/* ---- integrator (Sec. 3.5) ---------------------------------------------------- */
+#define DMFE_RK_AUTO      0  /* Dormand-Prince 5(4) until the controller step reaches the
+                                switch step, then SSPRK(10,4) with the step halved (default) */
+#define DMFE_RK_DP5       1  /* Dormand-Prince 5(4) throughout                               */
+#define DMFE_RK_SSPRK104  2  /* SSPRK(10,4) throughout                                       */
+
 #define DMFE_NS 10   /* rows of the history-integral output S, see dmfe_history_integrals */
 #define DMFE_MAX_TERMS 16
 #define DMFE_MAX_POWER 24
@@ -73,6 +80,12 @@ typedef struct {
     int           sparsify;     /* 1: sparsification pass whenever the store is full (default);
                                    0: off (a full store ends the run with DMFE_ERR_CAPACITY) */
     void*         stream;       /* cudaStream_t for all work; NULL: the solver's own stream */
+    int           integrator;   /* DMFE_RK_AUTO (default), DMFE_RK_DP5 or DMFE_RK_SSPRK104  */
+    double        rk_switch_dt; /* DMFE_RK_AUTO: controller step at which SSPRK(10,4) takes
+                                   over; 0 (default): beta_DP / (4 sqrt(f''(1))), the step at
+                                   which Dormand-Prince 5 (real stability interval beta_DP =
+                                   3.3066) reaches the spectral bound ||J|| <= 4 sqrt(f''(1))
+                                   of Sec. 3.5; no switch when f''(1) <= 0              */
 } dmfe_params;
 
 /* Per-solve counters. */
@@ -88,6 +101,12 @@ typedef struct {
     int       status;            /* device status word (0 or DMFE_ERR_*)      */
     int       L, history_cap;    /* sizes fixed at create                     */
     int       s, precision;
+    int       method;            /* integrator of the next step: DMFE_RK_DP5 or DMFE_RK_SSPRK104 */
+    double    t_switch;          /* time of the switch to SSPRK(10,4), -1 if none   */
+    double    rk_switch_dt;      /* switch step in force (+inf: none)                */
+    int       step_graph;        /* 0: no step graph yet; 1: all stages inline (the SSPRK
+                                    ones gate themselves off in Dormand-Prince steps);
+                                    2: SSPRK stages in a conditional graph node        */
 } dmfe_stats_t;
 
 /* Fill p with defaults for the given f (pointers are kept, not copied). */
@@ -110,16 +129,17 @@ int dmfe_grid(dmfe_solver* h, double* theta, double* omega, double* nu);
  * x3 for psi = theta_j / phi2 (Sec. 3.3). Any pointer may be NULL. */
 int dmfe_tables(dmfe_solver* h, double* x1, double* x2, double* x3);
 
-/* Advance with adaptive Dormand-Prince 5(4) to t_max <= grid_t_max with tolerance tol
- * (Secs. 3.1, 3.5, 3.6). Step control runs on the device; the host polls a status
- * word. Returns DMFE_ERR_STEP_UNDERFLOW, DMFE_ERR_NONFINITE or DMFE_ERR_CAPACITY when
+/* Advance with the adaptive integrator of dmfe_params.integrator to t_max <= grid_t_max
+ * with tolerance tol (Secs. 3.1, 3.5, 3.6). Step control, including the switch from
+ * Dormand-Prince to SSPRK(10,4), runs on the device; the host polls a status word. Returns DMFE_ERR_STEP_UNDERFLOW, DMFE_ERR_NONFINITE or DMFE_ERR_CAPACITY when
  * the device stops the run; the solver then holds the last accepted slice. */
 int dmfe_integrate(dmfe_solver* h, double t_max, double tol);
 
-/* Launch exactly nsteps Dormand-Prince trial steps toward t_max with tolerance tol on
- * the solver's stream (or `stream` if not NULL) without synchronising: each step is one
- * CUDA-graph launch of the stages, the device-side step rule and, when the store is
- * full, a sparsification pass. Steps after t_max is reached or after a device error
+/* Launch exactly nsteps trial steps toward t_max with tolerance tol on the solver's
+ * stream (or `stream` if not NULL) without synchronising: each step is one CUDA-graph
+ * launch of the stages (the last four stages of SSPRK(10,4) sit in a conditional graph
+ * node that the step's first kernel enables), the device-side step rule and, when the
+ * store is full, a sparsification pass. Steps after t_max is reached or after a device error
  * do nothing. dmfe_sync / dmfe_stats read the outcome. Used by benchmarks and by
  * callers that interleave their own work between steps. */
 int dmfe_step(dmfe_solver* h, int nsteps, double t_max, double tol, void* stream);

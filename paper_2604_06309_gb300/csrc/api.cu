@@ -1,6 +1,6 @@
 // Host side of the C ABI declared in include/dmfe.h: solver lifecycle, the integrate
-// loop (one CUDA graph per Dormand-Prince step, step control on the device, the host
-// polls a status word), lookups and checkpoint/restore.
+// loop (one CUDA graph per Runge-Kutta step, step control and the choice of method on
+// the device, the host polls a status word), lookups and checkpoint/restore.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,6 +25,7 @@ struct dmfe_solver {
     bool own_stream = false;
     cudaStream_t cap_stream = nullptr;  // private stream used only to capture the step graph
     cudaGraphExec_t step_exec = nullptr;
+    bool conditional_graph = false;  // the step graph holds the SSPRK stages in an IF node
     int hi_grid = 0;
     size_t hi_smem = 0;
     DevState* hstate = nullptr;  // pinned mirror of the device state
@@ -108,8 +109,45 @@ int validate(const dmfe_params* p) {
     if (!(p->dt0 > 0.0) || !(p->dt_min > 0.0)) return DMFE_ERR_ARG;
     if (p->precision != DMFE_FP64 && p->precision != DMFE_FP32_COMPENSATED && p->precision != DMFE_DOUBLE_FLOAT)
         return DMFE_ERR_ARG;
+    if (p->integrator != DMFE_RK_AUTO && p->integrator != DMFE_RK_DP5 && p->integrator != DMFE_RK_SSPRK104)
+        return DMFE_ERR_ARG;
+    if (!(p->rk_switch_dt >= 0.0)) return DMFE_ERR_ARG;
     if (p->s != 4 && p->s != 6 && p->s != 8 && p->s != 10) return DMFE_ERR_UNSUPPORTED;
     return DMFE_OK;
+}
+
+// Length of the real stability interval of Dormand-Prince 5: the largest x with
+// |R(-y)| <= 1 on [0, x] for its stability polynomial R(z) = sum_{k<=5} z^k/k! + z^6/600
+// (Hairer, Norsett & Wanner, Sec. II.5), by a scan and bisection.
+double dp5_real_stability() {
+    auto R = [](double y) {
+        const double z = -y;
+        const double c[7] = {1.0, 1.0, 1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 600};
+        double r = c[6];
+        for (int k = 5; k >= 0; --k) r = r * z + c[k];
+        return std::fabs(r);
+    };
+    double y = 0.0;
+    const double dy = 1e-3;
+    while (R(y + dy) <= 1.0 + 1e-14) y += dy;
+    double lo = y, hi = y + dy;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (R(mid) <= 1.0) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Controller step at which Dormand-Prince hands over to SSPRK(10,4) (Sec. 3.5): the
+// Jacobian's spectrum lies on the negative real axis within 4 sqrt(f''(1)).
+double switch_dt_for(const dmfe_params* p) {
+    if (p->integrator != DMFE_RK_AUTO) return INFINITY;
+    if (p->rk_switch_dt > 0.0) return p->rk_switch_dt;
+    double fpp1 = 0.0;
+    for (int k = 0; k < p->n_terms; ++k)
+        if (p->powers[k] >= 2) fpp1 += p->coefs[k] * p->powers[k] * (p->powers[k] - 1);
+    if (!(fpp1 > 0.0)) return INFINITY;
+    return dp5_real_stability() / (4.0 * std::sqrt(fpp1));
 }
 
 int create_impl(const dmfe_params* pin, dmfe_solver* h) {
@@ -127,6 +165,7 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
     v.sparsify = pin->sparsify ? 1 : 0;
     v.T = pin->T;
     v.beta0 = pin->beta0;
+    v.rk_switch_dt = switch_dt_for(&h->p);
     build_poly(h->powers, h->coefs, v.poly);
     v.gamma = host_gamma_from_tmax(pin->grid_t_max);
     v.ga = std::atan(std::exp(-v.gamma));
@@ -187,7 +226,7 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
     TRY(dev_alloc(h, &p, (size_t)kCtlGrid * sizeof(double))); v.epart = (double*)p;
     TRY(dev_alloc(h, &p, sizeof(int))); v.ctl_count = (int*)p;
     DMFE_CUDA_TRY(cudaMemsetAsync(v.ctl_count, 0, sizeof(int), h->stream));
-    TRY(dev_alloc(h, &p, 7 * 2 * (size_t)L * sizeof(double))); v.k = (double*)p;
+    TRY(dev_alloc(h, &p, (kMaxStages + 1) * 2 * (size_t)L * sizeof(double))); v.k = (double*)p;
     TRY(dev_alloc(h, &p, 2 * L * sizeof(double))); v.ynew = (double*)p;
     TRY(dev_alloc(h, &p, (size_t)DMFE_NS * L * sizeof(double))); v.S = (double*)p;
     // Partial sums for units of at least kMinChunk summation indices (the smallest chunk
@@ -231,6 +270,8 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
     h->hstate->dt = pin->dt0;
     h->hstate->dt_min = pin->dt_min;
     h->hstate->tol = 1e-8;
+    h->hstate->method = pin->integrator == DMFE_RK_SSPRK104 ? 1 : 0;
+    h->hstate->t_switch = -1.0;
     TRY(write_state(h));
     TRY(launch_tables(v, h->stream));
     TRY(launch_initial_slice(v, h->stream));
@@ -251,26 +292,29 @@ void destroy_impl(dmfe_solver* h) {
     delete h;
 }
 
-// Capture one Dormand-Prince step into a graph on the private capture stream.
+// The three parts of one step of this solver, for the graph capture.
+struct SoloParts : StepParts {
+    const dmfe_solver* h;
+    explicit SoloParts(const dmfe_solver* hh) : h(hh) {}
+    int head(cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) override {
+        return launch_step_head(h->v, h->hi_grid, cond, use_cond, s);
+    }
+    int tail(cudaStream_t s) override { return launch_step_tail(h->v, h->hi_grid, s); }
+    int sp(cudaStream_t s) override { return launch_step_sparsify(h->v, s); }
+};
+
+// Capture one step into a graph on the private capture stream: with the SSPRK stages in
+// a conditional node, or (if the runtime refuses that) inline, where they gate
+// themselves off in Dormand-Prince steps.
 int build_step_graph(dmfe_solver* h) {
     if (h->step_exec) return DMFE_OK;
-    cudaGraph_t g = nullptr;
-    DMFE_CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    int rc = launch_step(h->v, h->hi_grid, h->cap_stream);
-    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
-    if (rc || e != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        cudaGetLastError();
-        return rc ? rc : DMFE_ERR_CUDA;
+    SoloParts parts(h);
+    if (capture_step_graph(h->cap_stream, true, parts, &h->step_exec) == DMFE_OK) {
+        h->conditional_graph = true;
+        return DMFE_OK;
     }
-    e = cudaGraphInstantiate(&h->step_exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-        h->step_exec = nullptr;
-        cudaGetLastError();
-        return DMFE_ERR_CUDA;
-    }
-    return DMFE_OK;
+    h->conditional_graph = false;
+    return capture_step_graph(h->cap_stream, false, parts, &h->step_exec);
 }
 
 int upload_row(dmfe_solver* h, const double* C, const double* R, double* dst) {
@@ -306,6 +350,8 @@ void dmfe_default_params(dmfe_params* p) {
     p->dt_min = 1e-12;
     p->precision = DMFE_FP64;
     p->sparsify = 1;
+    p->integrator = DMFE_RK_AUTO;
+    p->rk_switch_dt = 0.0;
 }
 
 const char* dmfe_strerror(int code) {
@@ -355,7 +401,7 @@ unsigned long long dmfe_footprint(const dmfe_params* pin) {
     }
     add(sizeof(DevState)); add(4 * L * 8);
     add(2ull * kMaxPrepBlocks * 8); add(kCtlGrid * 8); add(4);
-    add(14 * L * 8); add(2 * L * 8); add(DMFE_NS * L * 8);
+    add(2ull * (kMaxStages + 1) * L * 8); add(2 * L * 8); add(DMFE_NS * L * 8);
     add((L / kMinChunk > 1 ? L / kMinChunk : 1) * 9 * L * 8); add(L * sizeof(B1Desc));
     if (p.precision != DMFE_DOUBLE_FLOAT) add(L * 4);
     add(L * 4); add(cap * 8); add(cap * 4); add(cap * 4); add((4 * L + 16) * 8);
@@ -656,6 +702,10 @@ int dmfe_stats(dmfe_solver* h, dmfe_stats_t* o) {
     o->history_cap = h->v.cap;
     o->s = h->v.s;
     o->precision = h->v.precision;
+    o->method = s.method == 1 ? DMFE_RK_SSPRK104 : DMFE_RK_DP5;
+    o->t_switch = s.t_switch;
+    o->rk_switch_dt = h->v.rk_switch_dt;
+    o->step_graph = h->step_exec ? (h->conditional_graph ? 2 : 1) : 0;
     return DMFE_OK;
 }
 
@@ -748,7 +798,8 @@ int dmfe_sync(dmfe_solver* h) {
 }
 
 // ---- checkpoint format: magic, version, parameters, f, device state, history (FP64).
-static const char kMagic[8] = {'D', 'M', 'F', 'E', 'C', 'K', 'P', '1'};
+static const char kMagic[8] = {'D', 'M', 'F', 'E', 'C', 'K', 'P', '2'};
+static const int kCkpVersion = 2;  // 2: integrator fields in the parameters and the state
 
 int dmfe_checkpoint(dmfe_solver* h, const char* path) {
     if (!h || !path) return DMFE_ERR_ARG;
@@ -764,7 +815,7 @@ int dmfe_checkpoint(dmfe_solver* h, const char* path) {
     if (!f) return DMFE_ERR_IO;
     bool ok = true;
     auto W = [&](const void* p, size_t n) { ok = ok && std::fwrite(p, 1, n, f) == n; };
-    const int version = 1;
+    const int version = kCkpVersion;
     dmfe_params p = h->p;
     p.powers = nullptr;
     p.coefs = nullptr;
@@ -794,7 +845,7 @@ int dmfe_restore(const char* path, void* stream, dmfe_solver** out) {
     R(magic, 8);
     R(&version, sizeof(int));
     R(&p, sizeof(p));
-    if (!ok || std::memcmp(magic, kMagic, 8) != 0 || version != 1 || p.n_terms < 1 || p.n_terms > DMFE_MAX_TERMS) {
+    if (!ok || std::memcmp(magic, kMagic, 8) != 0 || version != kCkpVersion || p.n_terms < 1 || p.n_terms > DMFE_MAX_TERMS) {
         std::fclose(f);
         return DMFE_ERR_IO;
     }

@@ -1,5 +1,6 @@
 // Batched solves: a table of slots in device memory, one captured graph per batched
-// Dormand-Prince step (launch_batch_step), admission and release of slots between steps.
+// Runge-Kutta step (slots may be in Dormand-Prince or SSPRK(10,4) steps), admission and
+// release of slots between steps.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -70,26 +71,25 @@ int upload_table(dmfe_batch* b) {
     return DMFE_OK;
 }
 
+struct BatchParts : StepParts {
+    const dmfe_batch* b;
+    explicit BatchParts(const dmfe_batch* bb) : b(bb) {}
+    int head(cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) override {
+        return launch_batch_step_head(b->d_table, b->precision, b->s, b->max_L, b->max_cap, b->max_slots,
+                                      b->hi_grid, b->hi_smem, cond, use_cond, s);
+    }
+    int tail(cudaStream_t s) override {
+        return launch_batch_step_tail(b->d_table, b->precision, b->s, b->max_L, b->max_cap, b->max_slots,
+                                      b->hi_grid, b->hi_smem, s);
+    }
+    int sp(cudaStream_t s) override { return launch_batch_step_sparsify(b->d_table, b->max_cap, b->max_slots, s); }
+};
+
 int build_graph(dmfe_batch* b) {
     if (b->exec) return DMFE_OK;
-    cudaGraph_t g = nullptr;
-    DMFE_CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-    const int rc = launch_batch_step(b->d_table, b->precision, b->s, b->max_L, b->max_cap, b->max_slots,
-                                     b->hi_grid, b->hi_smem, b->cap_stream);
-    const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
-    if (rc || e != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        cudaGetLastError();
-        return rc ? rc : DMFE_ERR_CUDA;
-    }
-    const cudaError_t e2 = cudaGraphInstantiate(&b->exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e2 != cudaSuccess) {
-        b->exec = nullptr;
-        cudaGetLastError();
-        return DMFE_ERR_CUDA;
-    }
-    return DMFE_OK;
+    BatchParts parts(b);
+    if (capture_step_graph(b->cap_stream, true, parts, &b->exec) == DMFE_OK) return DMFE_OK;
+    return capture_step_graph(b->cap_stream, false, parts, &b->exec);
 }
 
 }  // namespace

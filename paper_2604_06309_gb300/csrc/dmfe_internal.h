@@ -91,12 +91,30 @@ struct DevState {
     int removed_count;   // slices removed by the last pass
     int sp_ran;          // 1 between the select and finish kernels of a pass
     int n_new;           // slice count after the pass
+    int method;          // integrator of the next step: 0 Dormand-Prince 5(4), 1 SSPRK(10,4)
+    int rk;              // integrator of the step in progress (set by its first kernel)
+    int nst;             // its number of stage evaluations (6 or 10)
+    int pad_;
+    double t_switch;     // time of the switch to SSPRK(10,4), -1 if none
 };
+
+constexpr int kMaxStages = 10;  // stage evaluations per step of the longest method
+constexpr int kDP5Stages = 6;   // stage evaluations per Dormand-Prince step
+
+#if defined(__CUDACC__)
+// Gate of the kernels of stage `stage` (>= 1) of a step: they do nothing once the solve
+// has stopped (error or target reached) or when the step's method has fewer stages.
+// stage == 0 marks an explicit call outside the step loop (never gated).
+__device__ __forceinline__ bool stage_off(const DevState* st, int stage) {
+    return stage > 0 && (st->status != 0 || st->done || stage > st->nst);
+}
+#endif
 
 // Everything a kernel needs about one solver (passed by value).
 struct SolverView {
     int L, s, cap, precision;
     int sparsify;         // 1: pass when the store is full
+    double rk_switch_dt;  // controller step of the switch to SSPRK(10,4) (+inf: never)
     double T, beta0;
     double gamma, ga, gD, alpha, delta;  // grid: gamma, atan(e^-gamma), atan(e^gamma) - atan(e^-gamma)
     Poly poly;
@@ -134,7 +152,7 @@ struct SolverView {
     double* mupart;       // [2][kMaxPrepBlocks] per-block partial sums of mu's and E's integrands
     double* epart;        // [kCtlGrid] per-CTA partial sums of the step error
     int* ctl_count;       // CTAs finished in the last stage of a step (zero between steps)
-    double* k;            // [7][2L] stage derivatives
+    double* k;            // [kMaxStages + 1][2L] stage derivatives
     double* ynew;         // [2L] 5th-order solution of the trial step
     double* S;            // [NS][L]
     double* Spart;        // [parts][9][L] partial sums of the chunks of the i-range
@@ -152,6 +170,9 @@ struct BatchTable {
     int pad;
     long long uoff[kMaxSlots + 1];  // history-integral unit offsets (0 units: idle slot)
     long long woff[kMaxSlots + 1];  // work (pair) offsets: CTAs split the batch by work
+    long long woff_late[kMaxSlots + 1];  // the same over the slots whose step runs more than
+                                         // kDP5Stages stages (written on the device by the
+                                         // first kernel of every batched step)
     int active[kMaxSlots];          // 1: slot holds a solver
     SolverView views[kMaxSlots];
 };
@@ -166,12 +187,18 @@ constexpr int kCtlGrid = 64;          // their maximal grid
 int launch_tables(const SolverView& v, cudaStream_t s);
 // history integrals: row_dev = [2L] (C, R); t_dev != NULL reads the stage time from
 // device memory (integrate loop) and gates on the status word; otherwise uses t.
-int launch_history_integrals(const SolverView& v, const double* row_dev, double t, bool from_state,
+int launch_history_integrals(const SolverView& v, const double* row_dev, double t, int stage,
                              double* S_dev, int grid_ctas, cudaStream_t s);
 int hi_config(const SolverView& v, int* grid_ctas, size_t* smem);
 int launch_assemble(const SolverView& v, const double* row_dev, const double* S_dev, double t,
                     double* dC, double* dR, double* muE, cudaStream_t s);
+// one trial step: head = begin + stages 1..kDP5Stages, tail = the later stages (SSPRK),
+// then the sparsification kernels; launch_step issues all three
 int launch_step(const SolverView& v, int grid_ctas, cudaStream_t s);
+int launch_step_head(const SolverView& v, int grid_ctas, cudaGraphConditionalHandle cond, int use_cond,
+                     cudaStream_t s);
+int launch_step_tail(const SolverView& v, int grid_ctas, cudaStream_t s);
+int launch_step_sparsify(const SolverView& v, cudaStream_t s);
 int launch_begin_integrate(const SolverView& v, double t_target, double tol, cudaStream_t s);
 int launch_initial_slice(const SolverView& v, cudaStream_t s);
 int launch_sparsify(const SolverView& v, bool from_step, double tol, cudaStream_t s);
@@ -179,9 +206,9 @@ int launch_lookup(const SolverView& v, int n, const double* t, const double* tp,
                   double* out, cudaStream_t s);
 int launch_refresh_replica(const SolverView& v, cudaStream_t s);
 // per-stage preparation for every precision (kernels_df.cu)
-int launch_stage_prep(const SolverView& v, const double* row_dev, double t, bool from_state, cudaStream_t s);
+int launch_stage_prep(const SolverView& v, const double* row_dev, double t, int stage, cudaStream_t s);
 // double-float path (kernels_df.cu)
-int launch_history_integrals_df(const SolverView& v, const double* row_dev, double t, bool from_state,
+int launch_history_integrals_df(const SolverView& v, const double* row_dev, double t, int stage,
                                 double* S_dev, int grid_ctas, cudaStream_t s);
 int hi_config_df(const SolverView& v, int* grid_ctas, size_t* smem);
 
@@ -191,8 +218,23 @@ int batch_hi_config_df(int sw, int max_L, int max_cap, int* grid_ctas, size_t* s
 int launch_batch_hi(const BatchTable* bt, int precision, int sw, int stg, int grid, size_t smem, cudaStream_t s);
 int launch_batch_hi_df(const BatchTable* bt, int sw, int stg, int grid, size_t smem, cudaStream_t s);
 int launch_batch_prep(const BatchTable* bt, int stg, int max_tot, int slots, cudaStream_t s);
-int launch_batch_step(const BatchTable* bt, int precision, int sw, int max_L, int max_cap, int slots,
-                      int hi_grid, size_t hi_smem, cudaStream_t s);
+int launch_batch_step_head(const BatchTable* bt, int precision, int sw, int max_L, int max_cap, int slots,
+                           int hi_grid, size_t hi_smem, cudaGraphConditionalHandle cond, int use_cond,
+                           cudaStream_t s);
+int launch_batch_step_tail(const BatchTable* bt, int precision, int sw, int max_L, int max_cap, int slots,
+                           int hi_grid, size_t hi_smem, cudaStream_t s);
+int launch_batch_step_sparsify(const BatchTable* bt, int max_cap, int slots, cudaStream_t s);
+
+// Capture one step into an executable graph on stream `cap`: head(cond, use_cond, stream),
+// then tail(stream) inside a conditional IF node that the head's first kernel enables
+// (if `conditional`; otherwise inline), then sp(stream). (graph.cu)
+struct StepParts {
+    virtual int head(cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) = 0;
+    virtual int tail(cudaStream_t s) = 0;
+    virtual int sp(cudaStream_t s) = 0;
+    virtual ~StepParts() = default;
+};
+int capture_step_graph(cudaStream_t cap, bool conditional, StepParts& parts, cudaGraphExec_t* out);
 // accessors of a solver's internals (api.cu)
 struct dmfe_solver;
 const SolverView& solver_view(const dmfe_solver* h);

@@ -75,14 +75,16 @@ __device__ __forceinline__ void load_view(SolverView& dst, const SolverView& src
 // Work-balanced share of a batch for this CTA: the pairs of all slots are split evenly
 // over the CTAs and each slot's share is mapped to its units in proportion (a slot's
 // units carry nearly equal work). Calls f(k, lb, le) for every slot k with units [lb, le).
+// Stages beyond the Dormand-Prince ones split only the slots that run them (woff_late).
 template <typename F>
-__device__ __forceinline__ void batch_for_my_units(const BatchTable* bt, F&& f) {
-    const long long W = bt->woff[bt->count];
+__device__ __forceinline__ void batch_for_my_units(const BatchTable* bt, int stg, F&& f) {
+    const long long* woff = stg > kDP5Stages ? bt->woff_late : bt->woff;
+    const long long W = woff[bt->count];
     const long long g0 = W * blockIdx.x / gridDim.x, g1 = W * (blockIdx.x + 1) / gridDim.x;
     int k = 0;
-    while (k < bt->count && bt->woff[k + 1] <= g0) ++k;
-    for (; k < bt->count && bt->woff[k] < g1; ++k) {
-        const long long o = bt->woff[k], Wk = bt->woff[k + 1] - o;
+    while (k < bt->count && woff[k + 1] <= g0) ++k;
+    for (; k < bt->count && woff[k] < g1; ++k) {
+        const long long o = woff[k], Wk = woff[k + 1] - o;
         if (Wk <= 0) continue;
         const long long Uk = bt->uoff[k + 1] - bt->uoff[k];
         const long long a = (g0 > o ? g0 : o) - o, e = (g1 < o + Wk ? g1 : o + Wk) - o;

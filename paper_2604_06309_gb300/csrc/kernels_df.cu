@@ -36,7 +36,7 @@ __device__ __forceinline__ int find_slice_g(const double* ht, int n, double tau)
 __device__ __forceinline__ void stage_prep_body(const SolverView& v, const double* __restrict__ row, double t_arg,
                                                 int from_state) {
     const DevState* st = v.st;
-    if (from_state && (st->status != 0 || st->done)) return;
+    if (stage_off(st, from_state)) return;
     const int L = v.L, n = st->n, act = st->active;
     const double t = from_state ? st->t_stage : t_arg;
     const double* ht = v.ht[act];
@@ -201,7 +201,7 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
                                            int ub, int ue) {
     extern __shared__ __align__(32) unsigned char smraw[];
     const DevState* st = v.st;
-    if (from_state && (st->status != 0 || st->done)) return;
+    if (stage_off(st, from_state)) return;
     const int L = v.L, n = st->n, act = st->active;
     const double t = from_state ? st->t_stage : t_arg;
     const df8* __restrict__ H = v.histdf[act];
@@ -446,17 +446,17 @@ __global__ void k_batch_prep(const BatchTable* __restrict__ bt, int stg) {
     const int k = blockIdx.y;
     if (k >= bt->count || !bt->active[k]) return;
     const SolverView& v = bt->views[k];
-    stage_prep_body(v, v.Y + (size_t)(stg & 1) * 2 * v.L, 0.0, 1);
+    stage_prep_body(v, v.Y + (size_t)(stg & 1) * 2 * v.L, 0.0, stg);
 }
 
 template <int SW>
 __global__ void __launch_bounds__(DF_THREADS, 1) k_batch_hi_df(const BatchTable* __restrict__ bt, int stg) {
     __shared__ __align__(16) SolverView sview;
-    batch_for_my_units(bt, [&](int k, int lb, int le) {
+    batch_for_my_units(bt, stg, [&](int k, int lb, int le) {
         __syncthreads();  // the previous slot's shared-memory data are no longer read
         load_view(sview, bt->views[k]);
         __syncthreads();
-        hi_df_body<SW>(sview, 0.0, 1, sview.S, lb, le);
+        hi_df_body<SW>(sview, 0.0, stg, sview.S, lb, le);
     });
 }
 
@@ -477,9 +477,9 @@ void* df_kernel_for(int s) {
 
 }  // namespace
 
-int launch_stage_prep(const SolverView& v, const double* row_dev, double t, bool from_state, cudaStream_t s) {
+int launch_stage_prep(const SolverView& v, const double* row_dev, double t, int stage, cudaStream_t s) {
     const int tot = v.L > v.cap ? v.L : v.cap;
-    k_stage_prep<<<(tot + kPrepThreads - 1) / kPrepThreads, kPrepThreads, 0, s>>>(v, row_dev, t, from_state ? 1 : 0);
+    k_stage_prep<<<(tot + kPrepThreads - 1) / kPrepThreads, kPrepThreads, 0, s>>>(v, row_dev, t, stage);
     DMFE_CUDA_TRY(cudaGetLastError());
     return DMFE_OK;
 }
@@ -505,12 +505,12 @@ int hi_config_df(const SolverView& v, int* grid_ctas, size_t* smem) {
     return DMFE_OK;
 }
 
-int launch_history_integrals_df(const SolverView& v, const double* row_dev, double t, bool from_state,
+int launch_history_integrals_df(const SolverView& v, const double* row_dev, double t, int stage,
                                 double* S_dev, int grid_ctas, cudaStream_t s) {
     void* fn = df_kernel_for(v.s);
     if (!fn) return DMFE_ERR_UNSUPPORTED;
-    const int fs = from_state ? 1 : 0;
-    int rc = launch_stage_prep(v, row_dev, t, from_state, s);
+    const int fs = stage;
+    int rc = launch_stage_prep(v, row_dev, t, stage, s);
     if (rc) return rc;
     const size_t sm = df_smem_bytes(v);
     void* args[] = {(void*)&v, (void*)&t, (void*)&fs, (void*)&S_dev};

@@ -121,7 +121,7 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
                                             int from_state, double* __restrict__ S, int ub, int ue) {
     extern __shared__ __align__(32) unsigned char smraw[];
     const DevState* st = v.st;
-    if (from_state && (st->status != 0 || st->done)) return;
+    if (stage_off(st, from_state)) return;
     const int L = v.L;
     const int n = st->n;
     const int act = st->active;
@@ -292,7 +292,7 @@ __device__ __forceinline__ void hi_f32_body(const SolverView& v, const double* _
                                             int from_state, double* __restrict__ S, int ub, int ue) {
     extern __shared__ __align__(32) unsigned char smraw[];
     const DevState* st = v.st;
-    if (from_state && (st->status != 0 || st->done)) return;
+    if (stage_off(st, from_state)) return;
     const int L = v.L;
     const int n = st->n;
     const int act = st->active;
@@ -489,14 +489,14 @@ __global__ void __launch_bounds__(HI_THREADS, 1) k_hi_f32(SolverView v, const do
 template <int SW, int PREC>
 __global__ void __launch_bounds__(HI_THREADS, 1) k_batch_hi(const BatchTable* __restrict__ bt, int stg) {
     __shared__ __align__(16) SolverView sview;
-    batch_for_my_units(bt, [&](int k, int lb, int le) {
+    batch_for_my_units(bt, stg, [&](int k, int lb, int le) {
         __syncthreads();  // the previous slot's shared-memory data are no longer read
         load_view(sview, bt->views[k]);
         __syncthreads();
         const SolverView& v = sview;
         const double* row = v.Y + (size_t)(stg & 1) * 2 * v.L;
-        if (PREC == DMFE_FP64) hi_f64_body<SW>(v, row, 0.0, 1, v.S, lb, le);
-        else hi_f32_body<SW>(v, row, 0.0, 1, v.S, lb, le);
+        if (PREC == DMFE_FP64) hi_f64_body<SW>(v, row, 0.0, stg, v.S, lb, le);
+        else hi_f32_body<SW>(v, row, 0.0, stg, v.S, lb, le);
     });
 }
 
@@ -546,16 +546,16 @@ int hi_config(const SolverView& v, int* grid_ctas, size_t* smem) {
     return DMFE_OK;
 }
 
-int launch_history_integrals(const SolverView& v, const double* row_dev, double t, bool from_state,
+int launch_history_integrals(const SolverView& v, const double* row_dev, double t, int stage,
                              double* S_dev, int grid_ctas, cudaStream_t s) {
     if (v.precision == DMFE_DOUBLE_FLOAT)
-        return launch_history_integrals_df(v, row_dev, t, from_state, S_dev, grid_ctas, s);
+        return launch_history_integrals_df(v, row_dev, t, stage, S_dev, grid_ctas, s);
     void* fn = hi_kernel_for(v);
     if (!fn) return DMFE_ERR_UNSUPPORTED;
-    int rc = launch_stage_prep(v, row_dev, t, from_state, s);
+    int rc = launch_stage_prep(v, row_dev, t, stage, s);
     if (rc) return rc;
     size_t sm = hi_smem_bytes(v);
-    int fs = from_state ? 1 : 0;
+    int fs = stage;
     void* args[] = {(void*)&v, (void*)&row_dev, (void*)&t, (void*)&fs, (void*)&S_dev};
     DMFE_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid_ctas), dim3(HI_THREADS), args, sm, s));
     return DMFE_OK;

@@ -2,8 +2,9 @@
 //   (a)  stencil tables: fractional grid index of phi1, phi2 and psi for every (j, i)
 //        (Sec. 3.3, the precomputed theta-interpolation positions),
 //   RHS assembly: mu(t), E(t) and the total derivatives at fixed theta (Sec. 2.1),
-//   (c)  Dormand-Prince 5(4) stage combination, error estimate and the step rule with
-//        rollback (Sec. 3.5), all decided on the device,
+//   (c)  Runge-Kutta stage combination (Dormand-Prince 5(4) or SSPRK(10,4)), error
+//        estimate, the step rule with rollback and the switch between the two
+//        methods (Sec. 3.5), all decided on the device,
 //   (d)  sparsification (Sec. 3.6): residuals of every candidate slice, the greedy
 //        "remove n, skip n+1" selection, and compaction into the other history buffer,
 //   two-time lookups C(t,t'), R(t,t') for the API.
@@ -18,21 +19,55 @@ namespace {
 
 constexpr int CTL_THREADS = 1024;
 
-// Dormand & Prince (1980) RK5(4)7M coefficients. Stage l of the seven uses row l of A.
-__constant__ double kDP_C[7] = {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0};
-__constant__ double kDP_A[7][6] = {
-    {0, 0, 0, 0, 0, 0},
-    {1.0 / 5, 0, 0, 0, 0, 0},
-    {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
-    {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
-    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
-    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
-    {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84},
+// Explicit Runge-Kutta pairs in first-same-as-last form (Sec. 3.5). Stage 0 is the
+// stored derivative of the last slice; stage st = 1..n is evaluated at t + c[st] h on
+// Y_st = y + h sum_{l < st} a[st][l] k_l. Row a[n] is the propagating weight vector,
+// so Y_n is the new slice and k_n its derivative; the error estimate is
+// h sum_{l <= n} e[l] k_l.
+struct RKTab {
+    int n;
+    double c[kMaxStages + 1];
+    double a[kMaxStages + 1][kMaxStages];
+    double e[kMaxStages + 1];
 };
-// e = b5 - b4 (embedded error weights)
-__constant__ double kDP_E[7] = {35.0 / 384 - 5179.0 / 57600, 0.0, 500.0 / 1113 - 7571.0 / 16695,
-                                125.0 / 192 - 393.0 / 640, -2187.0 / 6784 + 92097.0 / 339200,
-                                11.0 / 84 - 187.0 / 2100, -1.0 / 40};
+
+// [0] Dormand & Prince (1980) RK5(4)7M, e = b5 - b4.
+// [1] SSPRK(10,4) of Ketcheson (2008): in low-storage form five Euler substeps of h/6,
+//     registers recombined as q2 = q2/25 + 9 q1/25, q1 = 15 q2 - 5 q1, four more
+//     substeps and u = q2 + 3 q1/5 + h/10 f(q1); as a Butcher tableau the rows below,
+//     uniform weights 1/10. Embedded estimate: the third-order weights of minimal
+//     2-norm on the same stages with a zero last weight,
+//     bhat = (3/20, 1/12, 7/120, 3/40, 2/15, 7/120, 3/40, 2/15, 7/30, 0), e = b - bhat.
+__constant__ RKTab kRK[2] = {
+    {6,
+     {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0},
+     {{0},
+      {1.0 / 5},
+      {3.0 / 40, 9.0 / 40},
+      {44.0 / 45, -56.0 / 15, 32.0 / 9},
+      {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729},
+      {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656},
+      {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}},
+     {35.0 / 384 - 5179.0 / 57600, 0.0, 500.0 / 1113 - 7571.0 / 16695, 125.0 / 192 - 393.0 / 640,
+      -2187.0 / 6784 + 92097.0 / 339200, 11.0 / 84 - 187.0 / 2100, -1.0 / 40}},
+    {10,
+     {0.0, 1.0 / 6, 2.0 / 6, 3.0 / 6, 4.0 / 6, 1.0 / 3, 1.0 / 2, 2.0 / 3, 5.0 / 6, 1.0, 1.0},
+     {{0},
+      {1.0 / 6},
+      {1.0 / 6, 1.0 / 6},
+      {1.0 / 6, 1.0 / 6, 1.0 / 6},
+      {1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6},
+      {1.0 / 15, 1.0 / 15, 1.0 / 15, 1.0 / 15, 1.0 / 15},
+      {1.0 / 15, 1.0 / 15, 1.0 / 15, 1.0 / 15, 1.0 / 15, 1.0 / 6},
+      {1.0 / 15, 1.0 / 15, 1.0 / 15, 1.0 / 15, 1.0 / 15, 1.0 / 6, 1.0 / 6},
+      {1.0 / 15, 1.0 / 15, 1.0 / 15, 1.0 / 15, 1.0 / 15, 1.0 / 6, 1.0 / 6, 1.0 / 6},
+      {1.0 / 15, 1.0 / 15, 1.0 / 15, 1.0 / 15, 1.0 / 15, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6},
+      {1.0 / 10, 1.0 / 10, 1.0 / 10, 1.0 / 10, 1.0 / 10, 1.0 / 10, 1.0 / 10, 1.0 / 10, 1.0 / 10,
+       1.0 / 10}},
+     {1.0 / 10 - 3.0 / 20, 1.0 / 10 - 1.0 / 12, 1.0 / 10 - 7.0 / 120, 1.0 / 10 - 3.0 / 40,
+      1.0 / 10 - 2.0 / 15, 1.0 / 10 - 7.0 / 120, 1.0 / 10 - 3.0 / 40, 1.0 / 10 - 2.0 / 15,
+      1.0 / 10 - 7.0 / 30, 1.0 / 10, 0.0}},
+};
 
 // ---------------------------------------------------------------- grid inverse
 __device__ double z_of_i_dev(double i, int L, double alpha, double delta) {
@@ -242,12 +277,15 @@ __global__ void __launch_bounds__(CTL_THREADS) k_begin_integrate(SolverView v, d
     st->done = (st->t >= t_target) ? 1 : 0;
 }
 
-// Start of a trial step (multi-CTA): h = min(dt, t_target - t), k_1 = stored derivative of
-// the last slice (first-same-as-last), stage-1 row Y_1 = y + h a_10 k_1 into buffer 1.
+// Start of a trial step (multi-CTA): the method of the step (fixed until the step ends),
+// h = min(dt, t_target - t), k_0 = stored derivative of the last slice
+// (first-same-as-last), stage-1 row Y_1 = y + h a_10 k_0 into buffer 1.
 __device__ __forceinline__ void step_begin_body(const SolverView& v, int cta, int ncta) {
     DevState* st = v.st;
     if (gated(st)) return;
     const int L = v.L;
+    const int m = st->method;
+    const RKTab& M = kRK[m];
     const dbl4* yrow = v.hist[st->active] + (size_t)(st->n - 1) * L;
     const double t = st->t;
     const double h = fmin(st->dt, st->t_target - t);
@@ -256,32 +294,37 @@ __device__ __forceinline__ void step_begin_body(const SolverView& v, int cta, in
         const dbl4 e = yrow[j];
         v.k[j] = e.y;
         v.k[L + j] = e.w;
-        Y1[j] = __dadd_rn(e.x, __dmul_rn(h, __dmul_rn(kDP_A[1][0], e.y)));
-        Y1[L + j] = __dadd_rn(e.z, __dmul_rn(h, __dmul_rn(kDP_A[1][0], e.w)));
+        Y1[j] = __dadd_rn(e.x, __dmul_rn(h, __dmul_rn(M.a[1][0], e.y)));
+        Y1[L + j] = __dadd_rn(e.z, __dmul_rn(h, __dmul_rn(M.a[1][0], e.w)));
     }
     if (cta == 0 && threadIdx.x == 0) {
+        st->rk = m;
+        st->nst = M.n;
         st->h = h;
-        st->t_stage = __dadd_rn(t, __dmul_rn(kDP_C[1], h));
+        st->t_stage = __dadd_rn(t, __dmul_rn(M.c[1], h));
     }
 }
 
-// End of stage stg (1..6), multi-CTA: k_stg from the sums S and the stage row (read from
-// buffer stg & 1); then either the next stage row (written to the other buffer) or,
-// after the last stage, the error estimate, whose per-CTA partials the last CTA to
-// finish adds in a fixed order before taking the step decision of Sec. 3.5 and
-// appending the slice. mu and E come from the per-block partial sums of the prep kernel.
+// End of stage stg (1..n of the step's method), multi-CTA: k_stg from the sums S and the
+// stage row (read from buffer stg & 1); then either the next stage row (written to the
+// other buffer) or, after the last stage, the error estimate, whose per-CTA partials
+// the last CTA to finish adds in a fixed order before taking the step decision of
+// Sec. 3.5 (and the switch to SSPRK(10,4)) and appending the slice. mu and E come from
+// the per-block partial sums of the prep kernel.
 __device__ __forceinline__ void stage_end_body(const SolverView& v, int stg, int prep_blocks, int cta, int ncta) {
     __shared__ double s_mu, s_E, red[kCtlThreads];
     __shared__ int s_last, s_append;
     DevState* st = v.st;
-    if (gated(st)) return;
+    if (stage_off(st, stg)) return;
+    const RKTab& M = kRK[st->rk];
+    const int nst = M.n;
     const int L = v.L;
     const int L2 = 2 * L;
     const int act = st->active;
     const int n = st->n;
     const dbl4* yrow = v.hist[act] + (size_t)(n - 1) * L;
     const double t = st->t, h = st->h;
-    const double ts = __dadd_rn(t, __dmul_rn(kDP_C[stg], h));  // this stage's time
+    const double ts = __dadd_rn(t, __dmul_rn(M.c[stg], h));  // this stage's time
     const double* Yc = v.Y + (size_t)(stg & 1) * L2;
     double* Yn = v.Y + (size_t)((stg + 1) & 1) * L2;
     const double C0 = Yc[0];
@@ -313,12 +356,12 @@ __device__ __forceinline__ void stage_end_body(const SolverView& v, int stg, int
         const bool diag = (j == L - 1);
         kC[j] = diag ? 0.0 : d1C + th * d2C;
         kC[L + j] = diag ? 0.0 : d1R + th * d2R;
-        if (stg < 6) {
-            // next stage row Y = y + h sum_{l <= stg} A[stg+1][l] k_l, rounded like the plain sum
+        if (stg < nst) {
+            // next stage row Y = y + h sum_{l <= stg} a[stg+1][l] k_l, rounded like the plain sum
             for (int half = 0; half < 2; ++half) {
                 const int q = j + half * L;
                 double acc = 0.0;
-                for (int l = 0; l <= stg; ++l) acc = __dadd_rn(acc, __dmul_rn(kDP_A[stg + 1][l], v.k[(size_t)l * L2 + q]));
+                for (int l = 0; l <= stg; ++l) acc = __dadd_rn(acc, __dmul_rn(M.a[stg + 1][l], v.k[(size_t)l * L2 + q]));
                 const double y = half == 0 ? yrow[j].x : yrow[j].z;
                 Yn[q] = __dadd_rn(y, __dmul_rn(h, acc));
             }
@@ -327,15 +370,15 @@ __device__ __forceinline__ void stage_end_body(const SolverView& v, int stg, int
             for (int half = 0; half < 2; ++half) {
                 const int q = j + half * L;
                 double acc = 0.0;
-                for (int l = 0; l < 7; ++l) acc = __dadd_rn(acc, __dmul_rn(kDP_E[l], v.k[(size_t)l * L2 + q]));
+                for (int l = 0; l <= nst; ++l) acc = __dadd_rn(acc, __dmul_rn(M.e[l], v.k[(size_t)l * L2 + q]));
                 pe += fabs(__dmul_rn(h, acc));
             }
         }
     }
-    if (stg < 6) {
+    if (stg < nst) {
         if (cta == 0 && threadIdx.x == 0) {
             st->stages += 1;
-            st->t_stage = __dadd_rn(t, __dmul_rn(kDP_C[stg + 1], h));
+            st->t_stage = __dadd_rn(t, __dmul_rn(M.c[stg + 1], h));
         }
         return;
     }
@@ -379,13 +422,20 @@ __device__ __forceinline__ void stage_end_body(const SolverView& v, int stg, int
             }
             if (eps > tol) st->dt *= 0.9;
             else if (eps < 0.5 * tol) st->dt *= 1.01;
+            if (st->rk == 0 && st->dt >= v.rk_switch_dt) {
+                // Dormand-Prince has reached its stability limit: SSPRK(10,4) from the
+                // next step on, with the step halved
+                st->method = 1;
+                st->dt *= 0.5;
+                st->t_switch = tnew;
+            }
         }
         if (st->status == 0 && st->dt < st->dt_min) st->status = DMFE_ERR_STEP_UNDERFLOW;
     }
     __syncthreads();
     if (s_append >= 0) {
-        // the 5th-order solution Y_6 sits in buffer 0, its derivative k_7 in k[6]
-        append_slice(v, act, s_append, st->t_pending, v.Y, v.k + (size_t)6 * L2);
+        // the new solution Y_n sits in buffer n & 1, its derivative in k[n]
+        append_slice(v, act, s_append, st->t_pending, v.Y + (size_t)(nst & 1) * L2, v.k + (size_t)nst * L2);
         __syncthreads();
         if (threadIdx.x == 0) {
             st->n = s_append + 1;
@@ -400,14 +450,36 @@ __device__ __forceinline__ int ctl_grid(int L) {
     return g < 1 ? 1 : (g > kCtlGrid ? kCtlGrid : g);
 }
 
-__global__ void __launch_bounds__(kCtlThreads) k_step_begin(SolverView v) { step_begin_body(v, blockIdx.x, gridDim.x); }
+// use_cond: the launch belongs to a step graph whose stages beyond kDP5Stages sit in a
+// conditional node with handle `cond`; one thread enables it for a live SSPRK step.
+__global__ void __launch_bounds__(kCtlThreads) k_step_begin(SolverView v, cudaGraphConditionalHandle cond,
+                                                            int use_cond) {
+    step_begin_body(v, blockIdx.x, gridDim.x);
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0 && !gated(v.st) && kRK[v.st->method].n > kDP5Stages)
+        cudaGraphSetConditional(cond, 1u);
+}
 
 __global__ void __launch_bounds__(kCtlThreads) k_stage_end(SolverView v, int stg, int prep_blocks) {
     stage_end_body(v, stg, prep_blocks, blockIdx.x, gridDim.x);
 }
 
 // Batched wrappers: blockIdx.y is the slot; each slot keeps its own CTA partition.
-__global__ void __launch_bounds__(kCtlThreads) k_batch_step_begin(const BatchTable* __restrict__ bt) {
+__global__ void __launch_bounds__(kCtlThreads) k_batch_step_begin(const BatchTable* __restrict__ bt,
+                                                                  cudaGraphConditionalHandle cond, int use_cond) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        // work offsets of the slots whose step has stages beyond the Dormand-Prince ones
+        // (their method does not change while the step runs), and the graph condition
+        long long* wl = const_cast<BatchTable*>(bt)->woff_late;
+        long long w = 0;
+        for (int q = 0; q < bt->count; ++q) {
+            wl[q] = w;
+            if (!bt->active[q]) continue;
+            const SolverView& vq = bt->views[q];
+            if (!gated(vq.st) && kRK[vq.st->method].n > kDP5Stages) w += (long long)vq.L * vq.L;
+        }
+        wl[bt->count] = w;
+        if (use_cond) cudaGraphSetConditional(cond, w > 0 ? 1u : 0u);
+    }
     const int k = blockIdx.y;
     if (k >= bt->count || !bt->active[k]) return;
     const SolverView& v = bt->views[k];
@@ -540,7 +612,10 @@ __device__ __forceinline__ void sp_finish_body(const SolverView& v) {
     const int nn = st->n_new;
     const bool pend = st->pending != 0;
     __syncthreads();
-    if (pend) append_slice(v, nxt, nn, st->t_pending, v.Y, v.k + (size_t)6 * 2 * v.L);
+    // the accepted solution of the step that left the slice pending: Y_n in buffer n & 1,
+    // its derivative in k[n] (n = the step's stage count)
+    const int nst = st->nst;
+    if (pend) append_slice(v, nxt, nn, st->t_pending, v.Y + (size_t)(nst & 1) * 2 * v.L, v.k + (size_t)nst * 2 * v.L);
     __syncthreads();
     if (threadIdx.x == 0) {
         st->active = nxt;
@@ -681,21 +756,46 @@ int launch_sparsify(const SolverView& v, bool from_step, double tol, cudaStream_
     return DMFE_OK;
 }
 
-// One Dormand-Prince step: begin, six stages of (history integrals, stage end), then the
-// sparsification kernels, which do nothing unless the step left a slice pending.
-int launch_step(const SolverView& v, int grid_ctas, cudaStream_t s) {
-    int g = (v.L + kCtlThreads - 1) / kCtlThreads;
-    g = g < 1 ? 1 : (g > kCtlGrid ? kCtlGrid : g);
+// One trial step, in three parts so that a graph can put the stages beyond the
+// Dormand-Prince ones into a conditional node: the head (begin and stages 1..6), the
+// tail (stages 7..10, which do nothing in a Dormand-Prince step) and the sparsification
+// kernels, which do nothing unless the step left a slice pending.
+static int ctl_grid_host(int L) {
+    int g = (L + kCtlThreads - 1) / kCtlThreads;
+    return g < 1 ? 1 : (g > kCtlGrid ? kCtlGrid : g);
+}
+
+static int launch_stages(const SolverView& v, int grid_ctas, int s0, int s1, cudaStream_t s) {
+    const int g = ctl_grid_host(v.L);
     const int tot = v.L > v.cap ? v.L : v.cap;
     const int prep_blocks = (tot + kPrepThreads - 1) / kPrepThreads;
-    k_step_begin<<<g, kCtlThreads, 0, s>>>(v);
-    for (int stg = 1; stg <= 6; ++stg) {
+    for (int stg = s0; stg <= s1; ++stg) {
         const double* row = v.Y + (size_t)(stg & 1) * 2 * v.L;
-        int rc = launch_history_integrals(v, row, 0.0, true, v.S, grid_ctas, s);
+        int rc = launch_history_integrals(v, row, 0.0, stg, v.S, grid_ctas, s);
         if (rc) return rc;
         k_stage_end<<<g, kCtlThreads, 0, s>>>(v, stg, prep_blocks);
     }
-    return launch_sparsify(v, true, 0.0, s);
+    DMFE_CUDA_TRY(cudaGetLastError());
+    return DMFE_OK;
+}
+
+int launch_step_head(const SolverView& v, int grid_ctas, cudaGraphConditionalHandle cond, int use_cond,
+                     cudaStream_t s) {
+    k_step_begin<<<ctl_grid_host(v.L), kCtlThreads, 0, s>>>(v, cond, use_cond);
+    return launch_stages(v, grid_ctas, 1, kDP5Stages, s);
+}
+
+int launch_step_tail(const SolverView& v, int grid_ctas, cudaStream_t s) {
+    return launch_stages(v, grid_ctas, kDP5Stages + 1, kMaxStages, s);
+}
+
+int launch_step_sparsify(const SolverView& v, cudaStream_t s) { return launch_sparsify(v, true, 0.0, s); }
+
+int launch_step(const SolverView& v, int grid_ctas, cudaStream_t s) {
+    int rc = launch_step_head(v, grid_ctas, 0, 0, s);
+    if (!rc) rc = launch_step_tail(v, grid_ctas, s);
+    if (!rc) rc = launch_step_sparsify(v, s);
+    return rc;
 }
 
 int launch_lookup(const SolverView& v, int n, const double* t, const double* tp, int which, double* out,
@@ -712,21 +812,37 @@ int launch_refresh_replica(const SolverView& v, cudaStream_t s) {
     return DMFE_OK;
 }
 
-// One batched Dormand-Prince step over every active slot of the batch table: the same
-// kernels as launch_step, with blockIdx.y (or blockIdx.x for per-slot kernels) the slot.
-int launch_batch_step(const BatchTable* bt, int precision, int sw, int max_L, int max_cap, int slots,
-                      int hi_grid, size_t hi_smem, cudaStream_t s) {
-    int g = (max_L + kCtlThreads - 1) / kCtlThreads;
-    g = g < 1 ? 1 : (g > kCtlGrid ? kCtlGrid : g);
+// One batched trial step over every active slot of the batch table, in the same three
+// parts as launch_step, with blockIdx.y (or blockIdx.x for per-slot kernels) the slot.
+static int launch_batch_stages(const BatchTable* bt, int precision, int sw, int max_L, int max_cap, int slots,
+                               int hi_grid, size_t hi_smem, int s0, int s1, cudaStream_t s) {
+    const int g = ctl_grid_host(max_L);
     const int max_tot = max_L > max_cap ? max_L : max_cap;
-    k_batch_step_begin<<<dim3(g, slots), kCtlThreads, 0, s>>>(bt);
-    for (int stg = 1; stg <= 6; ++stg) {
+    for (int stg = s0; stg <= s1; ++stg) {
         int rc = launch_batch_prep(bt, stg, max_tot, slots, s);
         if (rc) return rc;
         rc = launch_batch_hi(bt, precision, sw, stg, hi_grid, hi_smem, s);
         if (rc) return rc;
         k_batch_stage_end<<<dim3(g, slots), kCtlThreads, 0, s>>>(bt, stg);
     }
+    DMFE_CUDA_TRY(cudaGetLastError());
+    return DMFE_OK;
+}
+
+int launch_batch_step_head(const BatchTable* bt, int precision, int sw, int max_L, int max_cap, int slots,
+                           int hi_grid, size_t hi_smem, cudaGraphConditionalHandle cond, int use_cond,
+                           cudaStream_t s) {
+    k_batch_step_begin<<<dim3(ctl_grid_host(max_L), slots), kCtlThreads, 0, s>>>(bt, cond, use_cond);
+    return launch_batch_stages(bt, precision, sw, max_L, max_cap, slots, hi_grid, hi_smem, 1, kDP5Stages, s);
+}
+
+int launch_batch_step_tail(const BatchTable* bt, int precision, int sw, int max_L, int max_cap, int slots,
+                           int hi_grid, size_t hi_smem, cudaStream_t s) {
+    return launch_batch_stages(bt, precision, sw, max_L, max_cap, slots, hi_grid, hi_smem, kDP5Stages + 1,
+                               kMaxStages, s);
+}
+
+int launch_batch_step_sparsify(const BatchTable* bt, int max_cap, int slots, cudaStream_t s) {
     k_batch_sp_residual<<<dim3((max_cap + 7) / 8, slots), 256, 0, s>>>(bt);
     k_batch_sp_select<<<slots, 32, 0, s>>>(bt);
     k_batch_sp_compact<<<dim3(64, slots), 256, 0, s>>>(bt);

@@ -28,6 +28,10 @@ DMFE_FP64 = 0
 DMFE_FP32_COMPENSATED = 1
 DMFE_DOUBLE_FLOAT = 2
 PRECISIONS = {"fp64": DMFE_FP64, "fp32": DMFE_FP32_COMPENSATED, "df": DMFE_DOUBLE_FLOAT}
+DMFE_RK_AUTO = 0
+DMFE_RK_DP5 = 1
+DMFE_RK_SSPRK104 = 2
+INTEGRATORS = {"auto": DMFE_RK_AUTO, "dp5": DMFE_RK_DP5, "ssprk104": DMFE_RK_SSPRK104}
 DMFE_NS = 10
 
 _d = ctypes.c_double
@@ -41,7 +45,7 @@ class dmfe_params(ctypes.Structure):
     _fields_ = [("n_terms", _i), ("powers", _ip), ("coefs", _dp), ("T", _d), ("beta0", _d),
                 ("L", _i), ("s", _i), ("grid_t_max", _d), ("alpha", _d), ("delta", _d),
                 ("history_cap", _i), ("dt0", _d), ("dt_min", _d), ("precision", _i),
-                ("sparsify", _i), ("stream", _p)]
+                ("sparsify", _i), ("stream", _p), ("integrator", _i), ("rk_switch_dt", _d)]
 
 
 class dmfe_stats_t(ctypes.Structure):
@@ -50,7 +54,8 @@ class dmfe_stats_t(ctypes.Structure):
                 ("steps_rejected", ctypes.c_longlong), ("stages", ctypes.c_longlong),
                 ("sparsify_passes", ctypes.c_longlong), ("slices_removed", ctypes.c_longlong),
                 ("forced_removals", ctypes.c_longlong), ("n_slices", _i), ("status", _i),
-                ("L", _i), ("history_cap", _i), ("s", _i), ("precision", _i)]
+                ("L", _i), ("history_cap", _i), ("s", _i), ("precision", _i), ("method", _i),
+                ("t_switch", _d), ("rk_switch_dt", _d), ("step_graph", _i)]
 
 
 class dmfe_result(ctypes.Structure):
@@ -148,7 +153,7 @@ def _f64(a, n=None):
 
 
 def make_params(coefs, T, L, grid_t_max, s=4, beta0=0.0, alpha=0.0, delta=0.0, history_cap=None, dt0=1e-4,
-                dt_min=1e-12, precision="fp64", sparsify=True, stream=None):
+                dt_min=1e-12, precision="fp64", sparsify=True, stream=None, integrator="auto", switch_dt=0.0):
     """A dmfe_params structure; the returned tuple keeps the coefficient arrays alive."""
     lib = load()
     terms = sorted((int(p), float(c)) for p, c in dict(coefs).items())
@@ -166,6 +171,8 @@ def make_params(coefs, T, L, grid_t_max, s=4, beta0=0.0, alpha=0.0, delta=0.0, h
     prm.precision = PRECISIONS[precision]
     prm.sparsify = 1 if sparsify else 0
     prm.stream = stream
+    prm.integrator = INTEGRATORS[integrator]
+    prm.rk_switch_dt = float(switch_dt)
     return prm, (pw, cf)
 
 
@@ -284,14 +291,16 @@ class Solver:
 
     def __init__(self, coefs, T, L, grid_t_max, s=4, beta0=0.0, alpha=0.0, delta=0.0,
                  history_cap=None, dt0=1e-4, dt_min=1e-12, precision="fp64", sparsify=True,
-                 stream=None):
+                 stream=None, integrator="auto", switch_dt=0.0):
+        """integrator: "auto" (Dormand-Prince, then SSPRK(10,4) once the step reaches
+        switch_dt; 0 = the stability estimate), "dp5" or "ssprk104" (Sec. 3.5)."""
         lib = load()
         self._lib = lib
         self.h = _p()
         self._owned = True
         prm, keep = make_params(coefs, T, L, grid_t_max, s=s, beta0=beta0, alpha=alpha, delta=delta,
                                 history_cap=history_cap, dt0=dt0, dt_min=dt_min, precision=precision,
-                                sparsify=sparsify, stream=stream)
+                                sparsify=sparsify, stream=stream, integrator=integrator, switch_dt=switch_dt)
         _check(lib.dmfe_create(ctypes.byref(prm), ctypes.byref(self.h)), "dmfe_create")
         self._sizes()
 
