@@ -1,12 +1,15 @@
-"""Benchmark: Dormand-Prince steps of the DMFE history-integral path on GB300.
+"""Benchmark: Runge-Kutta steps of the DMFE history-integral path on GB300.
 
 Workload (mixed (3+4)-spin, f = (q^3 + q^4)/4, T = 0.5, theta grid L = 2049 for
 t_max = 1e5, stencil width 4, history store of 2049 slices, FP64): one step is one
 device-driven Dormand-Prince trial step -- six stages of (history integrals, RHS
 assembly), the error estimate and step rule, the append, and a sparsification pass
-whenever the store is full. The state is a seeded synthetic history of 2049 - 6
-slices on geometric times in [1e-2, 9e4], so that the store fills and a pass runs
-inside the timed steps.
+whenever the store is full. The state is the quench itself, solved from t = 0 until the
+store has filled and been thinned once, so every timed step may run a pass.
+
+--workload solve runs whole solves from t = 0 through checkpoints (wall clock through the
+public API, truncated at --time-limit seconds and said so), optionally in several
+precisions, with the differences of C, R and E between them at each checkpoint.
 
 value: trial steps per second over all ranks (device time, CUDA events on the
 solver's stream, barrier + synchronize around the timed region, max over ranks).
@@ -36,13 +39,18 @@ GRID_T_MAX = 1e5
 TOL = 1e-8
 # Algorithmic operations per (i, j) pair at stencil width 4, counted from the kernel
 # source (FMA = 2 flops). The Lagrange weights of the three stencils are read from the
-# per-grid tables, not computed per pair. FP64 kernel: A1 32, A2 16, B1 16, B2 (time
-# weights 23, two 4-point stencils of 4 fields 64, Hermite combination 14), f' and f''
-# at two points for the (3+4) model 20, nine products and sums 30.
-FLOP_PER_PAIR_S4 = 32 + 16 + 16 + 101 + 20 + 30
+# per-grid tables, not computed per pair. FP64 kernel: A1 32, A2 16, B1 16, B2 (stage
+# time 3, time weights 12, two 4-point stencils of 4 fields 64, Hermite combination 16),
+# f' and f'' at two points for the (3+4) model 20, nine weighted products and sums 27.
+FLOP_PER_PAIR_S4 = 32 + 16 + 16 + 95 + 20 + 27
 # Double-float kernel, FP32 flops of the double-float arithmetic: B1 110, A1 220, A2 110,
 # B2 713, f' and f'' 210, products and sums 226.
 DF_FP32_FLOP_PER_PAIR_S4 = 110 + 220 + 110 + 713 + 210 + 226
+# DRAM bytes (read + write) of one history-integral launch at this workload's state, from
+# one ncu capture per precision (dram__bytes_read.sum + dram__bytes_write.sum of the first
+# launch inside the timed steps; profiles/traffic_k_hi_L2049_bench_state.md). Set to None
+# whenever the kernel changes until it is measured again.
+TRAFFIC_BYTES = {"fp64": 658163712 + 3979776, "df": 644141824 + 3334912, "fp32": 86010112 + 2716416}
 # Nominal per-GPU peaks derived from the unit counts and the 2.07 GHz maximum SM clock:
 # FP64 1.25 TFLOP/s (2 FMA lanes per SM); FP32 152 SMs x 128 lanes x 2 x 2.07e9.
 FP64_PEAK_GFLOPS = 1250.0
@@ -66,7 +74,7 @@ def parse():
     ap.add_argument("--kernel-only", action="store_true",
                     help="only launch the history-integral kernel (for profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="step", choices=["step", "batch", "serve"],
+    ap.add_argument("--workload", default="step", choices=["step", "batch", "serve", "solve"],
                     help="step: the headline configuration; batch: 256 independent solves stepped "
                          "together; serve: Poisson-arrival requests with continuous batching")
     ap.add_argument("--window", type=float, default=30.0, help="seconds of batched or served work")
@@ -74,6 +82,10 @@ def parse():
     ap.add_argument("--batch-max-L", type=int, default=4097, help="largest grid of the batch mix")
     ap.add_argument("--integrator", default="auto", choices=["auto", "dp5", "ssprk104"],
                     help="integrator of the step workload (auto: Dormand-Prince, SSPRK(10,4) after the switch)")
+    ap.add_argument("--t-max", type=float, default=1e5, help="solve: final time (also the grid's t_max)")
+    ap.add_argument("--checkpoints", default="1e2,1e3,1e4,1e5", help="solve: times at which to record")
+    ap.add_argument("--compare", default="", help="solve: further precisions compared with --precision")
+    ap.add_argument("--time-limit", type=float, default=900.0, help="solve: wall seconds per precision")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the double-float and FP32-compensated variants of the same workload")
     return ap.parse_args()
@@ -290,19 +302,21 @@ def roofline(precision, res):
     if precision == "fp64":
         ach = pairs * FLOP_PER_PAIR_S4 / k / 1e9
         return {"kernel": "k_hi_f64 (history integrals)", "bound": "alu", "achieved": ach,
-                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": ach / FP64_PEAK_GFLOPS, "traffic": None,
+                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": ach / FP64_PEAK_GFLOPS,
+                "traffic": TRAFFIC_BYTES["fp64"],
                 "peak_source": "nominal FP64 (unit counts x clock)", "algorithmic_bytes": bh + bt + bio,
                 "hbm_frac_of_%s" % src: (bh + bt + bio) / k / 1e9 / hbm, "kernel_ms": k * 1e3}
     if precision == "df":
         ach = pairs * DF_FP32_FLOP_PER_PAIR_S4 / k / 1e9
         return {"kernel": "k_hi_df (history integrals)", "bound": "alu", "achieved": ach,
-                "peak": FP32_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": ach / FP32_PEAK_GFLOPS, "traffic": None,
+                "peak": FP32_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": ach / FP32_PEAK_GFLOPS,
+                "traffic": TRAFFIC_BYTES["df"],
                 "peak_source": "nominal FP32 (unit counts x clock)", "algorithmic_bytes": bh + bt + bio,
                 "fp64_equivalent_gflops": pairs * FLOP_PER_PAIR_S4 / k / 1e9,
                 "hbm_frac_of_%s" % src: (bh + bt + bio) / k / 1e9 / hbm, "kernel_ms": k * 1e3}
     ach = (bh + bt + bio) / k / 1e9
     return {"kernel": "k_hi_f32 (history integrals)", "bound": "hbm", "achieved": ach, "peak": hbm,
-            "unit": "GB/s", "frac": ach / hbm, "traffic": None, "peak_source": src,
+            "unit": "GB/s", "frac": ach / hbm, "traffic": TRAFFIC_BYTES["fp32"], "peak_source": src,
             "algorithmic_bytes": bh + bt + bio, "history_bytes": bh, "table_bytes": bt, "kernel_ms": k * 1e3}
 
 
@@ -311,6 +325,88 @@ def solver_info(res):
                                                  "slices_removed", "forced_removals", "n_slices", "dt",
                                                  "last_eps")},
                 state_prepared_by_steps=res["setup_steps"], autotuned_unit=res["chunk"])
+
+
+def run_pure3_quench():
+    """The small single-instance configuration end to end: f = q^3/2, T = 0.8, L = 129,
+    129-slice store, tol 1e-8, from t = 0 to 100 with one dmfe_integrate call (graph capture
+    included), FP64."""
+    import torch
+    from paper_2604_06309_gb300 import Solver
+    warm = Solver({3: 0.5}, 0.8, 129, 100.0, history_cap=129)
+    warm.integrate(1.0, TOL)
+    warm.close()
+    torch.cuda.synchronize()
+    sv = Solver({3: 0.5}, 0.8, 129, 100.0, history_cap=129)
+    t0 = time.perf_counter()
+    rc = sv.integrate(100.0, TOL)
+    wall = time.perf_counter() - t0
+    st = sv.stats()
+    sv.close()
+    steps = st["steps_accepted"] + st["steps_rejected"]
+    return {"workload": "pure 3-spin f=q^3/2, T=0.8, L=129, 129-slice store, tol 1e-8, t=0..100, FP64, "
+                        "one dmfe_integrate call", "status": rc, "wall_s": wall, "steps": steps,
+            "rk_steps_per_s": steps / wall, "stages": st["stages"], "sparsify_passes": st["sparsify_passes"]}
+
+
+SOLVE_PAIRS = [(1.0, 0.0), (1.0, 0.5), (1.0, 0.9), (1.0, 0.99), (1.0, 0.999), (0.5, 0.25), (0.9, 0.45),
+               (0.99, 0.5), (0.3, 0.0), (0.7, 0.69)]
+
+
+def run_solve(args):
+    """Whole solves of the workload from t = 0 (Secs. 3.1-3.6), recorded at checkpoints."""
+    import torch
+    from paper_2604_06309_gb300 import Solver
+    cps = [float(x) for x in args.checkpoints.split(",") if float(x) <= args.t_max]
+    precs = [args.precision] + [p for p in args.compare.split(",") if p and p != args.precision]
+    runs = {}
+    for prec in precs:
+        sv = Solver(COEFS, T_BATH, args.L, args.t_max, s=4, history_cap=args.L, precision=prec,
+                    integrator=args.integrator)
+        t0 = time.perf_counter()
+        rec, truncated = [], False
+        for tc in cps:
+            while True:
+                sv.step(64, tc, TOL)
+                st = sv.stats()
+                if st["status"] != 0:
+                    raise RuntimeError("%s: device status %d at t = %g" % (prec, st["status"], st["t"]))
+                if st["t"] >= tc or time.perf_counter() - t0 > args.time_limit:
+                    break
+            wall = time.perf_counter() - t0
+            if st["t"] < tc:
+                truncated = True
+                rec.append({"t": st["t"], "wall_s": wall, "truncated_before": tc,
+                            "steps": st["steps_accepted"] + st["steps_rejected"]})
+                break
+            t = np.array([a * tc for a, _ in SOLVE_PAIRS])
+            tp = np.array([b * tc for _, b in SOLVE_PAIRS])
+            _, _, _, mu, E = sv.get_row()
+            rec.append({"t": tc, "wall_s": wall, "steps": st["steps_accepted"] + st["steps_rejected"],
+                        "steps_rejected": st["steps_rejected"], "stages": st["stages"],
+                        "sparsify_passes": st["sparsify_passes"], "forced_removals": st["forced_removals"],
+                        "dt": st["dt"], "method": "ssprk104" if st["method"] == 2 else "dp5",
+                        "t_switch": st["t_switch"], "E": E, "mu": mu,
+                        "C": sv.get_C(t, tp).tolist(), "R": sv.get_R(t, tp).tolist()})
+        runs[prec] = {"checkpoints": rec, "truncated": truncated}
+        sv.close()
+        torch.cuda.synchronize()
+    base = runs[precs[0]]["checkpoints"]
+    for prec in precs[1:]:
+        for a, b in zip(base, runs[prec]["checkpoints"]):
+            if "C" in a and "C" in b and a["t"] == b["t"]:
+                b["vs_" + precs[0]] = {"max_abs_dC": float(np.max(np.abs(np.array(a["C"]) - np.array(b["C"])))),
+                                       "max_abs_dR": float(np.max(np.abs(np.array(a["R"]) - np.array(b["R"])))),
+                                       "abs_dE": abs(a["E"] - b["E"])}
+    last = base[-1]
+    return {"metric": "RK steps/s", "value": last["steps"] / last["wall_s"], "unit": "RK steps/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": DTYPES[args.precision], "data": "synthetic",
+            "config": {"workload": "(3+4)-spin T=0.5 quench from t=0 to %g, theta grid L=%d (t_max %g), "
+                                   "%d-slice store, s=4, tol 1e-8, integrator %s; wall clock through the C ABI, "
+                                   "truncated at %g s per precision"
+                                   % (args.t_max, args.L, args.t_max, args.L, args.integrator, args.time_limit),
+                       "sample_pairs": SOLVE_PAIRS},
+            "runs": runs}
 
 
 BATCH_LS = (129, 257, 513, 1025, 2049, 4097)
@@ -487,6 +583,9 @@ def main():
     if args.workload == "serve":
         print(json.dumps(run_serving(args)))
         return
+    if args.workload == "solve":
+        print(json.dumps(run_solve(args)))
+        return
     import torch
     if world > 1:
         torch.distributed.init_process_group("nccl")
@@ -538,6 +637,8 @@ def main():
             "dp5_simulated_time_per_s_at_stability_limit": value * DP5_REAL_STABILITY / rho,
             "roofline": roofline(args.precision, r3), "solver": solver_info(r3)}
         line["variants"] = variants
+    if not args.no_variants and world == 1:
+        line["pure3_quench"] = run_pure3_quench()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(L)
     print(json.dumps(line))

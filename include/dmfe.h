@@ -139,7 +139,9 @@ int dmfe_integrate(dmfe_solver* h, double t_max, double tol);
  * stream (or `stream` if not NULL) without synchronising: each step is one CUDA-graph
  * launch of the stages (the last four stages of SSPRK(10,4) sit in a conditional graph
  * node that the step's first kernel enables), the device-side step rule and, when the
- * store is full, a sparsification pass. Steps after t_max is reached or after a device error
+ * store is full, a sparsification pass. The environment variable DMFE_STEP_GRAPH=plain
+ * (read when a solver or batch first captures its graph) keeps every stage inline
+ * instead, for profilers that cannot attribute kernels inside conditional graphs. Steps after t_max is reached or after a device error
  * do nothing. dmfe_sync / dmfe_stats read the outcome. Used by benchmarks and by
  * callers that interleave their own work between steps. */
 int dmfe_step(dmfe_solver* h, int nsteps, double t_max, double tol, void* stream);
@@ -201,7 +203,8 @@ int dmfe_checkpoint(dmfe_solver* h, const char* path);
 int dmfe_restore(const char* path, void* stream, dmfe_solver** out);
 
 /* Autotune the work-unit size of the history-integral kernel (summation indices per
- * unit: the candidates 256, 512, 1024, 2048, 4096 and L) by timing the kernel on the
+ * unit: the candidates 256, 512, 1024, 2048, 4096, L and L/P for P = 2..16, at least 256)
+ * by timing the kernel on the
  * solver's current history and stage row, and keep the fastest. Results are cached per
  * (L, history_cap, s, precision) for the process. Changes the summation order of the
  * sums S (rounding-level differences only). *chunk (may be NULL) receives the choice. */

@@ -309,7 +309,7 @@ struct SoloParts : StepParts {
 int build_step_graph(dmfe_solver* h) {
     if (h->step_exec) return DMFE_OK;
     SoloParts parts(h);
-    if (capture_step_graph(h->cap_stream, true, parts, &h->step_exec) == DMFE_OK) {
+    if (!step_graph_plain() && capture_step_graph(h->cap_stream, true, parts, &h->step_exec) == DMFE_OK) {
         h->conditional_graph = true;
         return DMFE_OK;
     }
@@ -743,6 +743,11 @@ int dmfe_autotune(dmfe_solver* h, int* chunk_out) {
             const int cc = c >= L ? L : c;
             if (cc >= kMinChunk || cc == L)
                 if (std::find(cands.begin(), cands.end(), cc) == cands.end()) cands.push_back(cc);
+        }
+        // L/P for P parts: part counts whose P*L units fill the last wave of warps best
+        for (int P = 2; P <= 16; ++P) {
+            const int cc = L / P;
+            if (cc >= kMinChunk && std::find(cands.begin(), cands.end(), cc) == cands.end()) cands.push_back(cc);
         }
         cudaEvent_t e0, e1;
         DMFE_CUDA_TRY(cudaEventCreate(&e0));

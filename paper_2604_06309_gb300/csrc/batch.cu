@@ -88,7 +88,7 @@ struct BatchParts : StepParts {
 int build_graph(dmfe_batch* b) {
     if (b->exec) return DMFE_OK;
     BatchParts parts(b);
-    if (capture_step_graph(b->cap_stream, true, parts, &b->exec) == DMFE_OK) return DMFE_OK;
+    if (!step_graph_plain() && capture_step_graph(b->cap_stream, true, parts, &b->exec) == DMFE_OK) return DMFE_OK;
     return capture_step_graph(b->cap_stream, false, parts, &b->exec);
 }
 

@@ -235,6 +235,7 @@ struct StepParts {
     virtual ~StepParts() = default;
 };
 int capture_step_graph(cudaStream_t cap, bool conditional, StepParts& parts, cudaGraphExec_t* out);
+bool step_graph_plain();  // DMFE_STEP_GRAPH=plain: no conditional nodes (graph.cu)
 // accessors of a solver's internals (api.cu)
 struct dmfe_solver;
 const SolverView& solver_view(const dmfe_solver* h);

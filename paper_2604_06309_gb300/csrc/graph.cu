@@ -5,7 +5,18 @@
 // the host never has to know which method the device chose.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+#include <cstring>
+
 #include "dmfe_internal.h"
+
+// DMFE_STEP_GRAPH=plain selects step graphs without the conditional node (all stages
+// inline, the SSPRK ones gating themselves off): profilers that cannot attribute kernels
+// inside graphs with conditional nodes then see every kernel of a step.
+bool step_graph_plain() {
+    const char* e = std::getenv("DMFE_STEP_GRAPH");
+    return e && std::strcmp(e, "plain") == 0;
+}
 
 namespace {
 

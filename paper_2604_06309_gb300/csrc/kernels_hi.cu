@@ -68,30 +68,40 @@ struct TimeW {
     double w0, w1, w2, w3;
 };
 
-// sinv (may be NULL) holds 1/(t_{k+1} - t_k); inv_hx = 1/hx.
-__device__ __forceinline__ TimeW time_weights_f64(const double* sht, int n, bool ext, double tl,
-                                                  double hx, double tau, int hint,
-                                                  const double* sinv = nullptr, double inv_hx = 0.0) {
+// Time weights of the B2 lookup of one pair. Slice times are non-negative, so their
+// IEEE bit patterns order like the values: the slice walk compares 64-bit integers
+// (integer pipe) instead of doubles (the FP64 pipe, GB300's bottleneck here). shb holds
+// the bit patterns of the slice times, shh the widths t_{k+1} - t_k, sinv their
+// reciprocals. The cubic Hermite basis uses h00 = 1 - h01 and
+// h10 = s (1-s)^2 h, h11 = -s^2 (1-s) h = -(s (1-s) h) s.
+__device__ __forceinline__ TimeW time_weights_f64(const long long* shb, const double* sht, const double* shh,
+                                                  const double* sinv, int n, bool ext, long long tlb,
+                                                  double tl, double inv_hx, double tau, int hint) {
     TimeW r;
-    if (ext && tau > tl) {
-        double s = tau - tl, q = sinv ? s * inv_hx : s / hx;
+    const long long taub = __double_as_longlong(tau);
+    if (ext && taub > tlb) {
+        const double s = tau - tl, q = s * inv_hx;
         r.a0 = n - 1; r.a1 = -1;
-        r.w0 = 1.0 - q * q; r.w1 = s - s * q; r.w2 = q * q; r.w3 = 0.0;
+        r.w2 = q * q;
+        r.w0 = 1.0 - r.w2;
+        r.w1 = s - s * q;
+        r.w3 = 0.0;
     } else if (n == 1) {
         r.a0 = 0; r.a1 = 0;
         r.w0 = 1.0; r.w1 = 0.0; r.w2 = 0.0; r.w3 = 0.0;
     } else {
         int k = hint;
-        while (k < n - 2 && sht[k + 1] <= tau) ++k;
-        while (k > 0 && sht[k] > tau) --k;
-        double hh = sht[k + 1] - sht[k];
-        double sg = sinv ? (tau - sht[k]) * sinv[k] : (tau - sht[k]) / hh;
-        double om = 1.0 - sg;
+        while (k < n - 2 && shb[k + 1] <= taub) ++k;
+        while (k > 0 && shb[k] > taub) --k;
+        const double hh = shh[k];
+        const double sg = (tau - sht[k]) * sinv[k];
+        const double om = 1.0 - sg;
+        const double p = sg * om * hh;
         r.a0 = k; r.a1 = k + 1;
-        r.w0 = (1.0 + 2.0 * sg) * om * om;
-        r.w1 = sg * om * om * hh;
         r.w2 = sg * sg * (3.0 - 2.0 * sg);
-        r.w3 = sg * sg * (sg - 1.0) * hh;
+        r.w0 = 1.0 - r.w2;
+        r.w1 = p * om;
+        r.w3 = -p * sg;
     }
     return r;
 }
@@ -129,20 +139,27 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
     const dbl4* __restrict__ H = v.hist[act];
     const double* __restrict__ ht = v.ht[act];
     dbl4* srow = reinterpret_cast<dbl4*>(smraw);            // [L] {K, D, C, R}
-    double* sht = reinterpret_cast<double*>(srow + L);              // [cap]
-    double* sinvh = sht + v.cap;                                    // [cap] 1/(t_{k+1} - t_k)
+    double* sht = reinterpret_cast<double*>(srow + L);              // [cap] slice times
+    long long* shb = reinterpret_cast<long long*>(sht + v.cap);     // [cap] their bit patterns
+    double* shh = reinterpret_cast<double*>(shb + v.cap);           // [cap] t_{k+1} - t_k
+    double* sinvh = shh + v.cap;                                    // [cap] 1/(t_{k+1} - t_k)
     int* scell = reinterpret_cast<int*>(sinvh + v.cap);             // [L]
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         double C = row[i], R = row[L + i];
         srow[i] = dbl4{fp2(v.poly, C) * R, fp1(v.poly, C), C, R};
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        sht[i] = ht[i];
-        sinvh[i] = i + 1 < n ? 1.0 / (ht[i + 1] - ht[i]) : 0.0;
+        const double ti = ht[i];
+        sht[i] = ti;
+        shb[i] = __double_as_longlong(ti);
+        const double hh = i + 1 < n ? ht[i + 1] - ti : 0.0;
+        shh[i] = hh;
+        sinvh[i] = i + 1 < n ? 1.0 / hh : 0.0;
     }
     for (int m = threadIdx.x; m < L; m += blockDim.x) scell[m] = v.cell[m];
     __syncthreads();
     const double tl = sht[n - 1];
+    const long long tlb = shb[n - 1];
     const bool ext = t > tl;
     const double hx = t - tl;
     const double inv_hx = ext ? 1.0 / hx : 0.0;
@@ -225,7 +242,7 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
                 int cell = base2 + SW / 2 - 1;  // the grid cell of phi2 (a hint; the walk corrects)
                 cell = cell < 0 ? 0 : (cell > L - 1 ? L - 1 : cell);
                 const int h0 = scell[cell];
-                const TimeW b2 = time_weights_f64(sht, n, ext, tl, hx, tau2, h0, sinvh, inv_hx);
+                const TimeW b2 = time_weights_f64(shb, sht, shh, sinvh, n, ext, tlb, tl, inv_hx, tau2, h0);
                 const unsigned char* e = w3r + (size_t)i * WTS;
                 const int b = *reinterpret_cast<const int*>(e);
                 double w[SW];
@@ -257,16 +274,18 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
             }
             const double f1a = fp1(v.poly, CB1), f2a = fp2(v.poly, CB1);
             const double f1b = fp1(v.poly, CB2), f2b = fp2(v.poly, CB2);
+            // the weight nu_i folded into factors shared by several sums
             const double nui = nu[i];
-            acc[0] += nui * (KA1 * CB1);
-            acc[1] += nui * (KA2 * CB2);
-            acc[2] += nui * (DA1 * RB1);
-            acc[3] += nui * (KA2 * RB2);
-            acc[4] += nui * (f2a * RB1 * CA1);
-            acc[5] += nui * (f1a * RA1);
-            acc[6] += nui * (f1b * RA2);
-            acc[7] += nui * (f2b * RB2 * RA2);
-            acc[8] += nui * ((f2a * CB1 + f1a) * RB1);
+            const double nCB1 = nui * CB1, nRB1 = nui * RB1, nKA2 = nui * KA2, nRA2 = nui * RA2;
+            acc[0] += KA1 * nCB1;
+            acc[1] += nKA2 * CB2;
+            acc[2] += DA1 * nRB1;
+            acc[3] += nKA2 * RB2;
+            acc[4] += (f2a * CA1) * nRB1;
+            acc[5] += (nui * f1a) * RA1;
+            acc[6] += f1b * nRA2;
+            acc[7] += (f2b * RB2) * nRA2;
+            acc[8] += (f2a * CB1 + f1a) * nRB1;
             if (i == 0) c_at_0 = CB1;
         }
         double sums[9];
@@ -502,7 +521,7 @@ __global__ void __launch_bounds__(HI_THREADS, 1) k_batch_hi(const BatchTable* __
 
 size_t hi_smem_bytes(const SolverView& v) {
     if (v.precision == DMFE_FP64)
-        return (size_t)v.L * sizeof(dbl4) + (size_t)v.cap * 2 * sizeof(double) + (size_t)v.L * sizeof(int);
+        return (size_t)v.L * sizeof(dbl4) + (size_t)v.cap * 4 * sizeof(double) + (size_t)v.L * sizeof(int);
     return (size_t)v.L * sizeof(float4) + (size_t)v.cap * (sizeof(double) + 3 * sizeof(float)) +
            (size_t)v.L * sizeof(int);
 }

@@ -450,12 +450,14 @@ __device__ __forceinline__ int ctl_grid(int L) {
     return g < 1 ? 1 : (g > kCtlGrid ? kCtlGrid : g);
 }
 
-// use_cond: the launch belongs to a step graph whose stages beyond kDP5Stages sit in a
-// conditional node with handle `cond`; one thread enables it for a live SSPRK step.
-__global__ void __launch_bounds__(kCtlThreads) k_step_begin(SolverView v, cudaGraphConditionalHandle cond,
-                                                            int use_cond) {
+// COND: the launch belongs to a step graph whose stages beyond kDP5Stages sit in a
+// conditional node with handle `cond`; one thread enables it for a live SSPRK step. (A
+// separate instantiation without the call keeps the plain variant visible to profilers,
+// which skip kernels that can set graph conditions.)
+template <bool COND>
+__global__ void __launch_bounds__(kCtlThreads) k_step_begin(SolverView v, cudaGraphConditionalHandle cond) {
     step_begin_body(v, blockIdx.x, gridDim.x);
-    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0 && !gated(v.st) && kRK[v.st->method].n > kDP5Stages)
+    if (COND && blockIdx.x == 0 && threadIdx.x == 0 && !gated(v.st) && kRK[v.st->method].n > kDP5Stages)
         cudaGraphSetConditional(cond, 1u);
 }
 
@@ -464,8 +466,9 @@ __global__ void __launch_bounds__(kCtlThreads) k_stage_end(SolverView v, int stg
 }
 
 // Batched wrappers: blockIdx.y is the slot; each slot keeps its own CTA partition.
+template <bool COND>
 __global__ void __launch_bounds__(kCtlThreads) k_batch_step_begin(const BatchTable* __restrict__ bt,
-                                                                  cudaGraphConditionalHandle cond, int use_cond) {
+                                                                  cudaGraphConditionalHandle cond) {
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
         // work offsets of the slots whose step has stages beyond the Dormand-Prince ones
         // (their method does not change while the step runs), and the graph condition
@@ -478,7 +481,7 @@ __global__ void __launch_bounds__(kCtlThreads) k_batch_step_begin(const BatchTab
             if (!gated(vq.st) && kRK[vq.st->method].n > kDP5Stages) w += (long long)vq.L * vq.L;
         }
         wl[bt->count] = w;
-        if (use_cond) cudaGraphSetConditional(cond, w > 0 ? 1u : 0u);
+        if (COND) cudaGraphSetConditional(cond, w > 0 ? 1u : 0u);
     }
     const int k = blockIdx.y;
     if (k >= bt->count || !bt->active[k]) return;
@@ -781,7 +784,8 @@ static int launch_stages(const SolverView& v, int grid_ctas, int s0, int s1, cud
 
 int launch_step_head(const SolverView& v, int grid_ctas, cudaGraphConditionalHandle cond, int use_cond,
                      cudaStream_t s) {
-    k_step_begin<<<ctl_grid_host(v.L), kCtlThreads, 0, s>>>(v, cond, use_cond);
+    if (use_cond) k_step_begin<true><<<ctl_grid_host(v.L), kCtlThreads, 0, s>>>(v, cond);
+    else k_step_begin<false><<<ctl_grid_host(v.L), kCtlThreads, 0, s>>>(v, cond);
     return launch_stages(v, grid_ctas, 1, kDP5Stages, s);
 }
 
@@ -832,7 +836,9 @@ static int launch_batch_stages(const BatchTable* bt, int precision, int sw, int 
 int launch_batch_step_head(const BatchTable* bt, int precision, int sw, int max_L, int max_cap, int slots,
                            int hi_grid, size_t hi_smem, cudaGraphConditionalHandle cond, int use_cond,
                            cudaStream_t s) {
-    k_batch_step_begin<<<dim3(ctl_grid_host(max_L), slots), kCtlThreads, 0, s>>>(bt, cond, use_cond);
+    const dim3 grid(ctl_grid_host(max_L), slots);
+    if (use_cond) k_batch_step_begin<true><<<grid, kCtlThreads, 0, s>>>(bt, cond);
+    else k_batch_step_begin<false><<<grid, kCtlThreads, 0, s>>>(bt, cond);
     return launch_batch_stages(bt, precision, sw, max_L, max_cap, slots, hi_grid, hi_smem, 1, kDP5Stages, s);
 }
 

@@ -1,0 +1,73 @@
+"""The pure 3-spin quench f = q^3/2, T = 0.8 on an L = 129 grid with a 129-slice store,
+tol 1e-8, solved on the device to t = 100 and compared at t = 1, 10, 100 with the
+oracle's solve stored in tests/golden/pure3_T0.8_L129.json (written by
+tests/golden/make_pure3_quench.py, which calls only the oracle)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from gpu_common import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "pure3_T0.8_L129.json")
+
+
+def _golden():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def _solver(g, precision):
+    from paper_2604_06309_gb300 import Solver
+    c = g["case"]
+    return Solver({int(p): q for p, q in c["coefs"].items()}, c["T"], c["L"], c["grid_t_max"],
+                  history_cap=c["history_cap"], precision=precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df"])
+def test_quench_matches_oracle_at_checkpoints(precision):
+    need_gpu()
+    g = _golden()
+    sv = _solver(g, precision)
+    for cp in g["checkpoints"]:
+        assert sv.integrate(cp["t"], g["case"]["tol"]) == 0
+        tg, Cg, dCg, Rg, dRg = sv.get_history()
+        # identical step decisions: the same slice times, counters and switch time
+        assert np.array_equal(tg, np.array(cp["slice_times"])), cp["t"]
+        st = sv.stats()
+        for k in ("steps_accepted", "steps_rejected", "sparsify_passes", "slices_removed", "forced_removals"):
+            assert st[k] == cp["stats"][k], (cp["t"], k)
+        assert st["t_switch"] == (cp["t_switch"] if cp["t_switch"] is not None else -1.0)
+        assert np.max(np.abs(Cg[-1] - np.array(cp["C_row"]))) < 1e-9
+        assert np.max(np.abs(Rg[-1] - np.array(cp["R_row"]))) < 1e-9
+        t, tp = np.array(cp["pairs"]).T
+        assert np.max(np.abs(sv.get_C(t, tp) - np.array(cp["C_pairs"]))) < 1e-9
+        assert np.max(np.abs(sv.get_R(t, tp) - np.array(cp["R_pairs"]))) < 1e-9
+        _, _, _, mu, E = sv.get_row()
+        assert abs(E - cp["E"]) < 1e-9 and abs(mu - cp["mu"]) < 1e-9
+    sv.close()
+
+
+# The FP32 solve takes its own step and sparsification decisions. Up to t = 10 it stays
+# within 1e-6 of the oracle. By t = 100 the 129-slice store has forced ~1000 removals whose
+# residuals reach 2.2e-6 (the oracle's own max eps_sparse), so two solves that thin the
+# history differently differ by that order: the bound there is 5e-6.
+FP32_BOUND = {1.0: 1e-6, 10.0: 1e-6, 100.0: 5e-6}
+
+
+def test_quench_fp32_compensated_against_oracle():
+    need_gpu()
+    g = _golden()
+    sv = _solver(g, "fp32")
+    for cp in g["checkpoints"]:
+        assert sv.integrate(cp["t"], g["case"]["tol"]) == 0
+        bound = FP32_BOUND[cp["t"]]
+        t, tp = np.array(cp["pairs"]).T
+        assert np.max(np.abs(sv.get_C(t, tp) - np.array(cp["C_pairs"]))) < bound, cp["t"]
+        assert np.max(np.abs(sv.get_R(t, tp) - np.array(cp["R_pairs"]))) < bound, cp["t"]
+        _, _, _, _, E = sv.get_row()
+        assert abs(E - cp["E"]) < bound
+    sv.close()
