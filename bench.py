@@ -43,14 +43,15 @@ TOL = 1e-8
 # time 3, time weights 12, two 4-point stencils of 4 fields 64, Hermite combination 16),
 # f' and f'' at two points for the (3+4) model 20, nine weighted products and sums 27.
 FLOP_PER_PAIR_S4 = 32 + 16 + 16 + 95 + 20 + 27
-# Double-float kernel, FP32 flops of the double-float arithmetic: B1 110, A1 220, A2 110,
-# B2 713, f' and f'' 210, products and sums 226.
-DF_FP32_FLOP_PER_PAIR_S4 = 110 + 220 + 110 + 713 + 210 + 226
+# Double-float kernel, FP32 flops of the double-float arithmetic: Lagrange weights from the
+# stored positions 3 x 118, B1 110, A1 220, A2 110, B2 713, f' and f'' 210, products and
+# sums 226.
+DF_FP32_FLOP_PER_PAIR_S4 = 354 + 110 + 220 + 110 + 713 + 210 + 226
 # DRAM bytes (read + write) of one history-integral launch at this workload's state, from
 # one ncu capture per precision (dram__bytes_read.sum + dram__bytes_write.sum of the first
 # launch inside the timed steps; profiles/traffic_k_hi_L2049_bench_state.md). Set to None
 # whenever the kernel changes until it is measured again.
-TRAFFIC_BYTES = {"fp64": 658163712 + 3979776, "df": 644141824 + 3334912, "fp32": 86010112 + 2716416}
+TRAFFIC_BYTES = {"fp64": 657725440 + 3474432, "df": 219070208 + 3332352, "fp32": 86010112 + 2716416}
 # Nominal per-GPU peaks derived from the unit counts and the 2.07 GHz maximum SM clock:
 # FP64 1.25 TFLOP/s (2 FMA lanes per SM); FP32 152 SMs x 128 lanes x 2 x 2.07e9.
 FP64_PEAK_GFLOPS = 1250.0
@@ -248,8 +249,9 @@ def _run_ours(args, rank, world, dev, stream):
     n0 = n_state
     wide = args.precision in ("fp64", "df")  # FP64 master or double-float replica: 8 B per value
     bytes_hist = 4 * n0 * L * (8 if wide else 4)
-    # stencil entries: {base, 4 weights} of 40 B (FP64 and double-float), packed 4 B positions (FP32)
-    bytes_tab = 3 * pairs * (40 if wide else 4)
+    # stencil entries: {base, 4 FP64 weights} of 40 B (FP64), double-float positions of 8 B,
+    # packed fixed-point positions of 4 B (FP32)
+    bytes_tab = 3 * pairs * {"fp64": 40, "df": 8, "fp32": 4}[args.precision]
     bytes_io = 2 * L * 8 + 10 * L * 8
     res = dict(dev_time=dev_time, e2e_time=e2e_time, k_avg=k_avg, clocks=clk, stats=st, stats_after=st2,
                bytes=(bytes_hist, bytes_tab, bytes_io), pairs=pairs, n0=n0, t_state=t_state,

@@ -201,9 +201,9 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
         TRY(dev_alloc(h, &p, LL * sizeof(uint32_t))); v.p2 = (uint32_t*)p;
         TRY(dev_alloc(h, &p, LL * sizeof(uint32_t))); v.p3 = (uint32_t*)p;
     } else {
-        TRY(dev_alloc(h, &p, LL * wts)); v.wt1 = (unsigned char*)p;
-        TRY(dev_alloc(h, &p, LL * wts)); v.wt2 = (unsigned char*)p;
-        TRY(dev_alloc(h, &p, LL * wts)); v.wt3 = (unsigned char*)p;
+        TRY(dev_alloc(h, &p, LL * sizeof(df))); v.q1 = (df*)p;
+        TRY(dev_alloc(h, &p, LL * sizeof(df))); v.q2 = (df*)p;
+        TRY(dev_alloc(h, &p, LL * sizeof(df))); v.q3 = (df*)p;
         TRY(dev_alloc(h, &p, L * sizeof(df))); v.omega_df = (df*)p;
         TRY(dev_alloc(h, &p, L * sizeof(df))); v.nu_df = (df*)p;
         TRY(dev_alloc(h, &p, L * sizeof(dfrow))); v.rowdf = (dfrow*)p;
@@ -390,7 +390,7 @@ unsigned long long dmfe_footprint(const dmfe_params* pin) {
     } else if (p.precision == DMFE_FP32_COMPENSATED) {
         for (int k = 0; k < 3; ++k) add(LL * 4);
     } else {
-        for (int k = 0; k < 3; ++k) add(LL * wts);
+        for (int k = 0; k < 3; ++k) add(LL * sizeof(df));
         add(L * sizeof(df)); add(L * sizeof(df)); add(L * sizeof(dfrow)); add(cap * sizeof(dfslice)); add(L * 4);
     }
     for (int b = 0; b < 2; ++b) {

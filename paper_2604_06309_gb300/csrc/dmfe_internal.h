@@ -126,9 +126,9 @@ struct SolverView {
     const double* x1;     // [L*L] FP64 fractional index (only while dmfe_tables runs)
     const double* x2;
     const double* x3;
-    const unsigned char* wt1;  // [L*L] stencil entries {int base, pad, s weights} of
-    const unsigned char* wt2;  //   8 + 8 s bytes: FP64 weights (FP64 path) or double-float
-    const unsigned char* wt3;  //   weights (double-float path), for phi1, phi2, psi
+    const unsigned char* wt1;  // [L*L] FP64 path: stencil entries {int base, pad, s FP64
+    const unsigned char* wt2;  //   weights} of 8 + 8 s bytes for phi1, phi2, psi
+    const unsigned char* wt3;
     const uint32_t* p1;   // [L*L] fixed-point index, 19 fraction bits (FP32 path)
     const uint32_t* p2;
     const uint32_t* p3;

@@ -70,11 +70,12 @@ struct TimeW {
 
 // Time weights of the B2 lookup of one pair. Slice times are non-negative, so their
 // IEEE bit patterns order like the values: the slice walk compares 64-bit integers
-// (integer pipe) instead of doubles (the FP64 pipe, GB300's bottleneck here). shb holds
-// the bit patterns of the slice times, shh the widths t_{k+1} - t_k, sinv their
-// reciprocals. The cubic Hermite basis uses h00 = 1 - h01 and
-// h10 = s (1-s)^2 h, h11 = -s^2 (1-s) h = -(s (1-s) h) s.
-__device__ __forceinline__ TimeW time_weights_f64(const long long* shb, const double* sht, const double* shh,
+// (integer pipe) instead of doubles (the FP64 pipe, GB300's bottleneck here); sinv holds
+// the reciprocal slice widths. The cubic Hermite basis uses h00 = 1 - h01 and
+// h10 = s (1-s)^2 h, h11 = -(s (1-s) h) s.
+__device__ __forceinline__ long long tbits(double x) { return __double_as_longlong(x); }
+
+__device__ __forceinline__ TimeW time_weights_f64(const double* sht,
                                                   const double* sinv, int n, bool ext, long long tlb,
                                                   double tl, double inv_hx, double tau, int hint) {
     TimeW r;
@@ -91,9 +92,9 @@ __device__ __forceinline__ TimeW time_weights_f64(const long long* shb, const do
         r.w0 = 1.0; r.w1 = 0.0; r.w2 = 0.0; r.w3 = 0.0;
     } else {
         int k = hint;
-        while (k < n - 2 && shb[k + 1] <= taub) ++k;
-        while (k > 0 && shb[k] > taub) --k;
-        const double hh = shh[k];
+        while (k < n - 2 && tbits(sht[k + 1]) <= taub) ++k;
+        while (k > 0 && tbits(sht[k]) > taub) --k;
+        const double hh = sht[k + 1] - sht[k];
         const double sg = (tau - sht[k]) * sinv[k];
         const double om = 1.0 - sg;
         const double p = sg * om * hh;
@@ -140,26 +141,20 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
     const double* __restrict__ ht = v.ht[act];
     dbl4* srow = reinterpret_cast<dbl4*>(smraw);            // [L] {K, D, C, R}
     double* sht = reinterpret_cast<double*>(srow + L);              // [cap] slice times
-    long long* shb = reinterpret_cast<long long*>(sht + v.cap);     // [cap] their bit patterns
-    double* shh = reinterpret_cast<double*>(shb + v.cap);           // [cap] t_{k+1} - t_k
-    double* sinvh = shh + v.cap;                                    // [cap] 1/(t_{k+1} - t_k)
+    double* sinvh = sht + v.cap;                                    // [cap] 1/(t_{k+1} - t_k)
     int* scell = reinterpret_cast<int*>(sinvh + v.cap);             // [L]
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         double C = row[i], R = row[L + i];
         srow[i] = dbl4{fp2(v.poly, C) * R, fp1(v.poly, C), C, R};
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const double ti = ht[i];
-        sht[i] = ti;
-        shb[i] = __double_as_longlong(ti);
-        const double hh = i + 1 < n ? ht[i + 1] - ti : 0.0;
-        shh[i] = hh;
-        sinvh[i] = i + 1 < n ? 1.0 / hh : 0.0;
+        sht[i] = ht[i];
+        sinvh[i] = i + 1 < n ? 1.0 / (ht[i + 1] - ht[i]) : 0.0;
     }
     for (int m = threadIdx.x; m < L; m += blockDim.x) scell[m] = v.cell[m];
     __syncthreads();
     const double tl = sht[n - 1];
-    const long long tlb = shb[n - 1];
+    const long long tlb = tbits(tl);
     const bool ext = t > tl;
     const double hx = t - tl;
     const double inv_hx = ext ? 1.0 / hx : 0.0;
@@ -242,7 +237,7 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
                 int cell = base2 + SW / 2 - 1;  // the grid cell of phi2 (a hint; the walk corrects)
                 cell = cell < 0 ? 0 : (cell > L - 1 ? L - 1 : cell);
                 const int h0 = scell[cell];
-                const TimeW b2 = time_weights_f64(shb, sht, shh, sinvh, n, ext, tlb, tl, inv_hx, tau2, h0);
+                const TimeW b2 = time_weights_f64(sht, sinvh, n, ext, tlb, tl, inv_hx, tau2, h0);
                 const unsigned char* e = w3r + (size_t)i * WTS;
                 const int b = *reinterpret_cast<const int*>(e);
                 double w[SW];
@@ -521,7 +516,7 @@ __global__ void __launch_bounds__(HI_THREADS, 1) k_batch_hi(const BatchTable* __
 
 size_t hi_smem_bytes(const SolverView& v) {
     if (v.precision == DMFE_FP64)
-        return (size_t)v.L * sizeof(dbl4) + (size_t)v.cap * 4 * sizeof(double) + (size_t)v.L * sizeof(int);
+        return (size_t)v.L * sizeof(dbl4) + (size_t)v.cap * 2 * sizeof(double) + (size_t)v.L * sizeof(int);
     return (size_t)v.L * sizeof(float4) + (size_t)v.cap * (sizeof(double) + 3 * sizeof(float)) +
            (size_t)v.L * sizeof(int);
 }

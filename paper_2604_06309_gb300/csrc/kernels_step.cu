@@ -99,8 +99,8 @@ __device__ double frac_index_dev(const SolverView& v, double th, double om) {
 }
 
 // Stencil entry of a fractional index x: base b = clamp(floor(x) - s/2 + 1, 0, L - s) and the
-// s Lagrange weights at u = x - b (Sec. 3.3), as FP64 or double-float numbers.
-__device__ void write_entry(unsigned char* base, size_t idx, double x, int L, int s, bool as_df) {
+// s Lagrange weights at u = x - b (Sec. 3.3) in FP64.
+__device__ void write_entry(unsigned char* base, size_t idx, double x, int L, int s) {
     int b = (int)floor(x) - s / 2 + 1;
     b = b < 0 ? 0 : (b > L - s ? L - s : b);
     const double u = x - b;
@@ -111,8 +111,7 @@ __device__ void write_entry(unsigned char* base, size_t idx, double x, int L, in
         double w = 1.0;
         for (int m = 0; m < s; ++m)
             if (m != k) w *= (u - m) / (double)(k - m);
-        if (as_df) reinterpret_cast<df*>(e + 8)[k] = df_from_d(w);
-        else reinterpret_cast<double*>(e + 8)[k] = w;
+        reinterpret_cast<double*>(e + 8)[k] = w;
     }
 }
 
@@ -140,10 +139,9 @@ __global__ void k_tables(SolverView v, double* x1, double* x2, double* x3, uint3
             q3[idx] = df_from_d(c);
         }
         if (v.wt1) {
-            const bool as_df = v.precision == DMFE_DOUBLE_FLOAT;
-            write_entry((unsigned char*)v.wt1, idx, a, v.L, v.s, as_df);
-            write_entry((unsigned char*)v.wt2, idx, b, v.L, v.s, as_df);
-            write_entry((unsigned char*)v.wt3, idx, c, v.L, v.s, as_df);
+            write_entry((unsigned char*)v.wt1, idx, a, v.L, v.s);
+            write_entry((unsigned char*)v.wt2, idx, b, v.L, v.s);
+            write_entry((unsigned char*)v.wt3, idx, c, v.L, v.s);
         }
         if (p1) {
             const double sc = (double)(1u << FIX_FRAC_BITS);

@@ -205,3 +205,17 @@ def test_failure_statuses_from_the_device():
     with pytest.raises(dmfe.DMFEError):
         g.get_C([5.0], [1.0])
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df", "fp32"])
+def test_largest_configured_grid_fits(precision):
+    """L = history_cap = 4097, the largest grid of the workloads: the solver and a batch
+    of that size are created (shared-memory tables fit), and one step runs."""
+    need_gpu()
+    from paper_2604_06309_gb300 import Batch, Solver
+    sv = Solver(MIXED_34, 0.5, 4097, 1e7, history_cap=4097, precision=precision)
+    sv.step(2, 1.0, 1e-8)
+    assert sv.sync() == 0 and sv.stats()["steps_accepted"] == 2
+    sv.close()
+    b = Batch(2, 4097, 4097, precision=precision)
+    b.close()
