@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--kernel-only", action="store_true",
                     help="only launch the history-integral kernel (for profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="step", choices=["step", "batch", "serve", "solve"],
+    ap.add_argument("--workload", default="step", choices=["step", "batch", "serve", "solve", "aging"],
                     help="step: the headline configuration; batch: 256 independent solves stepped "
                          "together; serve: Poisson-arrival requests with continuous batching")
     ap.add_argument("--window", type=float, default=30.0, help="seconds of batched or served work")
@@ -87,6 +87,9 @@ def parse():
     ap.add_argument("--checkpoints", default="1e2,1e3,1e4,1e5", help="solve: times at which to record")
     ap.add_argument("--compare", default="", help="solve: further precisions compared with --precision")
     ap.add_argument("--time-limit", type=float, default=900.0, help="solve: wall seconds per precision")
+    ap.add_argument("--coefs", default="3:0.5", help="aging: f(q) as power:coefficient,...")
+    ap.add_argument("--T", type=float, default=0.0, help="aging: bath temperature")
+    ap.add_argument("--tol", type=float, default=1e-12, help="aging: RK tolerance")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the double-float and FP32-compensated variants of the same workload")
     return ap.parse_args()
@@ -355,6 +358,51 @@ SOLVE_PAIRS = [(1.0, 0.0), (1.0, 0.5), (1.0, 0.9), (1.0, 0.99), (1.0, 0.999), (0
                (0.99, 0.5), (0.3, 0.0), (0.7, 0.69)]
 
 
+def energy_threshold(coefs):
+    """E_th = (f(1) - f'(1)) / sqrt(f''(1)) - f(1) sqrt(f''(1)) / f'(1) (Sec. 4.3)."""
+    f = sum(coefs.values())
+    f1 = sum(c * p for p, c in coefs.items())
+    f2 = sum(c * p * (p - 1) for p, c in coefs.items())
+    return (f - f1) / np.sqrt(f2) - f * np.sqrt(f2) / f1
+
+
+def run_aging(args):
+    """A quench to T (default the pure 3-spin f = q^3/2 to T = 0, Sec. 4.3) at a tight
+    tolerance: E(t) at log-spaced times and the local exponent t d/dt log(E - E_th), which
+    approaches -2/3 for pure models."""
+    from paper_2604_06309_gb300 import Solver
+    coefs = {int(a): float(b) for a, b in (x.split(":") for x in args.coefs.split(","))}
+    eth = energy_threshold(coefs)
+    sv = Solver(coefs, args.T, args.L, args.t_max, s=4, history_cap=args.L, precision=args.precision,
+                integrator=args.integrator)
+    times = np.exp(np.linspace(np.log(1.0), np.log(args.t_max), 41))
+    rec, t0 = [], time.perf_counter()
+    for tc in times:
+        while True:
+            sv.step(64, float(tc), args.tol)
+            st = sv.stats()
+            if st["status"] != 0:
+                raise RuntimeError("device status %d at t = %g" % (st["status"], st["t"]))
+            if st["t"] >= tc or time.perf_counter() - t0 > args.time_limit:
+                break
+        if st["t"] < tc:
+            break
+        _, _, _, mu, E = sv.get_row()
+        rec.append((float(tc), E, time.perf_counter() - t0, st["steps_accepted"] + st["steps_rejected"]))
+    sv.close()
+    t = np.array([r[0] for r in rec])
+    dE = np.array([r[1] for r in rec]) - eth
+    slope = np.gradient(np.log(dE), np.log(t)) if len(t) > 2 else np.array([])
+    return {"metric": "local energy exponent", "value": float(slope[-1]) if len(slope) else None,
+            "unit": "t d log(E - E_th) / dt", "n_gpus": 1, "higher_is_better": False,
+            "dtype": DTYPES[args.precision], "data": "synthetic",
+            "config": {"workload": "quench of f=%s to T=%g from a random initial state, L=%d, %d-slice store, "
+                                   "tol %g, integrator %s" % (args.coefs, args.T, args.L, args.L, args.tol,
+                                                              args.integrator), "E_th": eth},
+            "trace": [{"t": r[0], "E": r[1], "dE": float(d), "local_exponent": float(e), "wall_s": r[2],
+                       "steps": r[3]} for r, d, e in zip(rec, dE, slope)]}
+
+
 def run_solve(args):
     """Whole solves of the workload from t = 0 (Secs. 3.1-3.6), recorded at checkpoints."""
     import torch
@@ -587,6 +635,9 @@ def main():
         return
     if args.workload == "solve":
         print(json.dumps(run_solve(args)))
+        return
+    if args.workload == "aging":
+        print(json.dumps(run_aging(args)))
         return
     import torch
     if world > 1:

@@ -219,3 +219,24 @@ def test_largest_configured_grid_fits(precision):
     sv.close()
     b = Batch(2, 4097, 4097, precision=precision)
     b.close()
+
+
+def test_pure3_zero_temperature_energy_exponent():
+    """Sec. 4.3: after a quench of f = q^3/2 to T = 0 the energy approaches
+    E_th = -sqrt(4/3) from above as t^(-2/3). Over t = 25 .. 100 the local exponent
+    t d/dt log(E - E_th) is already within a few percent of -2/3 (-0.68 at t = 40, -0.675
+    at t = 100 on L = 1025 at tol 1e-12)."""
+    need_gpu()
+    from paper_2604_06309_gb300 import Solver
+    eth = -np.sqrt(4.0 / 3.0)
+    sv = Solver({3: 0.5}, 0.0, 513, 100.0, history_cap=513, precision="df")
+    ts = [25.0, 50.0, 100.0]
+    dE = []
+    for t in ts:
+        assert sv.integrate(t, 1e-11) == 0
+        dE.append(sv.get_row()[4] - eth)
+    sv.close()
+    assert all(d > 0 for d in dE) and dE[0] > dE[1] > dE[2]
+    slope = np.log(dE[2] / dE[1]) / np.log(2.0)
+    assert -0.70 < slope < -0.655, slope
+    assert 0.010 < dE[2] < 0.020, dE
