@@ -151,6 +151,24 @@ class Clocks:
         return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
 
 
+def reduce_max_over_ranks(vals, world):
+    """Each value's maximum over the ranks (an all-reduce after the timed region's barrier);
+    the values themselves at N = 1."""
+    if world == 1:
+        return [float(x) for x in vals]
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x) for x in vals], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def whole_job_rate(world, steps, max_time):
+    """Steps of all ranks per second of the slowest rank (each rank runs its own replica)."""
+    return world * steps / max_time
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2604_06309_gb300 import Solver
@@ -641,27 +659,21 @@ def main():
         return
     import torch
     if world > 1:
-        torch.distributed.init_process_group("nccl")
+        torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     res = run_ours(args, rank, world)
     if res is None:
         return
-    dev_time = res["dev_time"]
-    if world > 1:
-        t = torch.tensor([dev_time, res["e2e_time"]], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dev_time, e2e_time = float(t[0]), float(t[1])
-    else:
-        e2e_time = res["e2e_time"]
+    dev_time, e2e_time = reduce_max_over_ranks([res["dev_time"], res["e2e_time"]], world)
     if rank != 0:
         return
-    value = world * args.steps / dev_time
+    value = whole_job_rate(world, args.steps, dev_time)
     L = args.L
     roof = roofline(args.precision, res)
     line = {"metric": "RK steps/s", "value": value, "unit": "RK steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dev_time / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision],
             "data": "synthetic", "config": cfg,
-            "e2e": {"value": world * args.steps / e2e_time, "unit": "RK steps/s", "h2d_bytes_per_step": 0,
+            "e2e": {"value": whole_job_rate(world, args.steps, e2e_time), "unit": "RK steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 2 * L * 8 + 3 * 8},
             "gpu_launches": args.steps * LAUNCHES_PER_STEP,
             "roofline": roof, "clocks": res["clocks"], "solver": solver_info(res)}
@@ -692,7 +704,7 @@ def main():
         line["variants"] = variants
     if not args.no_variants and world == 1:
         line["pure3_quench"] = run_pure3_quench()
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(L)
     print(json.dumps(line))
 

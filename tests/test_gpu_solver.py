@@ -240,3 +240,22 @@ def test_pure3_zero_temperature_energy_exponent():
     slope = np.log(dE[2] / dE[1]) / np.log(2.0)
     assert -0.70 < slope < -0.655, slope
     assert 0.010 < dE[2] < 0.020, dE
+
+
+def test_mixed_3_9_quench_and_waiting_time_correlations():
+    """The (3+9)-spin mixture f = (q^3 + q^9)/4 (lambda = 1/2, Sec. 4.3) quenched to
+    T = 0.5: step-by-step parity with the oracle and the waiting-time correlations
+    C(t_w + t, t_w) read through dmfe_get_C."""
+    need_gpu()
+    coefs = {3: 0.25, 9: 0.25}
+    g, o = _pair(coefs, 0.5, 33, 100.0, cap=120)
+    assert g.integrate(4.0, 1e-8) == 0
+    assert o.integrate(4.0, 1e-8) == 0
+    _compare_runs(g, o)
+    tw = np.array([0.5, 1.0, 2.0])
+    for dt in (0.25, 1.0, 2.0):
+        got = g.get_C(tw + dt, tw)
+        assert np.max(np.abs(got - o.get_C(tw + dt, tw))) < 1e-9
+        # aging: the older the system, the slower C(t_w + t, t_w) decays
+        assert got[0] < got[1] < got[2]
+    g.close()
