@@ -75,7 +75,8 @@ def parse():
     ap.add_argument("--kernel-only", action="store_true",
                     help="only launch the history-integral kernel (for profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="step", choices=["step", "batch", "serve", "solve", "aging"],
+    ap.add_argument("--workload", default="step",
+                    choices=["step", "batch", "serve", "solve", "aging", "capacity"],
                     help="step: the headline configuration; batch: 256 independent solves stepped "
                          "together; serve: Poisson-arrival requests with continuous batching")
     ap.add_argument("--window", type=float, default=30.0, help="seconds of batched or served work")
@@ -555,6 +556,55 @@ def run_batch(args):
     return res
 
 
+def run_capacity(args, n_req=256, seed=20260406):
+    """Solves/s of the serving loop when it is never idle: n_req requests of the scaled
+    serving mix (L~U{65,129,257}, t_max~logU[10,100]) are all queued at once and served
+    with continuous batching; against the same requests solved one at a time by the plain
+    FP64 solver (each solve one dmfe_integrate call, for a fixed wall window). E of every
+    request finished by both is compared."""
+    import torch
+    from paper_2604_06309_gb300 import Server, Solver
+    reqs = batch_requests(n_req, seed=seed + 2, Ls=SERVE_LS, tmax_range=(10.0, 100.0))
+    free, _ = torch.cuda.mem_get_info()
+    srv = Server(args.slots, max(SERVE_LS), max(SERVE_LS), precision=args.precision, hbm_budget=int(0.5 * free),
+                 steps_per_round=4)
+    t0 = time.perf_counter()
+    ids = [srv.submit(r["coefs"], r["T"], r["L"], r["t_max"], r["t_max"], TOL, history_cap=r["L"]) for r in reqs]
+    results = []
+    while len(results) < n_req and time.perf_counter() - t0 < args.window:
+        results += srv.poll()
+        time.sleep(0.005)
+    wall = time.perf_counter() - t0
+    results += srv.poll()
+    srv.stop()
+    ok = {r["id"]: r for r in results if r["status"] == 0}
+    served_rate = len(ok) / wall
+    # the same requests one at a time, FP64, one dmfe_integrate per solve
+    seq, t1 = {}, time.perf_counter()
+    for rid, r in zip(ids, reqs):
+        if time.perf_counter() - t1 > args.window:
+            break
+        sv = Solver(r["coefs"], r["T"], r["L"], r["t_max"], history_cap=r["L"], precision="fp64")
+        if sv.integrate(r["t_max"], TOL) == 0:
+            seq[rid] = sv.get_row()[4]
+        sv.close()
+    seq_wall = time.perf_counter() - t1
+    seq_rate = len(seq) / seq_wall
+    both = [rid for rid in seq if rid in ok]
+    dE = max(abs(ok[rid]["E"] - seq[rid]) for rid in both) if both else None
+    lat = np.array([r["done_s"] - r["submit_s"] for r in ok.values()]) if ok else np.array([np.nan])
+    return {"metric": "served solves/s (saturated)", "value": served_rate, "unit": "solves/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": DTYPES[args.precision], "data": "synthetic",
+            "config": {"workload": "%d requests of (3+4)-spin solves, T~U[0.3,1], lambda~U[0,1], L=cap~U{65,129,257}, "
+                                   "t_max~logU[10,100], tol 1e-8, all queued at t=0, continuous batching in %d slots"
+                                   % (n_req, args.slots), "window_s": args.window},
+            "capacity": {"completed": len(ok), "wall_s": wall, "p50_latency_s": float(np.median(lat)),
+                         "p99_latency_s": float(np.percentile(lat, 99)),
+                         "single_fp64_completed": len(seq), "single_fp64_wall_s": seq_wall,
+                         "single_fp64_solves_per_s": seq_rate, "gain_vs_single_fp64": served_rate / seq_rate,
+                         "requests_compared": len(both), "max_abs_dE_vs_single_fp64": dE}}
+
+
 MIX_FOR_SINGLE = {3: 0.25, 4: 0.25}
 SERVE_LS = (65, 129, 257)
 
@@ -656,6 +706,9 @@ def main():
         return
     if args.workload == "aging":
         print(json.dumps(run_aging(args)))
+        return
+    if args.workload == "capacity":
+        print(json.dumps(run_capacity(args)))
         return
     import torch
     if world > 1:
