@@ -39,10 +39,11 @@ GRID_T_MAX = 1e5
 TOL = 1e-8
 # Algorithmic operations per (i, j) pair at stencil width 4, counted from the kernel
 # source (FMA = 2 flops). The Lagrange weights of the three stencils are read from the
-# per-grid tables, not computed per pair. FP64 kernel: A1 32, A2 16, B1 16, B2 (stage
-# time 3, time weights 12, two 4-point stencils of 4 fields 64, Hermite combination 16),
-# f' and f'' at two points for the (3+4) model 20, nine weighted products and sums 27.
-FLOP_PER_PAIR_S4 = 32 + 16 + 16 + 95 + 20 + 27
+# per-grid tables, not computed per pair. FP64 kernel: A1 32, A2 16, B1 12 (Horner on the
+# interval's monomial Hermite coefficients), B2 (stage time 3, interval coordinate 2, a
+# 4-point stencil of 8 coefficients 64, Horner 12), f' and f'' at two points for the (3+4)
+# model 20, nine weighted products and sums 27.
+FLOP_PER_PAIR_S4 = 32 + 16 + 12 + 81 + 20 + 27
 # Double-float kernel, FP32 flops of the double-float arithmetic: Lagrange weights from the
 # stored positions 3 x 118, B1 110, A1 220, A2 110, B2 713, f' and f'' 210, products and
 # sums 226.
@@ -51,7 +52,7 @@ DF_FP32_FLOP_PER_PAIR_S4 = 354 + 110 + 220 + 110 + 713 + 210 + 226
 # one ncu capture per precision (dram__bytes_read.sum + dram__bytes_write.sum of the first
 # launch inside the timed steps; profiles/traffic_k_hi_L2049_bench_state.md). Set to None
 # whenever the kernel changes until it is measured again.
-TRAFFIC_BYTES = {"fp64": 657725440 + 3474432, "df": 219070208 + 3332352, "fp32": 86010112 + 2716416}
+TRAFFIC_BYTES = {"fp64": 706801920 + 4269824, "df": 219070208 + 3332352, "fp32": 86010112 + 2716416}
 # Nominal per-GPU peaks derived from the unit counts and the 2.07 GHz maximum SM clock:
 # FP64 1.25 TFLOP/s (2 FMA lanes per SM); FP32 152 SMs x 128 lanes x 2 x 2.07e9.
 FP64_PEAK_GFLOPS = 1250.0
@@ -269,8 +270,9 @@ def _run_ours(args, rank, world, dev, stream):
 
     pairs = L * L
     n0 = n_state
-    wide = args.precision in ("fp64", "df")  # FP64 master or double-float replica: 8 B per value
-    bytes_hist = 4 * n0 * L * (8 if wide else 4)
+    # history read by the kernel: FP64 -- the intervals' monomial coefficients (8 doubles per
+    # interval and grid point); double-float replica (4 x 8 B); FP32 replica (4 x 4 B)
+    bytes_hist = {"fp64": 64 * (n0 - 1) * L, "df": 32 * n0 * L, "fp32": 16 * n0 * L}[args.precision]
     # stencil entries: {base, 4 FP64 weights} of 40 B (FP64), double-float positions of 8 B,
     # packed fixed-point positions of 4 B (FP32)
     bytes_tab = 3 * pairs * {"fp64": 40, "df": 8, "fp32": 4}[args.precision]

@@ -219,6 +219,9 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
         if (v.precision == DMFE_DOUBLE_FLOAT) {
             TRY(dev_alloc(h, &p, (size_t)cap * L * sizeof(df8))); v.histdf[b] = (df8*)p;
         }
+        if (v.precision == DMFE_FP64) {
+            TRY(dev_alloc(h, &p, (size_t)cap * L * sizeof(dbl8))); v.hcoef[b] = (dbl8*)p;
+        }
     }
     TRY(dev_alloc(h, &p, sizeof(DevState))); v.st = (DevState*)p;
     TRY(dev_alloc(h, &p, 2 * 2 * (size_t)L * sizeof(double))); v.Y = (double*)p;
@@ -398,6 +401,7 @@ unsigned long long dmfe_footprint(const dmfe_params* pin) {
         add(cap * L * sizeof(dbl4));
         if (p.precision == DMFE_FP32_COMPENSATED) add(cap * L * sizeof(float4));
         if (p.precision == DMFE_DOUBLE_FLOAT) add(cap * L * sizeof(df8));
+        if (p.precision == DMFE_FP64) add(cap * L * sizeof(dbl8));
     }
     add(sizeof(DevState)); add(4 * L * 8);
     add(2ull * kMaxPrepBlocks * 8); add(kCtlGrid * 8); add(4);

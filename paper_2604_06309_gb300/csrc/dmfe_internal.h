@@ -45,6 +45,14 @@ struct __align__(16) B1Desc {
     int a0, a1;
     double w[4];
     df wd[4];
+    double s;  // interior interval (a1 = a0 + 1): (theta_j t - t_a0) / (t_a1 - t_a0)
+};
+
+// Cubic Hermite interpolant of the history between slices k and k+1 (Sec. 3.3) in monomial
+// form in s = (tau - t_k) / (t_{k+1} - t_k): C = c0 + s (c1 + s (c2 + s c3)), R alike.
+// The FP64 kernel evaluates it by Horner's rule instead of forming four basis weights.
+struct __align__(64) dbl8 {
+    double c0, c1, c2, c3, r0, r1, r2, r3;
 };
 
 // Per-slice constants of one stage for the double-float kernel: complement
@@ -136,6 +144,7 @@ struct SolverView {
     dbl4* hist[2];        // [cap][L] {C, dC, R, dR} FP64 master
     float4* hist32[2];    // [cap][L] FP32 replica (FP32 path)
     df8* histdf[2];       // [cap][L] double-float replica (double-float path)
+    dbl8* hcoef[2];       // [cap][L] FP64 path: row k = monomial coefficients of interval k
     const df* q1;         // [L*L] double-float fractional index (double-float path)
     const df* q2;
     const df* q3;

@@ -57,6 +57,7 @@ __device__ __forceinline__ void stage_prep_body(const SolverView& v, const doubl
             const int c = find_slice_g(ht, n, tau);
             v.cell[q] = c;
             B1Desc d;
+            d.s = 0.0;
             if (ext && tau > tl) {
                 const double s = tau - tl, qq = s / hx;
                 d.a0 = n - 1; d.a1 = -1;
@@ -68,6 +69,7 @@ __device__ __forceinline__ void stage_prep_body(const SolverView& v, const doubl
                 const double hh = ht[c + 1] - ht[c];
                 const double sg = (tau - ht[c]) / hh, om = 1.0 - sg;
                 d.a0 = c; d.a1 = c + 1;
+                d.s = sg;
                 d.w[0] = (1.0 + 2.0 * sg) * om * om;
                 d.w[1] = sg * om * om * hh;
                 d.w[2] = sg * sg * (3.0 - 2.0 * sg);

@@ -138,6 +138,7 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
     const int act = st->active;
     const double t = from_state ? st->t_stage : t_arg;
     const dbl4* __restrict__ H = v.hist[act];
+    const dbl8* __restrict__ HC = v.hcoef[act];
     const double* __restrict__ ht = v.ht[act];
     dbl4* srow = reinterpret_cast<dbl4*>(smraw);            // [L] {K, D, C, R}
     double* sht = reinterpret_cast<double*>(srow + L);              // [cap] slice times
@@ -169,11 +170,14 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
         hi_unit_range(u, L, chunk, &j, &i0, &i1);
         const double thj = theta[j], omj = omega[j];
         TimeW b1;
+        double s1;
         {
             const B1Desc d = v.b1[j];
             b1.a0 = d.a0; b1.a1 = d.a1;
             b1.w0 = d.w[0]; b1.w1 = d.w[1]; b1.w2 = d.w[2]; b1.w3 = d.w[3];
+            s1 = d.s;
         }
+        const bool b1_interior = b1.a1 == b1.a0 + 1;  // else: the extension or a single slice
         constexpr size_t WTS = 8 + 8 * SW;  // bytes per stencil entry
         const unsigned char* __restrict__ w1r = v.wt1 + (size_t)j * L * WTS;
         const unsigned char* __restrict__ w2r = v.wt2 + (size_t)j * L * WTS;
@@ -185,7 +189,11 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
         for (int i = i0 + lane; i < i1; i += 32) {
             // ---- B1: on-grid column i at time theta_j t
             double CB1, RB1;
-            {
+            if (b1_interior) {
+                const dbl8 c = HC[(size_t)b1.a0 * L + i];
+                CB1 = c.c0 + s1 * (c.c1 + s1 * (c.c2 + s1 * c.c3));
+                RB1 = c.r0 + s1 * (c.r1 + s1 * (c.r2 + s1 * c.r3));
+            } else {
                 dbl4 h0 = H[(size_t)b1.a0 * L + i];
                 CB1 = b1.w0 * h0.x + b1.w1 * h0.y;
                 RB1 = b1.w0 * h0.z + b1.w1 * h0.w;
@@ -234,38 +242,52 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
             {
                 const double thi = theta[i];
                 const double tau2 = (thj + omj * thi) * t;
-                int cell = base2 + SW / 2 - 1;  // the grid cell of phi2 (a hint; the walk corrects)
-                cell = cell < 0 ? 0 : (cell > L - 1 ? L - 1 : cell);
-                const int h0 = scell[cell];
-                const TimeW b2 = time_weights_f64(sht, sinvh, n, ext, tlb, tl, inv_hx, tau2, h0);
+                const long long taub = tbits(tau2);
                 const unsigned char* e = w3r + (size_t)i * WTS;
                 const int b = *reinterpret_cast<const int*>(e);
                 double w[SW];
 #pragma unroll
                 for (int k = 0; k < SW; ++k) w[k] = reinterpret_cast<const double*>(e + 8)[k];
-                double c0 = 0, dc0 = 0, r0 = 0, dr0 = 0, c1 = 0, dc1 = 0, r1 = 0, dr1 = 0;
-                const dbl4* __restrict__ s0 = H + (size_t)b2.a0 * L + b;
+                if (n > 1 && !(ext && taub > tlb)) {
+                    // inside the stored history: the slice interval by a short walk from the
+                    // cell hint, theta stencil of its monomial coefficients, Horner in s
+                    int cell = base2 + SW / 2 - 1;  // the grid cell of phi2 (the walk corrects)
+                    cell = cell < 0 ? 0 : (cell > L - 1 ? L - 1 : cell);
+                    int k = scell[cell];
+                    while (k < n - 2 && tbits(sht[k + 1]) <= taub) ++k;
+                    while (k > 0 && tbits(sht[k]) > taub) --k;
+                    const double sg = (tau2 - sht[k]) * sinvh[k];
+                    const dbl8* __restrict__ P = HC + (size_t)k * L + b;
+                    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, q0 = 0, q1 = 0, q2 = 0, q3 = 0;
 #pragma unroll
-                for (int k = 0; k < SW; ++k) {
-                    dbl4 q = s0[k];
-                    c0 += w[k] * q.x; dc0 += w[k] * q.y; r0 += w[k] * q.z; dr0 += w[k] * q.w;
-                }
-                if (b2.a1 >= 0) {
-                    const dbl4* __restrict__ s1 = H + (size_t)b2.a1 * L + b;
-#pragma unroll
-                    for (int k = 0; k < SW; ++k) {
-                        dbl4 q = s1[k];
-                        c1 += w[k] * q.x; dc1 += w[k] * q.y; r1 += w[k] * q.z; dr1 += w[k] * q.w;
+                    for (int m = 0; m < SW; ++m) {
+                        const dbl8 c = P[m];
+                        a0 += w[m] * c.c0; a1 += w[m] * c.c1; a2 += w[m] * c.c2; a3 += w[m] * c.c3;
+                        q0 += w[m] * c.r0; q1 += w[m] * c.r1; q2 += w[m] * c.r2; q3 += w[m] * c.r3;
                     }
+                    CB2 = a0 + sg * (a1 + sg * (a2 + sg * a3));
+                    RB2 = q0 + sg * (q1 + sg * (q2 + sg * q3));
                 } else {
+                    // beyond the last slice (quadratic extension with the stage row) or a
+                    // single stored slice
+                    const TimeW b2 = time_weights_f64(sht, sinvh, n, ext, tlb, tl, inv_hx, tau2, 0);
+                    double c0 = 0, dc0 = 0, r0 = 0, dr0 = 0, c1 = 0, r1 = 0;
+                    const dbl4* __restrict__ s0 = H + (size_t)b2.a0 * L + b;
 #pragma unroll
-                    for (int k = 0; k < SW; ++k) {
-                        dbl4 q = srow[b + k];
-                        c1 += w[k] * q.z; r1 += w[k] * q.w;
+                    for (int m = 0; m < SW; ++m) {
+                        dbl4 q = s0[m];
+                        c0 += w[m] * q.x; dc0 += w[m] * q.y; r0 += w[m] * q.z; dr0 += w[m] * q.w;
                     }
+                    if (b2.a1 < 0) {
+#pragma unroll
+                        for (int m = 0; m < SW; ++m) {
+                            dbl4 q = srow[b + m];
+                            c1 += w[m] * q.z; r1 += w[m] * q.w;
+                        }
+                    }
+                    CB2 = b2.w0 * c0 + b2.w1 * dc0 + b2.w2 * c1;
+                    RB2 = b2.w0 * r0 + b2.w1 * dr0 + b2.w2 * r1;
                 }
-                CB2 = b2.w0 * c0 + b2.w1 * dc0 + b2.w2 * c1 + b2.w3 * dc1;
-                RB2 = b2.w0 * r0 + b2.w1 * dr0 + b2.w2 * r1 + b2.w3 * dr1;
             }
             const double f1a = fp1(v.poly, CB1), f2a = fp2(v.poly, CB1);
             const double f1b = fp1(v.poly, CB2), f2b = fp2(v.poly, CB2);

@@ -251,18 +251,38 @@ __global__ void __launch_bounds__(CTL_THREADS) k_initial(SolverView v) {
 
 __device__ __forceinline__ bool gated(const DevState* st) { return st->status != 0 || st->done; }
 
-// Write slice `slot` = (t, Y, dY) to the active buffer (FP64 master and FP32 replica).
+// Monomial coefficients of the cubic Hermite interpolant between history points a (at t_k)
+// and b (at t_k + h), for C (x, y = value, derivative) and R (z, w).
+__device__ __forceinline__ dbl8 interval_coef(const dbl4& a, const dbl4& b, double h) {
+    const double dC = b.x - a.x, dR = b.z - a.z;
+    dbl8 c;
+    c.c0 = a.x;
+    c.c1 = h * a.y;
+    c.c2 = 3.0 * dC - h * (2.0 * a.y + b.y);
+    c.c3 = -2.0 * dC + h * (a.y + b.y);
+    c.r0 = a.z;
+    c.r1 = h * a.w;
+    c.r2 = 3.0 * dR - h * (2.0 * a.w + b.w);
+    c.r3 = -2.0 * dR + h * (a.w + b.w);
+    return c;
+}
+
+// Write slice `slot` = (t, Y, dY) to buffer `act`: FP64 master, the replica of the
+// precision, and (FP64 path) the interval coefficients between slots slot-1 and slot.
 __device__ void append_slice(const SolverView& v, int act, int slot, double t, const double* Y,
                              const double* dY) {
     const int L = v.L;
     dbl4* H = v.hist[act] + (size_t)slot * L;
     float4* H32 = v.hist32[act] ? v.hist32[act] + (size_t)slot * L : nullptr;
     df8* HD = v.histdf[act] ? v.histdf[act] + (size_t)slot * L : nullptr;
+    dbl8* HC = (v.hcoef[act] && slot >= 1) ? v.hcoef[act] + (size_t)(slot - 1) * L : nullptr;
+    const double hprev = slot >= 1 ? t - v.ht[act][slot - 1] : 0.0;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         const dbl4 e{Y[i], dY[i], Y[L + i], dY[L + i]};
         H[i] = e;
         if (H32) H32[i] = make_float4((float)e.x, (float)e.y, (float)e.z, (float)e.w);
         if (HD) HD[i] = df8{df_from_d(e.x), df_from_d(e.y), df_from_d(e.z), df_from_d(e.w)};
+        if (HC) HC[i] = interval_coef(H[(long long)i - L], e, hprev);
     }
     if (threadIdx.x == 0) v.ht[act][slot] = t;
 }
@@ -601,6 +621,13 @@ __device__ __forceinline__ void sp_compact_body(const SolverView& v, int cta, in
         v.hist[nxt][dst] = v.hist[act][q];
         if (v.hist32[act]) v.hist32[nxt][dst] = v.hist32[act][q];
         if (v.histdf[act]) v.histdf[nxt][dst] = v.histdf[act][q];
+        if (v.hcoef[act] && k > 0) {
+            // interval from the previous kept slice (slice 0 is never removed)
+            int p = k - 1;
+            while (p > 0 && !v.keep[p]) --p;
+            v.hcoef[nxt][dst - L] = interval_coef(v.hist[act][(size_t)p * L + i], v.hist[act][q],
+                                                  v.ht[act][k] - v.ht[act][p]);
+        }
         if (i == 0) v.ht[nxt][v.newidx[k]] = v.ht[act][k];
     }
 }
@@ -709,6 +736,9 @@ __global__ void k_refresh_replica(SolverView v) {
         const dbl4 e = v.hist[act][q];
         if (v.hist32[act]) v.hist32[act][q] = make_float4((float)e.x, (float)e.y, (float)e.z, (float)e.w);
         if (v.histdf[act]) v.histdf[act][q] = df8{df_from_d(e.x), df_from_d(e.y), df_from_d(e.z), df_from_d(e.w)};
+        const int k = (int)(q / v.L);
+        if (v.hcoef[act] && k + 1 < st->n)
+            v.hcoef[act][q] = interval_coef(e, v.hist[act][q + v.L], v.ht[act][k + 1] - v.ht[act][k]);
     }
 }
 
@@ -808,7 +838,7 @@ int launch_lookup(const SolverView& v, int n, const double* t, const double* tp,
 }
 
 int launch_refresh_replica(const SolverView& v, cudaStream_t s) {
-    if (!v.hist32[0] && !v.histdf[0]) return DMFE_OK;
+    if (!v.hist32[0] && !v.histdf[0] && !v.hcoef[0]) return DMFE_OK;
     k_refresh_replica<<<grid_for((long long)v.cap * v.L, 256), 256, 0, s>>>(v);
     DMFE_CUDA_TRY(cudaGetLastError());
     return DMFE_OK;

@@ -259,3 +259,25 @@ def test_mixed_3_9_quench_and_waiting_time_correlations():
         # aging: the older the system, the slower C(t_w + t, t_w) decays
         assert got[0] < got[1] < got[2]
     g.close()
+
+
+@pytest.mark.parametrize("kw", [
+    dict(L=65, s=10),                              # the paper's default 9th-order stencil
+    dict(L=33, beta0=1.2),                         # equilibrium initial state (forcing F_C)
+    dict(L=49, alpha=0.5, delta=0.2),              # trade-off parameters of Eq. (theta)
+    dict(L=16, history_cap=16),                    # the smallest grid and store
+    dict(L=33, s=6, history_cap=20, dt0=0.2),      # rejections and passes at s = 6
+])
+def test_solve_variants_match_oracle_step_by_step(kw):
+    need_gpu()
+    kw = dict(kw)
+    L = kw.pop("L")
+    cap = kw.pop("history_cap", 200)
+    g, o = _pair(MIXED_34, 0.5, L, 100.0, cap=cap, **kw)
+    assert g.integrate(1.5, 1e-8) == 0
+    assert o.integrate(1.5, 1e-8) == 0
+    _compare_runs(g, o)
+    t, tp = np.array([1.5, 1.5, 1.2]), np.array([0.0, 0.7, 1.1])
+    assert np.max(np.abs(g.get_C(t, tp) - o.get_C(t, tp))) < 1e-9
+    assert np.max(np.abs(g.get_R(t, tp) - o.get_R(t, tp))) < 1e-9
+    g.close()
