@@ -86,6 +86,10 @@ typedef struct {
                                    which Dormand-Prince 5 (real stability interval beta_DP =
                                    3.3066) reaches the spectral bound ||J|| <= 4 sqrt(f''(1))
                                    of Sec. 3.5; no switch when f''(1) <= 0              */
+    int           hi_chunk;     /* summation indices per work unit of the history-integral
+                                   kernel, >= 32; 0 (default): chosen from L and the precision
+                                   for a single solve, L for a batch slot. Changes only the
+                                   summation order (see dmfe_autotune)                   */
 } dmfe_params;
 
 /* Per-solve counters. */
@@ -203,7 +207,7 @@ int dmfe_checkpoint(dmfe_solver* h, const char* path);
 int dmfe_restore(const char* path, void* stream, dmfe_solver** out);
 
 /* Autotune the work-unit size of the history-integral kernel (summation indices per
- * unit: the candidates 256, 512, 1024, 2048, 4096, L and L/P for P = 2..16, at least 256)
+ * unit: the candidates 32, 64, ..., 4096, L and L/P for P = 2..16, at least 32)
  * by timing the kernel on the
  * solver's current history and stage row, and keep the fastest. Results are cached per
  * (L, history_cap, s, precision) for the process. Changes the summation order of the

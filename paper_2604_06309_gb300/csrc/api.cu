@@ -86,12 +86,17 @@ void build_poly(const std::vector<int>& pw, const std::vector<double>& cf, Poly&
 }
 
 // Work-unit size of the history-integral kernels (summation indices per unit).
-constexpr int kMinChunk = 256;
+constexpr int kMinChunk = 32;
 int default_chunk(int precision, int L) {
-    // measured on GB300 at L = 2049 and 4097: the FP32-pipe kernels run best with one
-    // unit per output index; the FP64 kernel with 1024-index units up to L ~ 3000
-    if (precision == DMFE_FP64 && L < 3072) return 1024;
-    return L;
+    // Enough units to give every warp slot of the GPU (152 SMs x 16 warps) some work at
+    // small L; at large L measured on GB300 (L = 2049, 4097): the FP32-pipe kernels run
+    // best with one unit per output index, the FP64 kernel with 1024-index units up to
+    // L ~ 3000.
+    const long long per_warp = (long long)L * L / (152 * 16);
+    int c = per_warp < kMinChunk ? kMinChunk : (int)((per_warp + 31) / 32 * 32);
+    const int cap = (precision == DMFE_FP64 && L < 3072) ? 1024 : L;
+    if (c > cap) c = cap;
+    return c >= L ? L : c;
 }
 
 int validate(const dmfe_params* p) {
@@ -112,6 +117,7 @@ int validate(const dmfe_params* p) {
     if (p->integrator != DMFE_RK_AUTO && p->integrator != DMFE_RK_DP5 && p->integrator != DMFE_RK_SSPRK104)
         return DMFE_ERR_ARG;
     if (!(p->rk_switch_dt >= 0.0)) return DMFE_ERR_ARG;
+    if (p->hi_chunk != 0 && p->hi_chunk < kMinChunk) return DMFE_ERR_ARG;
     if (p->s != 4 && p->s != 6 && p->s != 8 && p->s != 10) return DMFE_ERR_UNSUPPORTED;
     return DMFE_OK;
 }
@@ -240,10 +246,10 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
     if (!v.cell) { TRY(dev_alloc(h, &p, L * sizeof(int))); v.cell = (int*)p; }
     TRY(dev_alloc(h, &p, (size_t)L * sizeof(int))); v.jcount = (int*)p;
     DMFE_CUDA_TRY(cudaMemsetAsync(v.jcount, 0, (size_t)L * sizeof(int), h->stream));
-    v.hi_chunk = default_chunk(v.precision, L);
+    v.hi_chunk = pin->hi_chunk > 0 ? (pin->hi_chunk < L ? pin->hi_chunk : L) : default_chunk(v.precision, L);
     if (const char* e = std::getenv("DMFE_HI_CHUNK")) {
         const int c = std::atoi(e);
-        if (c >= kMinChunk && c % 32 == 0) v.hi_chunk = c;
+        if (c >= kMinChunk) v.hi_chunk = c < L ? c : L;
     }
     TRY(dev_alloc(h, &p, cap * sizeof(double))); v.eps_sp = (double*)p;
     TRY(dev_alloc(h, &p, cap * sizeof(int))); v.keep = (int*)p;
@@ -355,6 +361,7 @@ void dmfe_default_params(dmfe_params* p) {
     p->sparsify = 1;
     p->integrator = DMFE_RK_AUTO;
     p->rk_switch_dt = 0.0;
+    p->hi_chunk = 0;
 }
 
 const char* dmfe_strerror(int code) {
@@ -743,7 +750,7 @@ int dmfe_autotune(dmfe_solver* h, int* chunk_out) {
         double* d = h->scratch;
         DMFE_CUDA_TRY(cudaMemcpyAsync(d, CR.data(), 2 * L * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         std::vector<int> cands;
-        for (int c : {kMinChunk, 512, 1024, 2048, 4096, L}) {
+        for (int c : {kMinChunk, 64, 128, 256, 512, 1024, 2048, 4096, L}) {
             const int cc = c >= L ? L : c;
             if (cc >= kMinChunk || cc == L)
                 if (std::find(cands.begin(), cands.end(), cc) == cands.end()) cands.push_back(cc);

@@ -161,6 +161,9 @@ int dmfe_batch_add(dmfe_batch* b, const dmfe_params* p, double t_max, double tol
     if (k == b->max_slots) return DMFE_ERR_CAPACITY;
     dmfe_params q = *p;
     q.stream = b->stream;
+    // one unit per output index unless asked otherwise: a batch has parallelism across
+    // slots, and larger units carry less per-unit reduction overhead
+    if (q.hi_chunk == 0) q.hi_chunk = q.L;
     dmfe_solver* h = nullptr;
     TRYB(dmfe_create(&q, &h));
     const int rc = launch_begin_integrate(solver_view(h), t_max, tol, b->stream);

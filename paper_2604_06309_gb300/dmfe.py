@@ -45,7 +45,7 @@ class dmfe_params(ctypes.Structure):
     _fields_ = [("n_terms", _i), ("powers", _ip), ("coefs", _dp), ("T", _d), ("beta0", _d),
                 ("L", _i), ("s", _i), ("grid_t_max", _d), ("alpha", _d), ("delta", _d),
                 ("history_cap", _i), ("dt0", _d), ("dt_min", _d), ("precision", _i),
-                ("sparsify", _i), ("stream", _p), ("integrator", _i), ("rk_switch_dt", _d)]
+                ("sparsify", _i), ("stream", _p), ("integrator", _i), ("rk_switch_dt", _d), ("hi_chunk", _i)]
 
 
 class dmfe_stats_t(ctypes.Structure):
@@ -153,7 +153,8 @@ def _f64(a, n=None):
 
 
 def make_params(coefs, T, L, grid_t_max, s=4, beta0=0.0, alpha=0.0, delta=0.0, history_cap=None, dt0=1e-4,
-                dt_min=1e-12, precision="fp64", sparsify=True, stream=None, integrator="auto", switch_dt=0.0):
+                dt_min=1e-12, precision="fp64", sparsify=True, stream=None, integrator="auto", switch_dt=0.0,
+                hi_chunk=0):
     """A dmfe_params structure; the returned tuple keeps the coefficient arrays alive."""
     lib = load()
     terms = sorted((int(p), float(c)) for p, c in dict(coefs).items())
@@ -173,6 +174,7 @@ def make_params(coefs, T, L, grid_t_max, s=4, beta0=0.0, alpha=0.0, delta=0.0, h
     prm.stream = stream
     prm.integrator = INTEGRATORS[integrator]
     prm.rk_switch_dt = float(switch_dt)
+    prm.hi_chunk = int(hi_chunk)
     return prm, (pw, cf)
 
 
@@ -291,7 +293,7 @@ class Solver:
 
     def __init__(self, coefs, T, L, grid_t_max, s=4, beta0=0.0, alpha=0.0, delta=0.0,
                  history_cap=None, dt0=1e-4, dt_min=1e-12, precision="fp64", sparsify=True,
-                 stream=None, integrator="auto", switch_dt=0.0):
+                 stream=None, integrator="auto", switch_dt=0.0, hi_chunk=0):
         """integrator: "auto" (Dormand-Prince, then SSPRK(10,4) once the step reaches
         switch_dt; 0 = the stability estimate), "dp5" or "ssprk104" (Sec. 3.5)."""
         lib = load()
@@ -300,7 +302,8 @@ class Solver:
         self._owned = True
         prm, keep = make_params(coefs, T, L, grid_t_max, s=s, beta0=beta0, alpha=alpha, delta=delta,
                                 history_cap=history_cap, dt0=dt0, dt_min=dt_min, precision=precision,
-                                sparsify=sparsify, stream=stream, integrator=integrator, switch_dt=switch_dt)
+                                sparsify=sparsify, stream=stream, integrator=integrator, switch_dt=switch_dt,
+                                hi_chunk=hi_chunk)
         _check(lib.dmfe_create(ctypes.byref(prm), ctypes.byref(self.h)), "dmfe_create")
         self._sizes()
 

@@ -17,7 +17,9 @@ CASES = [  # (f, T, L, cap, grid t_max, t_max)
 def _alone(case, precision, tol):
     from paper_2604_06309_gb300 import Solver
     f, T, L, cap, gtm, tmax = case
-    sv = Solver(f, T, L, gtm, history_cap=cap, precision=precision)
+    # a batch slot runs one work unit per output index (hi_chunk = L): the same here, so
+    # that the summation order, and hence every bit, agrees
+    sv = Solver(f, T, L, gtm, history_cap=cap, precision=precision, hi_chunk=L)
     assert sv.integrate(tmax, tol) == 0
     out = sv.get_history()
     st = sv.stats()
@@ -109,7 +111,7 @@ def test_server_results_equal_solo_runs():
     assert len(res) == len(CASES) and st["completed"] == len(CASES) and st["failed"] == 0
     for rid, c in ids.items():
         f, T, L, cap, gtm, tmax = c
-        sv = Solver(f, T, L, gtm, history_cap=cap, precision="df")
+        sv = Solver(f, T, L, gtm, history_cap=cap, precision="df", hi_chunk=L)
         assert sv.integrate(tmax, tol) == 0
         t, _, _, mu, E = sv.get_row()
         r = res[rid]

@@ -115,7 +115,7 @@ def test_batch_mixing_methods_is_bitwise_equal_to_solo_runs(precision):
     assert running == 0
     for (f, T, L, cap, tmax, kw), k in zip(cases, slots):
         assert status[k] == 1 and t[k] == tmax
-        sv = Solver(f, T, L, 1e3, history_cap=cap, precision=precision, **kw)
+        sv = Solver(f, T, L, 1e3, history_cap=cap, precision=precision, hi_chunk=L, **kw)
         assert sv.integrate(tmax, tol) == 0
         for x, y in zip(b.solver(k).get_history(), sv.get_history()):
             assert np.array_equal(x, y)
