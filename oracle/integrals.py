@@ -63,7 +63,7 @@ mu = T - p E for pure models; the theta = 1 value d1 C(t, t^-) = -T).
 
 import numpy as np
 
-from .interp import lagrange_stencil, hermite
+from .interp import lagrange_stencil, scheme_stencil, hermite
 
 NS = 10  # number of rows of S
 
@@ -78,9 +78,13 @@ class Grid:
 
     CACHE_MAX_L = 1024
 
-    def __init__(self, L, t_max, s=4, alpha=0.0, delta=0.0):
+    def __init__(self, L, t_max, s=4, alpha=0.0, delta=0.0, interp="lagrange_index", fh_d=3):
         from . import grid as g
         from .quadrature import spline_weights
+        from .interp import SCHEMES
+        if interp not in SCHEMES:
+            raise ValueError("unknown interpolation scheme %r" % interp)
+        self.interp, self.fh_d = interp, int(fh_d)
         self.L, self.s = int(L), int(s)
         self.t_max, self.alpha, self.delta = float(t_max), float(alpha), float(delta)
         self.gamma = g.gamma_from_tmax(t_max)
@@ -89,7 +93,8 @@ class Grid:
         self._cache = self.positions(slice(0, self.L)) if self.L <= self.CACHE_MAX_L else None
 
     def positions(self, js):
-        """(phi2, x1, x2, x3) for output rows js: fractional indices of phi1, phi2, psi."""
+        """(phi2, x1, x2, x3, o1, o2, o3) for output rows js: fractional indices of phi1,
+        phi2, psi and their complements 1 - phi1, 1 - phi2, 1 - psi."""
         from . import grid as g
         th, om = self.theta, self.omega
         thj, omj = th[js][:, None], om[js][:, None]  # output index j along axis 0
@@ -103,16 +108,20 @@ class Grid:
         psi = np.where(phi2 > 0, thj / safe, 0.0)
         opsi = np.where(phi2 > 0, omj * thi / safe, 1.0)
         fi = lambda a, b: g.frac_index(a, b, self.L, self.gamma, self.alpha, self.delta)
-        return phi2, fi(phi1, ophi1), fi(phi2, ophi2), fi(psi, opsi)
+        return phi2, fi(phi1, ophi1), fi(phi2, ophi2), fi(psi, opsi), ophi1, ophi2, opsi
+
+    def stencil_at(self, x, om):
+        """(base, weights) of the grid's interpolation scheme at fractional index x whose
+        point has complement om = 1 - theta."""
+        return scheme_stencil(x, om, self.omega, self.L, self.s, self.interp, self.fh_d)
 
     def stencils(self, js):
-        """(phi2, st1, st2, st3) for rows js; st = (base, weights) of lagrange_stencil."""
+        """(phi2, st1, st2, st3) for rows js; st = (base, weights) of the grid's scheme."""
         if self._cache is not None:
-            phi2, x1, x2, x3 = (a[js] for a in self._cache)
+            phi2, x1, x2, x3, o1, o2, o3 = (a[js] for a in self._cache)
         else:
-            phi2, x1, x2, x3 = self.positions(js)
-        return (phi2, lagrange_stencil(x1, self.L, self.s), lagrange_stencil(x2, self.L, self.s),
-                lagrange_stencil(x3, self.L, self.s))
+            phi2, x1, x2, x3, o1, o2, o3 = self.positions(js)
+        return phi2, self.stencil_at(x1, o1), self.stencil_at(x2, o2), self.stencil_at(x3, o3)
 
 
 class History:

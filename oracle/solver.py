@@ -261,13 +261,13 @@ class Solver:
 
     def __init__(self, coefs, T, L, grid_t_max, s=4, beta0=0.0, alpha=0.0, delta=0.0,
                  history_cap=None, dt0=1e-4, dt_min=1e-12, sparsify=True, integrator="auto",
-                 switch_dt=0.0):
+                 switch_dt=0.0, interp="lagrange_index", fh_d=3):
         """integrator: "dp5" (Dormand-Prince throughout), "ssprk104" (SSPRK(10,4)
         throughout) or "auto" (Dormand-Prince, then SSPRK(10,4) once dt reaches
         switch_dt; switch_dt = 0 takes the stability estimate switch_dt_auto)."""
         from .model import Model
         self.model = Model(coefs, T, beta0)
-        self.grid = Grid(L, grid_t_max, s, alpha, delta)
+        self.grid = Grid(L, grid_t_max, s, alpha, delta, interp=interp, fh_d=fh_d)
         self.cap = int(history_cap if history_cap is not None else L)
         if self.cap < 16:
             raise ValueError("history_cap must be at least 16")
@@ -377,7 +377,7 @@ def get_two_time(grid, hist, t, tp, which):
     th = np.where(pos, small / np.where(pos, big, 1.0), 1.0)
     om = np.where(pos, (big - small) / np.where(pos, big, 1.0), 0.0)
     x = gridmod.frac_index(th, om, grid.L, grid.gamma, grid.alpha, grid.delta)
-    b, w = lagrange_stencil(x, grid.L, grid.s)
+    b, w = grid.stencil_at(x, om)
     Y, dY = (hist.C, hist.dC) if which == "C" else (hist.R, hist.dR)
     N = hist.N
     if N == 1:

@@ -145,8 +145,8 @@ def test_planted_mistakes_are_caught_by_the_p2_pin(mutation):
         dC, dR = d1C, -mu * R + t * G.omega * S[3]
     else:  # B2 read at theta_i / phi2 instead of theta_j / phi2 (phi2 itself is symmetric)
         G2 = Grid(129, 100.0, s=6)
-        phi2, x1, x2, x3 = G2._cache
-        G2._cache = (phi2, x1, x2, x3.T.copy())
+        phi2, x1, x2, x3, o1, o2, o3 = G2._cache
+        G2._cache = (phi2, x1, x2, x3.T.copy(), o1, o2, o3.T.copy())
         S = I.history_integrals(P2, G2, H, t, C, R)
         dC, dR = I.assemble_rhs(P2, G, t, C, R, S, mu)
     _, dCx, _, dRx = cf.p2_fields(t, G.theta, G.omega)
