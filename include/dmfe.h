@@ -51,6 +51,12 @@ extern "C" {
                                      FP32 pipes over a double-float history replica; FP64 for
                                      everything else. FP64-class results at FP32-pipe speed */
 
+/* ---- theta interpolation (Sec. 3.3) ------------------------------------------- */
+#define DMFE_INTERP_LAGRANGE_INDEX 0  /* Lagrange in the grid index (default)                  */
+#define DMFE_INTERP_FH_INDEX       1  /* Floater-Hormann rational, blending degree fh_d, index  */
+#define DMFE_INTERP_LAGRANGE_THETA 2  /* Lagrange on the theta values of the stencil nodes      */
+#define DMFE_INTERP_FH_THETA       3  /* Floater-Hormann on the theta values                    */
+
 /* ---- integrator (Sec. 3.5) ---------------------------------------------------- */
 #define DMFE_RK_AUTO      0  /* Dormand-Prince 5(4) until the controller step reaches the
                                 switch step, then SSPRK(10,4) with the step halved (default) */
@@ -90,6 +96,12 @@ typedef struct {
                                    kernel, >= 32; 0 (default): chosen from L and the precision
                                    for a single solve, L for a batch slot. Changes only the
                                    summation order (see dmfe_autotune)                   */
+    int           interp;       /* DMFE_INTERP_*: the theta-stencil scheme (default Lagrange in
+                                   the index). The other schemes need DMFE_FP64 (their
+                                   weights live in the FP64 stencil tables); otherwise
+                                   dmfe_create returns DMFE_ERR_UNSUPPORTED              */
+    int           fh_d;         /* Floater-Hormann blending degree, 0 <= fh_d <= s-1
+                                   (default 3; fh_d = s-1 is the polynomial interpolant)  */
 } dmfe_params;
 
 /* Per-solve counters. */

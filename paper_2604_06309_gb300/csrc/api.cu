@@ -118,7 +118,13 @@ int validate(const dmfe_params* p) {
         return DMFE_ERR_ARG;
     if (!(p->rk_switch_dt >= 0.0)) return DMFE_ERR_ARG;
     if (p->hi_chunk != 0 && p->hi_chunk < kMinChunk) return DMFE_ERR_ARG;
+    if (p->interp < DMFE_INTERP_LAGRANGE_INDEX || p->interp > DMFE_INTERP_FH_THETA) return DMFE_ERR_ARG;
+    if ((p->interp == DMFE_INTERP_FH_INDEX || p->interp == DMFE_INTERP_FH_THETA) &&
+        (p->fh_d < 0 || p->fh_d > p->s - 1))
+        return DMFE_ERR_ARG;
     if (p->s != 4 && p->s != 6 && p->s != 8 && p->s != 10) return DMFE_ERR_UNSUPPORTED;
+    // the other schemes' weights live in the FP64 stencil tables
+    if (p->interp != DMFE_INTERP_LAGRANGE_INDEX && p->precision != DMFE_FP64) return DMFE_ERR_UNSUPPORTED;
     return DMFE_OK;
 }
 
@@ -172,6 +178,8 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
     v.T = pin->T;
     v.beta0 = pin->beta0;
     v.rk_switch_dt = switch_dt_for(&h->p);
+    v.interp = pin->interp;
+    v.fh_d = pin->fh_d;
     build_poly(h->powers, h->coefs, v.poly);
     v.gamma = host_gamma_from_tmax(pin->grid_t_max);
     v.ga = std::atan(std::exp(-v.gamma));
@@ -362,6 +370,8 @@ void dmfe_default_params(dmfe_params* p) {
     p->integrator = DMFE_RK_AUTO;
     p->rk_switch_dt = 0.0;
     p->hi_chunk = 0;
+    p->interp = DMFE_INTERP_LAGRANGE_INDEX;
+    p->fh_d = 3;
 }
 
 const char* dmfe_strerror(int code) {

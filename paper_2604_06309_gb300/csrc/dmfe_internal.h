@@ -123,6 +123,7 @@ struct SolverView {
     int L, s, cap, precision;
     int sparsify;         // 1: pass when the store is full
     double rk_switch_dt;  // controller step of the switch to SSPRK(10,4) (+inf: never)
+    int interp, fh_d;     // theta-stencil scheme (DMFE_INTERP_*) and Floater-Hormann degree
     double T, beta0;
     double gamma, ga, gD, alpha, delta;  // grid: gamma, atan(e^-gamma), atan(e^gamma) - atan(e^-gamma)
     Poly poly;

@@ -98,21 +98,59 @@ __device__ double frac_index_dev(const SolverView& v, double th, double om) {
     return x < 0.0 ? 0.0 : (x > L - 1.0 ? L - 1.0 : x);
 }
 
-// Stencil entry of a fractional index x: base b = clamp(floor(x) - s/2 + 1, 0, L - s) and the
-// s Lagrange weights at u = x - b (Sec. 3.3) in FP64.
-__device__ void write_entry(unsigned char* base, size_t idx, double x, int L, int s) {
+// Weights of the s-point theta stencil at base b (Sec. 3.3) for the solver's scheme: the
+// default Lagrange basis in the index at u = x - b (product form), or Floater-Hormann
+// rational interpolation (Floater & Hormann 2007) with blending degree d -- barycentric
+// weights beta_k = sum_{i in J_k} (-1)^i prod_{j=i..i+d, j != k} 1/(x_k - x_j), J_k =
+// {max(0, k-d) .. min(k, s-1-d)}, w_k proportional to beta_k / (point - x_k) -- on the
+// index nodes 0..s-1 or on the complements 1 - theta of the nodes, at the point's
+// complement om (theta schemes; d = s - 1 there for Lagrange).
+__device__ void stencil_weights(const SolverView& v, int b, double x, double om, double* w) {
+    const int s = v.s;
+    if (v.interp == DMFE_INTERP_LAGRANGE_INDEX) {
+        const double u = x - b;
+        for (int k = 0; k < s; ++k) {
+            double p = 1.0;
+            for (int m = 0; m < s; ++m)
+                if (m != k) p *= (u - m) / (double)(k - m);
+            w[k] = p;
+        }
+        return;
+    }
+    const bool theta_nodes = v.interp == DMFE_INTERP_LAGRANGE_THETA || v.interp == DMFE_INTERP_FH_THETA;
+    const int d = (v.interp == DMFE_INTERP_LAGRANGE_THETA) ? s - 1 : v.fh_d;
+    double xn[16];
+    for (int k = 0; k < s; ++k) xn[k] = theta_nodes ? v.omega[b + k] : (double)k;
+    const double pt = theta_nodes ? om : x - b;
+    double sum = 0.0;
+    int hit = -1;
+    for (int k = 0; k < s; ++k) {
+        double beta = 0.0;
+        const int i0 = k - d > 0 ? k - d : 0, i1 = k < s - 1 - d ? k : s - 1 - d;
+        for (int i = i0; i <= i1; ++i) {
+            double term = (i & 1) ? -1.0 : 1.0;
+            for (int j = i; j <= i + d; ++j)
+                if (j != k) term /= (xn[k] - xn[j]);
+            beta += term;
+        }
+        const double diff = pt - xn[k];
+        if (diff == 0.0) hit = k;
+        w[k] = diff == 0.0 ? 0.0 : beta / diff;
+        sum += w[k];
+    }
+    for (int k = 0; k < s; ++k) w[k] = hit >= 0 ? (k == hit ? 1.0 : 0.0) : w[k] / sum;
+}
+
+// Stencil entry of a fractional index x (point complement om): base b = clamp(floor(x) -
+// s/2 + 1, 0, L - s) and the s FP64 weights of the solver's scheme.
+__device__ void write_entry(const SolverView& v, unsigned char* base, size_t idx, double x, double om) {
+    const int L = v.L, s = v.s;
     int b = (int)floor(x) - s / 2 + 1;
     b = b < 0 ? 0 : (b > L - s ? L - s : b);
-    const double u = x - b;
     unsigned char* e = base + idx * (size_t)(8 + 8 * s);
     reinterpret_cast<int*>(e)[0] = b;
     reinterpret_cast<int*>(e)[1] = 0;
-    for (int k = 0; k < s; ++k) {
-        double w = 1.0;
-        for (int m = 0; m < s; ++m)
-            if (m != k) w *= (u - m) / (double)(k - m);
-        reinterpret_cast<double*>(e + 8)[k] = w;
-    }
+    stencil_weights(v, b, x, om, reinterpret_cast<double*>(e + 8));
 }
 
 __global__ void k_tables(SolverView v, double* x1, double* x2, double* x3, uint32_t* p1, uint32_t* p2,
@@ -139,9 +177,9 @@ __global__ void k_tables(SolverView v, double* x1, double* x2, double* x3, uint3
             q3[idx] = df_from_d(c);
         }
         if (v.wt1) {
-            write_entry((unsigned char*)v.wt1, idx, a, v.L, v.s);
-            write_entry((unsigned char*)v.wt2, idx, b, v.L, v.s);
-            write_entry((unsigned char*)v.wt3, idx, c, v.L, v.s);
+            write_entry(v, (unsigned char*)v.wt1, idx, a, oph1);
+            write_entry(v, (unsigned char*)v.wt2, idx, b, oph2);
+            write_entry(v, (unsigned char*)v.wt3, idx, c, ops);
         }
         if (p1) {
             const double sc = (double)(1u << FIX_FRAC_BITS);
@@ -697,14 +735,8 @@ __global__ void k_lookup(SolverView v, int nq, const double* tq, const double* t
     const double x = frac_index_dev(v, th, om);
     int b = (int)floor(x) - s / 2 + 1;
     b = b < 0 ? 0 : (b > L - s ? L - s : b);
-    const double u = x - b;
     double w[16];
-    for (int k = 0; k < s; ++k) {
-        double p = 1.0;
-        for (int m = 0; m < s; ++m)
-            if (m != k) p *= (u - m) / (double)(k - m);
-        w[k] = p;
-    }
+    stencil_weights(v, b, x, om, w);
     const dbl4* H = v.hist[act];
     const double* ht = v.ht[act];
     auto val = [&](int sl, bool deriv) {
