@@ -77,7 +77,7 @@ def parse():
                     help="only launch the history-integral kernel (for profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="step",
-                    choices=["step", "batch", "serve", "solve", "aging", "capacity"],
+                    choices=["step", "batch", "serve", "solve", "aging", "capacity", "quench"],
                     help="step: the headline configuration; batch: 256 independent solves stepped "
                          "together; serve: Poisson-arrival requests with continuous batching")
     ap.add_argument("--window", type=float, default=30.0, help="seconds of batched or served work")
@@ -364,9 +364,11 @@ def run_pure3_quench():
     warm.close()
     torch.cuda.synchronize()
     sv = Solver({3: 0.5}, 0.8, 129, 100.0, history_cap=129)
+    torch.cuda.nvtx.range_push("quench")
     t0 = time.perf_counter()
     rc = sv.integrate(100.0, TOL)
     wall = time.perf_counter() - t0
+    torch.cuda.nvtx.range_pop()
     st = sv.stats()
     sv.close()
     steps = st["steps_accepted"] + st["steps_rejected"]
@@ -711,6 +713,12 @@ def main():
         return
     if args.workload == "capacity":
         print(json.dumps(run_capacity(args)))
+        return
+    if args.workload == "quench":
+        q = run_pure3_quench()
+        print(json.dumps({"metric": "RK steps/s", "value": q["rk_steps_per_s"], "unit": "RK steps/s", "n_gpus": 1,
+                          "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": q["workload"]}, "quench": q}))
         return
     import torch
     if world > 1:

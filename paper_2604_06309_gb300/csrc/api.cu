@@ -802,6 +802,7 @@ int dmfe_autotune(dmfe_solver* h, int* chunk_out) {
         cudaEventDestroy(e1);
         if (rc) {
             v.hi_chunk = saved;
+            hi_config(v, &h->hi_grid, &h->hi_smem);
             return rc;
         }
         std::lock_guard<std::mutex> lock(g_tune_mutex);

@@ -124,6 +124,7 @@ struct SolverView {
     int sparsify;         // 1: pass when the store is full
     double rk_switch_dt;  // controller step of the switch to SSPRK(10,4) (+inf: never)
     int interp, fh_d;     // theta-stencil scheme (DMFE_INTERP_*) and Floater-Hormann degree
+    int hi_threads;       // block size of a single solve's history-integral launch
     double T, beta0;
     double gamma, ga, gD, alpha, delta;  // grid: gamma, atan(e^-gamma), atan(e^gamma) - atan(e^-gamma)
     Poly poly;
@@ -199,7 +200,9 @@ int launch_tables(const SolverView& v, cudaStream_t s);
 // device memory (integrate loop) and gates on the status word; otherwise uses t.
 int launch_history_integrals(const SolverView& v, const double* row_dev, double t, int stage,
                              double* S_dev, int grid_ctas, cudaStream_t s);
-int hi_config(const SolverView& v, int* grid_ctas, size_t* smem);
+// grid and block size (stored in v.hi_threads) of a single solve's history-integral launch
+int hi_config(SolverView& v, int* grid_ctas, size_t* smem);
+int hi_launch_shape(long long units, int nsm, int max_warps, int* warps);
 int launch_assemble(const SolverView& v, const double* row_dev, const double* S_dev, double t,
                     double* dC, double* dR, double* muE, cudaStream_t s);
 // one trial step: head = begin + stages 1..kDP5Stages, tail = the later stages (SSPRK),
@@ -220,7 +223,7 @@ int launch_stage_prep(const SolverView& v, const double* row_dev, double t, int 
 // double-float path (kernels_df.cu)
 int launch_history_integrals_df(const SolverView& v, const double* row_dev, double t, int stage,
                                 double* S_dev, int grid_ctas, cudaStream_t s);
-int hi_config_df(const SolverView& v, int* grid_ctas, size_t* smem);
+int hi_config_df(SolverView& v, int* grid_ctas, size_t* smem);
 
 // ---- batched execution (batch.cu and the kernel files) ----
 int batch_hi_config(int precision, int sw, int max_L, int max_cap, int* grid_ctas, size_t* smem);

@@ -231,7 +231,7 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
     const int d1 = v.poly.deg1, d2 = v.poly.deg2;
 
     const int chunk = v.hi_chunk;
-    for (int u_ = ub + (threadIdx.x >> 5); u_ < ue; u_ += DF_WARPS) {
+    for (int u_ = ub + (threadIdx.x >> 5); u_ < ue; u_ += (int)(blockDim.x >> 5)) {
         int j, i0, i1;
         hi_unit_range(u_, L, chunk, &j, &i0, &i1);
         // ---- per unit: B1 time weights prepared once per stage
@@ -476,7 +476,7 @@ int launch_stage_prep(const SolverView& v, const double* row_dev, double t, int 
     return DMFE_OK;
 }
 
-int hi_config_df(const SolverView& v, int* grid_ctas, size_t* smem) {
+int hi_config_df(SolverView& v, int* grid_ctas, size_t* smem) {
     void* fn = df_kernel_for(v.s);
     if (!fn) return DMFE_ERR_UNSUPPORTED;
     if (v.L > 65535) return DMFE_ERR_UNSUPPORTED;
@@ -487,12 +487,14 @@ int hi_config_df(const SolverView& v, int* grid_ctas, size_t* smem) {
     DMFE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     if (sm > (size_t)max_optin) return DMFE_ERR_UNSUPPORTED;
     DMFE_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int warps = 0;
+    const int want = hi_launch_shape((long long)hi_parts(v.L, v.hi_chunk) * v.L, nsm, DF_WARPS, &warps);
     int per_sm = 0;
-    DMFE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, DF_THREADS, sm));
+    DMFE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, sm));
     if (per_sm < 1) return DMFE_ERR_UNSUPPORTED;
-    const int want = (hi_parts(v.L, v.hi_chunk) * v.L + DF_WARPS - 1) / DF_WARPS;
     const int cap = nsm * per_sm;
     *grid_ctas = want < cap ? want : cap;
+    v.hi_threads = warps * 32;
     *smem = sm;
     return DMFE_OK;
 }
@@ -506,7 +508,8 @@ int launch_history_integrals_df(const SolverView& v, const double* row_dev, doub
     if (rc) return rc;
     const size_t sm = df_smem_bytes(v);
     void* args[] = {(void*)&v, (void*)&t, (void*)&fs, (void*)&S_dev};
-    DMFE_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid_ctas), dim3(DF_THREADS), args, sm, s));
+    DMFE_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid_ctas), dim3(v.hi_threads > 0 ? v.hi_threads : DF_THREADS), args,
+                                   sm, s));
     return DMFE_OK;
 }
 

@@ -165,7 +165,7 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
     const double* __restrict__ nu = v.nu;
     const int chunk = v.hi_chunk;
 
-    for (int u = ub + (threadIdx.x >> 5); u < ue; u += HI_WARPS) {
+    for (int u = ub + (threadIdx.x >> 5); u < ue; u += (int)(blockDim.x >> 5)) {
         int j, i0, i1;
         hi_unit_range(u, L, chunk, &j, &i0, &i1);
         const double thj = theta[j], omj = omega[j];
@@ -368,7 +368,7 @@ __device__ __forceinline__ void hi_f32_body(const SolverView& v, const double* _
     const float fscale = 1.0f / (float)(1u << FIX_FRAC_BITS);
     const int chunk = v.hi_chunk;
 
-    for (int u = ub + (threadIdx.x >> 5); u < ue; u += HI_WARPS) {
+    for (int u = ub + (threadIdx.x >> 5); u < ue; u += (int)(blockDim.x >> 5)) {
         int j, i0, i1;
         hi_unit_range(u, L, chunk, &j, &i0, &i1);
         const float omj = om32[j];
@@ -560,7 +560,17 @@ void* hi_kernel_for(const SolverView& v) {
 
 }  // namespace
 
-int hi_config(const SolverView& v, int* grid_ctas, size_t* smem) {
+// Block size and grid of a single solve's history-integral launch: enough warps per CTA
+// that the units of one stage cover every SM once (at least 4 and at most 16 warps), and
+// at most the CTAs that can be resident (the kernel is persistent over its unit blocks).
+int hi_launch_shape(long long units, int nsm, int max_warps, int* warps) {
+    long long w = (units + nsm - 1) / nsm;
+    w = w < 4 ? 4 : (w > max_warps ? max_warps : w);
+    *warps = (int)w;
+    return (int)((units + w - 1) / w);
+}
+
+int hi_config(SolverView& v, int* grid_ctas, size_t* smem) {
     if (v.precision == DMFE_DOUBLE_FLOAT) return hi_config_df(v, grid_ctas, smem);
     void* fn = hi_kernel_for(v);
     if (!fn) return DMFE_ERR_UNSUPPORTED;
@@ -572,12 +582,14 @@ int hi_config(const SolverView& v, int* grid_ctas, size_t* smem) {
     DMFE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     if (sm > (size_t)max_optin) return DMFE_ERR_UNSUPPORTED;
     DMFE_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int warps = 0;
+    const int want = hi_launch_shape((long long)hi_parts(v.L, v.hi_chunk) * v.L, nsm, HI_WARPS, &warps);
     int per_sm = 0;
-    DMFE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, HI_THREADS, sm));
+    DMFE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, sm));
     if (per_sm < 1) return DMFE_ERR_UNSUPPORTED;
-    int want = (hi_parts(v.L, v.hi_chunk) * v.L + HI_WARPS - 1) / HI_WARPS;
-    int cap = nsm * per_sm;
+    const int cap = nsm * per_sm;
     *grid_ctas = want < cap ? want : cap;
+    v.hi_threads = warps * 32;
     *smem = sm;
     return DMFE_OK;
 }
@@ -593,7 +605,8 @@ int launch_history_integrals(const SolverView& v, const double* row_dev, double 
     size_t sm = hi_smem_bytes(v);
     int fs = stage;
     void* args[] = {(void*)&v, (void*)&row_dev, (void*)&t, (void*)&fs, (void*)&S_dev};
-    DMFE_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid_ctas), dim3(HI_THREADS), args, sm, s));
+    DMFE_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid_ctas), dim3(v.hi_threads > 0 ? v.hi_threads : HI_THREADS), args,
+                                   sm, s));
     return DMFE_OK;
 }
 
