@@ -674,8 +674,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     cfg = {"workload": "mixed (3+4)-spin T=0.5 quench, theta grid L=%d (t_max 1e5), %d-slice store, s=4"
                        % (args.L, args.L),
-           "model": "spherical mixed p-spin DMFE, f=(q^3+q^4)/4", "global_batch": world, "seq_len": args.L,
-           "parallelism": "replicas x%d" % world, "l2": "flushed before every timed step (256 MB write)"}
+           "f": "(q^3+q^4)/4", "T": T_BATH, "L": args.L, "history_cap": args.L, "s": 4, "tol": TOL,
+           "replicas": world, "l2": "flushed before every timed step (256 MB write)"}
     if args.impl == "reference":
         if rank != 0:
             return
