@@ -89,6 +89,7 @@ def parse():
     ap.add_argument("--checkpoints", default="1e2,1e3,1e4,1e5", help="solve: times at which to record")
     ap.add_argument("--compare", default="", help="solve: further precisions compared with --precision")
     ap.add_argument("--time-limit", type=float, default=900.0, help="solve: wall seconds per precision")
+    ap.add_argument("--serve-tmax", default="10,100", help="serve: t_max range of the requests (log-uniform)")
     ap.add_argument("--coefs", default="3:0.5", help="aging: f(q) as power:coefficient,...")
     ap.add_argument("--T", type=float, default=0.0, help="aging: bath temperature")
     ap.add_argument("--tol", type=float, default=1e-12, help="aging: RK tolerance")
@@ -614,9 +615,11 @@ SERVE_LS = (65, 129, 257)
 
 
 def run_serving(args, rate=20.0, seed=20260406):
-    """Config 5 scaled so that a few-minute run reaches a steady state: Poisson arrivals of
-    (3+4)-spin requests (T~U[0.3,1], lambda~U[0,1], L~U{65,129,257}, t_max~logU[10,100]),
-    admitted by device footprint into a continuously stepped batch."""
+    """Poisson arrivals of (3+4)-spin requests (T~U[0.3,1], lambda~U[0,1], L~U{65,129,257},
+    t_max log-uniform in --serve-tmax), admitted by device footprint into a continuously
+    stepped batch. The default t_max range [10, 100] reaches a steady state within a
+    minute; the configuration's own range [1e3, 1e7] does not (the queue grows), and its
+    run reports admissions, completions and the queue over the window."""
     import torch
     from paper_2604_06309_gb300 import Server, footprint
     rng = np.random.default_rng(seed)
@@ -624,7 +627,8 @@ def run_serving(args, rate=20.0, seed=20260406):
     budget = int(0.5 * free)
     srv = Server(args.slots, max(SERVE_LS), max(SERVE_LS), precision=args.precision, hbm_budget=budget,
                  steps_per_round=4)
-    reqs = batch_requests(100000, seed=seed + 1, Ls=SERVE_LS, tmax_range=(10.0, 100.0))
+    tr = tuple(float(x) for x in args.serve_tmax.split(","))
+    reqs = batch_requests(100000, seed=seed + 1, Ls=SERVE_LS, tmax_range=tr)
     t0 = time.perf_counter()
     next_arrival = rng.exponential(1.0 / rate)
     submitted, results, peak_bytes, samples = 0, [], 0, []
@@ -654,8 +658,8 @@ def run_serving(args, rate=20.0, seed=20260406):
     return {"metric": "served solves/s", "value": len(ok) / args.window, "unit": "solves/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": DTYPES[args.precision], "data": "synthetic",
             "config": {"workload": "Poisson arrivals %.0f req/s of (3+4)-spin solves, T~U[0.3,1], lambda~U[0,1], "
-                                   "L=cap~U{%s}, t_max~logU[10,100], tol 1e-8, seed %d, continuous batching"
-                                   % (rate, ",".join(map(str, SERVE_LS)), seed),
+                                   "L=cap~U{%s}, t_max~logU[%g,%g], tol 1e-8, seed %d, continuous batching"
+                                   % (rate, ",".join(map(str, SERVE_LS)), tr[0], tr[1], seed),
                        "window_s": args.window, "max_slots": args.slots, "hbm_budget_bytes": budget},
             "serve": {"submitted": submitted, "completed": len(ok), "failed": st["failed"],
                       "queued_at_end": st["queued"], "running_at_end": st["running"],
@@ -664,7 +668,10 @@ def run_serving(args, rate=20.0, seed=20260406):
                       "solves_per_s_second_half": len(second_half) / (args.window / 2),
                       "mean_running": float(np.mean([x[1] for x in samples])) if samples else 0.0,
                       "peak_hbm_bytes": peak_bytes, "hbm_utilisation_of_total": peak_bytes / total,
-                      "batched_steps": st["batched_steps"]},
+                      "batched_steps": st["batched_steps"], "admitted": st["admitted"],
+                      "queue_over_time": [(round(x[0], 1), x[1], x[2]) for x in
+                                          samples[::max(1, len(samples) // 10)]],
+                      "completed_t_max_max": max((r["t_final"] for r in ok), default=0.0)},
             "clocks": clk}
 
 
