@@ -61,6 +61,7 @@ __device__ __forceinline__ void stage_prep_body(const SolverView& v, const doubl
             if (ext && tau > tl) {
                 const double s = tau - tl, qq = s / hx;
                 d.a0 = n - 1; d.a1 = -1;
+                d.s = qq;
                 d.w[0] = 1.0 - qq * qq; d.w[1] = s - s * qq; d.w[2] = qq * qq; d.w[3] = 0.0;
             } else if (n == 1) {
                 d.a0 = 0; d.a1 = 0;
@@ -78,6 +79,15 @@ __device__ __forceinline__ void stage_prep_body(const SolverView& v, const doubl
 #pragma unroll
             for (int k = 0; k < 4; ++k) d.wd[k] = df_from_d(d.w[k]);
             v.b1[q] = d;
+            if (v.hcoef[act] && ext) {
+                // FP64 path: the quadratic extension through the last slice and this stage
+                // row as a virtual interval n-1 = [t_last, t] in monomial form (c3 = 0)
+                const dbl4 e = v.hist[act][(size_t)(n - 1) * L + q];
+                dbl8 c;
+                c.c0 = e.x; c.c1 = hx * e.y; c.c2 = Cq - e.x - hx * e.y; c.c3 = 0.0;
+                c.r0 = e.z; c.r1 = hx * e.w; c.r2 = Rq - e.z - hx * e.w; c.r3 = 0.0;
+                v.hcoef[act][(size_t)(n - 1) * L + q] = c;
+            }
             if (v.rowdf) {
                 const double C = row[q], R = row[L + q];
                 v.rowdf[q] = dfrow{df_from_d(fp2(v.poly, C) * R), df_from_d(fp1(v.poly, C)), df_from_d(C), df_from_d(R)};

@@ -68,55 +68,10 @@ struct TimeW {
     double w0, w1, w2, w3;
 };
 
-// Time weights of the B2 lookup of one pair. Slice times are non-negative, so their
-// IEEE bit patterns order like the values: the slice walk compares 64-bit integers
-// (integer pipe) instead of doubles (the FP64 pipe, GB300's bottleneck here); sinv holds
-// the reciprocal slice widths. The cubic Hermite basis uses h00 = 1 - h01 and
-// h10 = s (1-s)^2 h, h11 = -(s (1-s) h) s.
+// Slice times are non-negative, so their IEEE bit patterns order like the values: the slice
+// walk compares 64-bit integers (integer pipe) instead of doubles (the FP64 pipe, GB300's
+// bottleneck here).
 __device__ __forceinline__ long long tbits(double x) { return __double_as_longlong(x); }
-
-__device__ __forceinline__ TimeW time_weights_f64(const double* sht,
-                                                  const double* sinv, int n, bool ext, long long tlb,
-                                                  double tl, double inv_hx, double tau, int hint) {
-    TimeW r;
-    const long long taub = __double_as_longlong(tau);
-    if (ext && taub > tlb) {
-        const double s = tau - tl, q = s * inv_hx;
-        r.a0 = n - 1; r.a1 = -1;
-        r.w2 = q * q;
-        r.w0 = 1.0 - r.w2;
-        r.w1 = s - s * q;
-        r.w3 = 0.0;
-    } else if (n == 1) {
-        r.a0 = 0; r.a1 = 0;
-        r.w0 = 1.0; r.w1 = 0.0; r.w2 = 0.0; r.w3 = 0.0;
-    } else {
-        int k = hint;
-        while (k < n - 2 && tbits(sht[k + 1]) <= taub) ++k;
-        while (k > 0 && tbits(sht[k]) > taub) --k;
-        const double hh = sht[k + 1] - sht[k];
-        const double sg = (tau - sht[k]) * sinv[k];
-        const double om = 1.0 - sg;
-        const double p = sg * om * hh;
-        r.a0 = k; r.a1 = k + 1;
-        r.w2 = sg * sg * (3.0 - 2.0 * sg);
-        r.w0 = 1.0 - r.w2;
-        r.w1 = p * om;
-        r.w3 = -p * sg;
-    }
-    return r;
-}
-
-// Largest k <= n-2 with sht[k] <= tau (0 when n == 1).
-__device__ __forceinline__ int find_slice(const double* sht, int n, double tau) {
-    if (n <= 2) return 0;
-    int lo = 0, hi = n - 2;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (sht[mid] <= tau) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -140,25 +95,29 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
     const dbl4* __restrict__ H = v.hist[act];
     const dbl8* __restrict__ HC = v.hcoef[act];
     const double* __restrict__ ht = v.ht[act];
+    // Slice times with the stage time appended when the stage lies beyond the last slice:
+    // the quadratic extension is then the virtual interval n-1 = [t_last, t], whose
+    // monomial coefficients the prep kernel wrote into row n-1 of HC, and every pair takes
+    // the same Horner path (no divergence near theta = 1).
+    const double tl = ht[n - 1];
+    const bool ext = t > tl;
+    const double hx = t - tl;
     dbl4* srow = reinterpret_cast<dbl4*>(smraw);            // [L] {K, D, C, R}
-    double* sht = reinterpret_cast<double*>(srow + L);              // [cap] slice times
-    double* sinvh = sht + v.cap;                                    // [cap] 1/(t_{k+1} - t_k)
-    int* scell = reinterpret_cast<int*>(sinvh + v.cap);             // [L]
+    double* sht = reinterpret_cast<double*>(srow + L);              // [cap + 1] slice times
+    double* sinvh = sht + v.cap + 1;                                // [cap + 1] 1/(t_{k+1} - t_k)
+    int* scell = reinterpret_cast<int*>(sinvh + v.cap + 1);         // [L]
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         double C = row[i], R = row[L + i];
         srow[i] = dbl4{fp2(v.poly, C) * R, fp1(v.poly, C), C, R};
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         sht[i] = ht[i];
-        sinvh[i] = i + 1 < n ? 1.0 / (ht[i + 1] - ht[i]) : 0.0;
+        sinvh[i] = i + 1 < n ? 1.0 / (ht[i + 1] - ht[i]) : (ext ? 1.0 / hx : 0.0);
     }
+    if (threadIdx.x == 0) sht[n] = t;
     for (int m = threadIdx.x; m < L; m += blockDim.x) scell[m] = v.cell[m];
     __syncthreads();
-    const double tl = sht[n - 1];
-    const long long tlb = tbits(tl);
-    const bool ext = t > tl;
-    const double hx = t - tl;
-    const double inv_hx = ext ? 1.0 / hx : 0.0;
+    const int kmax = ext ? n - 1 : n - 2;  // last interval a B2 point can fall in
     const int lane = threadIdx.x & 31;
     const double* __restrict__ theta = v.theta;
     const double* __restrict__ omega = v.omega;
@@ -177,7 +136,9 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
             b1.w0 = d.w[0]; b1.w1 = d.w[1]; b1.w2 = d.w[2]; b1.w3 = d.w[3];
             s1 = d.s;
         }
-        const bool b1_interior = b1.a1 == b1.a0 + 1;  // else: the extension or a single slice
+        // an interval of the history or the virtual extension interval (a1 < 0); else a
+        // single stored slice at the stage time t = 0
+        const bool b1_interior = b1.a1 == b1.a0 + 1 || b1.a1 < 0;
         constexpr size_t WTS = 8 + 8 * SW;  // bytes per stencil entry
         const unsigned char* __restrict__ w1r = v.wt1 + (size_t)j * L * WTS;
         const unsigned char* __restrict__ w2r = v.wt2 + (size_t)j * L * WTS;
@@ -248,45 +209,35 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
                 double w[SW];
 #pragma unroll
                 for (int k = 0; k < SW; ++k) w[k] = reinterpret_cast<const double*>(e + 8)[k];
-                if (n > 1 && !(ext && taub > tlb)) {
-                    // inside the stored history: the slice interval by a short walk from the
-                    // cell hint, theta stencil of its monomial coefficients, Horner in s
+                if (kmax >= 0) {
+                    // the slice interval (or the virtual extension interval) by a short walk
+                    // from the cell hint; each stencil node's interpolant by Horner's rule
+                    // in s (6 FMAs), then the theta stencil (2 FMAs)
                     int cell = base2 + SW / 2 - 1;  // the grid cell of phi2 (the walk corrects)
                     cell = cell < 0 ? 0 : (cell > L - 1 ? L - 1 : cell);
                     int k = scell[cell];
-                    while (k < n - 2 && tbits(sht[k + 1]) <= taub) ++k;
+                    while (k < kmax && tbits(sht[k + 1]) <= taub) ++k;
                     while (k > 0 && tbits(sht[k]) > taub) --k;
                     const double sg = (tau2 - sht[k]) * sinvh[k];
                     const dbl8* __restrict__ P = HC + (size_t)k * L + b;
-                    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+                    CB2 = 0.0;
+                    RB2 = 0.0;
 #pragma unroll
                     for (int m = 0; m < SW; ++m) {
                         const dbl8 c = P[m];
-                        a0 += w[m] * c.c0; a1 += w[m] * c.c1; a2 += w[m] * c.c2; a3 += w[m] * c.c3;
-                        q0 += w[m] * c.r0; q1 += w[m] * c.r1; q2 += w[m] * c.r2; q3 += w[m] * c.r3;
+                        CB2 += w[m] * (c.c0 + sg * (c.c1 + sg * (c.c2 + sg * c.c3)));
+                        RB2 += w[m] * (c.r0 + sg * (c.r1 + sg * (c.r2 + sg * c.r3)));
                     }
-                    CB2 = a0 + sg * (a1 + sg * (a2 + sg * a3));
-                    RB2 = q0 + sg * (q1 + sg * (q2 + sg * q3));
                 } else {
-                    // beyond the last slice (quadratic extension with the stage row) or a
-                    // single stored slice
-                    const TimeW b2 = time_weights_f64(sht, sinvh, n, ext, tlb, tl, inv_hx, tau2, 0);
-                    double c0 = 0, dc0 = 0, r0 = 0, dr0 = 0, c1 = 0, r1 = 0;
-                    const dbl4* __restrict__ s0 = H + (size_t)b2.a0 * L + b;
+                    // a single stored slice and the stage at its time
+                    CB2 = 0.0;
+                    RB2 = 0.0;
 #pragma unroll
                     for (int m = 0; m < SW; ++m) {
-                        dbl4 q = s0[m];
-                        c0 += w[m] * q.x; dc0 += w[m] * q.y; r0 += w[m] * q.z; dr0 += w[m] * q.w;
+                        const dbl4 q = H[b + m];
+                        CB2 += w[m] * q.x;
+                        RB2 += w[m] * q.z;
                     }
-                    if (b2.a1 < 0) {
-#pragma unroll
-                        for (int m = 0; m < SW; ++m) {
-                            dbl4 q = srow[b + m];
-                            c1 += w[m] * q.z; r1 += w[m] * q.w;
-                        }
-                    }
-                    CB2 = b2.w0 * c0 + b2.w1 * dc0 + b2.w2 * c1;
-                    RB2 = b2.w0 * r0 + b2.w1 * dr0 + b2.w2 * r1;
                 }
             }
             const double f1a = fp1(v.poly, CB1), f2a = fp2(v.poly, CB1);
@@ -538,7 +489,7 @@ __global__ void __launch_bounds__(HI_THREADS, 1) k_batch_hi(const BatchTable* __
 
 size_t hi_smem_bytes(const SolverView& v) {
     if (v.precision == DMFE_FP64)
-        return (size_t)v.L * sizeof(dbl4) + (size_t)v.cap * 2 * sizeof(double) + (size_t)v.L * sizeof(int);
+        return (size_t)v.L * sizeof(dbl4) + (size_t)(v.cap + 1) * 2 * sizeof(double) + (size_t)v.L * sizeof(int);
     return (size_t)v.L * sizeof(float4) + (size_t)v.cap * (sizeof(double) + 3 * sizeof(float)) +
            (size_t)v.L * sizeof(int);
 }
