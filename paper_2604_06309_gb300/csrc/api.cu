@@ -221,7 +221,8 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
         TRY(dev_alloc(h, &p, L * sizeof(df))); v.omega_df = (df*)p;
         TRY(dev_alloc(h, &p, L * sizeof(df))); v.nu_df = (df*)p;
         TRY(dev_alloc(h, &p, L * sizeof(dfrow))); v.rowdf = (dfrow*)p;
-        TRY(dev_alloc(h, &p, cap * sizeof(dfslice))); v.slicedf = (dfslice*)p;
+        TRY(dev_alloc(h, &p, (cap + 1) * sizeof(dfslice))); v.slicedf = (dfslice*)p;
+        TRY(dev_alloc(h, &p, L * sizeof(df8))); v.vrowdf = (df8*)p;
         TRY(dev_alloc(h, &p, L * sizeof(int))); v.cell = (int*)p;
     }
     for (int b = 0; b < 2; ++b) {
@@ -411,7 +412,8 @@ unsigned long long dmfe_footprint(const dmfe_params* pin) {
         for (int k = 0; k < 3; ++k) add(LL * 4);
     } else {
         for (int k = 0; k < 3; ++k) add(LL * sizeof(df));
-        add(L * sizeof(df)); add(L * sizeof(df)); add(L * sizeof(dfrow)); add(cap * sizeof(dfslice)); add(L * 4);
+        add(L * sizeof(df)); add(L * sizeof(df)); add(L * sizeof(dfrow)); add((cap + 1) * sizeof(dfslice));
+        add(L * sizeof(df8)); add(L * 4);
     }
     for (int b = 0; b < 2; ++b) {
         add(cap * 8);

@@ -153,7 +153,8 @@ struct SolverView {
     const df* omega_df;   // [L]
     const df* nu_df;      // [L]
     dfrow* rowdf;         // [L] stage row prepared for the double-float kernel
-    dfslice* slicedf;     // [cap]
+    dfslice* slicedf;     // [cap + 1] (entry n: the stage time, for a stage beyond the last slice)
+    df8* vrowdf;          // [L] double-float path: virtual slice at the stage time (see prep)
     int* cell;            // [L] slice of time theta_m t
     B1Desc* b1;           // [L] per-stage B1 time weights
     int hi_chunk;         // summation indices per work unit

@@ -43,7 +43,7 @@ __device__ __forceinline__ void stage_prep_body(const SolverView& v, const doubl
     const double tl = ht[n - 1];
     const bool ext = t > tl;
     const double hx = t - tl;
-    const int tot = L > n ? L : n;
+    const int tot = L > n + 1 ? L : n + 1;
     __shared__ double red_m[kPrepThreads], red_e[kPrepThreads];
     double pm = 0.0, pe = 0.0;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += gridDim.x * blockDim.x) {
@@ -91,14 +91,24 @@ __device__ __forceinline__ void stage_prep_body(const SolverView& v, const doubl
             if (v.rowdf) {
                 const double C = row[q], R = row[L + q];
                 v.rowdf[q] = dfrow{df_from_d(fp2(v.poly, C) * R), df_from_d(fp1(v.poly, C)), df_from_d(C), df_from_d(R)};
+                if (ext) {
+                    // double-float path: the quadratic extension through the last slice and
+                    // this stage row equals the cubic Hermite interpolant to a virtual slice
+                    // (t, Y, 2 (Y - y_last) / hx - y'_last); the kernel reads it as slice n
+                    const dbl4 e = v.hist[act][(size_t)(n - 1) * L + q];
+                    const double dCv = 2.0 * (C - e.x) / hx - e.y, dRv = 2.0 * (R - e.z) / hx - e.w;
+                    v.vrowdf[q] = df8{df_from_d(C), df_from_d(dCv), df_from_d(R), df_from_d(dRv)};
+                }
             }
         }
-        if (q < n && v.slicedf) {
-            const double tk = ht[q];
+        if (q <= n && v.slicedf) {
+            // slice q (q = n: the stage time itself, the virtual slice of an extension)
+            const double tk = q < n ? ht[q] : t;
+            const double tn = q + 1 < n ? ht[q + 1] : t;
             dfslice e;
             e.v = df_from_d((t - tk) / t);
-            if (q + 1 < n) {
-                const double w = ht[q + 1] - tk;
+            if (q + 1 < n || (q + 1 == n && ext)) {
+                const double w = tn - tk;
                 e.inv = df_from_d(t / w);
                 e.h = (float)w;
             } else {
@@ -209,28 +219,30 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
     const double t = from_state ? st->t_stage : t_arg;
     const df8* __restrict__ H = v.histdf[act];
     const double* __restrict__ ht = v.ht[act];
+    const double tl = ht[n - 1];
+    const bool ext = t > tl;
+    // slices, and for a stage beyond the last slice the virtual slice n at the stage time
+    // (the prep kernel's quadratic extension in Hermite form): all pairs take one path
+    const int nsl = ext ? n + 1 : n;
+    const int kmax = nsl - 2;
     dfrow* srow = reinterpret_cast<dfrow*>(smraw);                   // [L]
-    df* sv = reinterpret_cast<df*>(srow + L);                         // [cap] v_k
-    df* sinv = sv + v.cap;                                            // [cap] t/(t_{k+1} - t_k)
-    float* sh = reinterpret_cast<float*>(sinv + v.cap);               // [cap] t_{k+1} - t_k
-    uint16_t* scell = reinterpret_cast<uint16_t*>(sh + v.cap);        // [L]
+    df* sv = reinterpret_cast<df*>(srow + L);                         // [cap + 1] v_k
+    df* sinv = sv + v.cap + 1;                                        // [cap + 1] t/(t_{k+1} - t_k)
+    float* sh = reinterpret_cast<float*>(sinv + v.cap + 1);           // [cap + 1] t_{k+1} - t_k
+    uint16_t* scell = reinterpret_cast<uint16_t*>(sh + v.cap + 1);    // [L]
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         srow[i] = v.rowdf[i];
         scell[i] = (uint16_t)v.cell[i];
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = threadIdx.x; i < nsl; i += blockDim.x) {
         const dfslice e = v.slicedf[i];
         sv[i] = e.v;
         sinv[i] = e.inv;
         sh[i] = e.h;
     }
     __syncthreads();
-    const double tl = ht[n - 1];
-    const bool ext = t > tl;
-    const double hx = t - tl;
-    const df vlast = sv[n - 1];
-    const df inv_vlast = df_from_d(ext ? t / hx : 0.0);
-    const df hx_df = df_from_d(hx);
+    const df8* __restrict__ VR = v.vrowdf;
+    const df hx_df = df_from_d(t - tl);
     const int lane = threadIdx.x & 31;
     const df* __restrict__ omdf = v.omega_df;
     const df* __restrict__ nudf = v.nu_df;
@@ -325,30 +337,32 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
                 const df u = df_mul(omj, omdf[i]);  // 1 - phi2 = omega_j omega_i
                 int s0, s1;
                 df tw0, tw1, tw2, tw3;
-                if (ext && df_lt(u, vlast)) {
-                    const df q = df_mul(df_sub(vlast, u), inv_vlast);
-                    const df q2 = df_mul(q, q);
-                    s0 = n - 1; s1 = -1;
-                    tw0 = df_add_f(df_neg(q2), 1.f);
-                    tw1 = df_mul(hx_df, df_sub(q, q2));
-                    tw2 = q2;
-                    tw3 = df{0.f, 0.f};
-                } else if (n == 1) {
-                    s0 = 0; s1 = 0;
+                if (kmax < 0) {
+                    // a single stored slice and the stage at its time
+                    s0 = 0; s1 = -1;
                     tw0 = df{1.f, 0.f}; tw1 = df{0.f, 0.f}; tw2 = df{0.f, 0.f}; tw3 = df{0.f, 0.f};
                 } else {
                     int k = scell[(int)floorf(x2.hi) < L ? (int)floorf(x2.hi) : L - 1];
-                    while (k < n - 2 && df_ge(sv[k + 1], u)) ++k;
+                    while (k < kmax && df_ge(sv[k + 1], u)) ++k;
                     while (k > 0 && df_lt(sv[k], u)) --k;
                     const df sg = df_mul(df_sub(sv[k], u), sinv[k]);
-                    const float hh = sh[k];
                     const df om = df_add_f(df_neg(sg), 1.f);
                     const df om2 = df_mul(om, om), sg2 = df_mul(sg, sg);
                     s0 = k; s1 = k + 1;
                     tw0 = df_mul(df_add_f(df_mul_f(sg, 2.f), 1.f), om2);
-                    tw1 = df_mul_f(df_mul(sg, om2), hh);
                     tw2 = df_mul(sg2, df_add_f(df_mul_f(sg, -2.f), 3.f));
-                    tw3 = df_mul_f(df_mul(sg2, df_add_f(sg, -1.f)), hh);
+                    const df a1 = df_mul(sg, om2), a3 = df_mul(sg2, df_add_f(sg, -1.f));
+                    if (k < n - 1) {
+                        // a stored interval: its width in FP32 (the derivative terms are
+                        // O(h) corrections)
+                        tw1 = df_mul_f(a1, sh[k]);
+                        tw3 = df_mul_f(a3, sh[k]);
+                    } else {
+                        // the virtual interval: the width in full double-float, since the
+                        // virtual slice's derivative need not be small
+                        tw1 = df_mul(a1, hx_df);
+                        tw3 = df_mul(a3, hx_df);
+                    }
                 }
                 df w[SW];
                 const int b = stencil_df<SW>(q3r[i], L, w);
@@ -372,7 +386,7 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
                 dacc_add(tc, tw1, dc0);
                 dacc_add(tr, tw1, dr0);
                 if (s1 >= 0) {
-                    const df8* __restrict__ p1 = H + (size_t)s1 * L + b;
+                    const df8* __restrict__ p1 = (s1 < n ? H + (size_t)s1 * L : VR) + b;
                     const df8 e0 = p1[0];
                     dacc ac = dacc_prod(w[0], e0.C), adc = dacc_prod(w[0], e0.dC);
                     dacc ar = dacc_prod(w[0], e0.R), adr = dacc_prod(w[0], e0.dR);
@@ -388,17 +402,6 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
                     dacc_add(tc, tw3, dacc_get(adc));
                     dacc_add(tr, tw2, dacc_get(ar));
                     dacc_add(tr, tw3, dacc_get(adr));
-                } else {
-                    const dfrow e0 = srow[b];
-                    dacc ac = dacc_prod(w[0], e0.C), ar = dacc_prod(w[0], e0.R);
-#pragma unroll
-                    for (int m = 1; m < SW; ++m) {
-                        const dfrow e = srow[b + m];
-                        dacc_add(ac, w[m], e.C);
-                        dacc_add(ar, w[m], e.R);
-                    }
-                    dacc_add(tc, tw2, dacc_get(ac));
-                    dacc_add(tr, tw2, dacc_get(ar));
                 }
                 CB2 = dacc_get(tc);
                 RB2 = dacc_get(tr);
@@ -463,7 +466,7 @@ __global__ void __launch_bounds__(DF_THREADS, 1) k_batch_hi_df(const BatchTable*
 }
 
 size_t df_smem_bytes(const SolverView& v) {
-    return (size_t)v.L * sizeof(dfrow) + (size_t)v.cap * (2 * sizeof(df) + sizeof(float)) +
+    return (size_t)v.L * sizeof(dfrow) + (size_t)(v.cap + 1) * (2 * sizeof(df) + sizeof(float)) +
            (size_t)v.L * sizeof(uint16_t) + 16;
 }
 
