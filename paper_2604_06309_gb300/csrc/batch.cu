@@ -24,6 +24,7 @@ struct dmfe_batch {
     int hi_grid = 0;
     size_t hi_smem = 0;
     DevState* h_state = nullptr;  // pinned, one per slot
+    DevState* d_state = nullptr;  // device copies gathered by one kernel per poll
 };
 
 namespace {
@@ -62,6 +63,17 @@ void rebuild_table(dmfe_batch* b) {
         t.woff[k] = woff;
     }
     b->dirty = true;
+}
+
+// Copy every present slot's device state word block into one array, so that a poll is one
+// launch and one transfer instead of a transfer per slot.
+__global__ void k_gather_states(const BatchTable* __restrict__ bt, DevState* __restrict__ out) {
+    const int k = blockIdx.x;
+    if (k >= bt->count || !bt->active[k]) return;
+    static_assert(sizeof(DevState) % 8 == 0, "state size");
+    const long long* src = reinterpret_cast<const long long*>(bt->views[k].st);
+    long long* dst = reinterpret_cast<long long*>(out + k);
+    for (int q = threadIdx.x; q < (int)(sizeof(DevState) / 8); q += blockDim.x) dst[q] = src[q];
 }
 
 int upload_table(dmfe_batch* b) {
@@ -126,6 +138,7 @@ int dmfe_batch_create(int max_slots, int max_L, int max_cap, int precision, int 
     if (!rc && cudaMallocHost((void**)&b->h_table, sizeof(BatchTable)) != cudaSuccess) rc = DMFE_ERR_OOM;
     if (!rc && cudaMallocHost((void**)&b->h_state, sizeof(DevState) * max_slots) != cudaSuccess) rc = DMFE_ERR_OOM;
     if (!rc && cudaMalloc((void**)&b->d_table, sizeof(BatchTable)) != cudaSuccess) rc = DMFE_ERR_OOM;
+    if (!rc && cudaMalloc((void**)&b->d_state, sizeof(DevState) * max_slots) != cudaSuccess) rc = DMFE_ERR_OOM;
     if (rc) {
         cudaGetLastError();
         dmfe_batch_destroy(b);
@@ -144,6 +157,7 @@ void dmfe_batch_destroy(dmfe_batch* b) {
         if (h) dmfe_destroy(h);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->d_table) cudaFree(b->d_table);
+    if (b->d_state) cudaFree(b->d_state);
     if (b->h_table) cudaFreeHost(b->h_table);
     if (b->h_state) cudaFreeHost(b->h_state);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
@@ -203,10 +217,14 @@ int dmfe_batch_step(dmfe_batch* b, int nsteps) {
 
 int dmfe_batch_poll(dmfe_batch* b, int* status, double* t, int* running) {
     if (!b) return DMFE_ERR_ARG;
-    for (int k = 0; k < b->max_slots; ++k)
-        if (b->slots[k])
-            DMFE_CUDA_TRY(cudaMemcpyAsync(&b->h_state[k], solver_view(b->slots[k]).st, sizeof(DevState),
-                                          cudaMemcpyDeviceToHost, b->stream));
+    TRYB(upload_table(b));
+    const int count = b->h_table->count;
+    if (count > 0) {
+        k_gather_states<<<count, 32, 0, b->stream>>>(b->d_table, b->d_state);
+        DMFE_CUDA_TRY(cudaGetLastError());
+        DMFE_CUDA_TRY(cudaMemcpyAsync(b->h_state, b->d_state, sizeof(DevState) * count, cudaMemcpyDeviceToHost,
+                                      b->stream));
+    }
     DMFE_CUDA_TRY(cudaStreamSynchronize(b->stream));
     int run = 0;
     bool changed = false;
