@@ -147,8 +147,9 @@ int dmfe_tables(dmfe_solver* h, double* x1, double* x2, double* x3);
 
 /* Advance with the adaptive integrator of dmfe_params.integrator to t_max <= grid_t_max
  * with tolerance tol (Secs. 3.1, 3.5, 3.6). Step control, including the switch from
- * Dormand-Prince to SSPRK(10,4), runs on the device; the host polls a status word. Returns DMFE_ERR_STEP_UNDERFLOW, DMFE_ERR_NONFINITE or DMFE_ERR_CAPACITY when
- * the device stops the run; the solver then holds the last accepted slice. */
+ * Dormand-Prince to SSPRK(10,4), runs on the device; the host polls a status word.
+ * Returns DMFE_ERR_STEP_UNDERFLOW, DMFE_ERR_NONFINITE or DMFE_ERR_CAPACITY when the device
+ * stops the run; the solver then holds the last accepted slice. */
 int dmfe_integrate(dmfe_solver* h, double t_max, double tol);
 
 /* Launch exactly nsteps trial steps toward t_max with tolerance tol on the solver's
@@ -231,9 +232,10 @@ int dmfe_sync(dmfe_solver* h);
 
 /* ---- batched and served solves ------------------------------------------------------
  * A batch runs many independent solves (one per slot) with one CUDA graph per
- * Dormand-Prince step: each stage is one persistent history-integral launch over the
- * units of every active slot (the slots may have different L, history caps, f, T and
- * t_max), plus batched control kernels. Slots read a batch table in device memory, so
+ * Runge-Kutta step (slots may be in Dormand-Prince or SSPRK(10,4) steps; the stages beyond
+ * the sixth run only for the latter): each stage is one persistent history-integral launch
+ * over the units of every active slot (the slots may have different L, history caps, f, T,
+ * t_max and integrators), plus batched control kernels. Slots read a batch table in device memory, so
  * slots can be added and removed between steps without re-capturing the graph
  * (continuous batching). A slot's results are bitwise identical to the same solve run
  * alone with the same work-unit size. All slots share the batch's precision and stencil
