@@ -67,3 +67,14 @@ def test_reference_arm_line_on_rank_zero():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["metric"] == "RK steps/s"
+
+
+def test_energy_threshold_of_the_aging_workload():
+    """Sec. 4.3: the generic E_th formula gives -sqrt(2(p-1)/p) for pure models f = q^p/2
+    (p = 3: -sqrt(4/3)) and -1 for the pure 2-spin model."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    for p in (2, 3, 4, 5):
+        assert abs(bench.energy_threshold({p: 0.5}) + np.sqrt(2.0 * (p - 1) / p)) < 1e-15
+    assert abs(bench.energy_threshold({2: 0.5}) + 1.0) < 1e-15
