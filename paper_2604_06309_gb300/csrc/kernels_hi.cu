@@ -34,24 +34,36 @@ namespace {
 constexpr int HI_THREADS = 512;
 constexpr int HI_WARPS = HI_THREADS / 32;
 
-// Lagrange weights on nodes 0..SW-1 at u: w_k = prod_{m != k} (u - m) / (k - m).
-template <int SW, typename R>
-__device__ __forceinline__ void lagrange(R u, R (&w)[SW]) {
-    R pre[SW], suf[SW];
-    pre[0] = R(1);
-#pragma unroll
-    for (int k = 1; k < SW; ++k) pre[k] = pre[k - 1] * (u - R(k - 1));
-    suf[SW - 1] = R(1);
-#pragma unroll
-    for (int k = SW - 2; k >= 0; --k) suf[k] = suf[k + 1] * (u - R(k + 1));
-#pragma unroll
-    for (int k = 0; k < SW; ++k) {
-        // 1 / prod_{m != k} (k - m) = (-1)^{SW-1-k} / (k! (SW-1-k)!)
-        double c = 1.0;
-        for (int m = 0; m < SW; ++m)
-            if (m != k) c /= double(k - m);
-        w[k] = pre[k] * suf[k] * R(c);
+// 1 / prod_{m != k} (k - m) = (-1)^{SW-1-k} / (k! (SW-1-k)!), evaluated by the compiler.
+__host__ __device__ constexpr double lagrange_denom(int k, int sw) {
+    double c = 1.0;
+    for (int m = 0; m < sw; ++m)
+        if (m != k) c /= double(k - m);
+    return c;
+}
+
+template <int SW>
+struct LagrangeDenoms {
+    float v[SW];
+    __host__ __device__ constexpr LagrangeDenoms() : v() {
+        for (int k = 0; k < SW; ++k) v[k] = (float)lagrange_denom(k, SW);
     }
+};
+
+// Lagrange weights on nodes 0..SW-1 at u (FP32): w_k = prod_{m != k} (u - m) / (k - m), the
+// products as prefix and suffix products, the denominators compile-time constants.
+template <int SW>
+__device__ __forceinline__ void lagrange(float u, float (&w)[SW]) {
+    constexpr LagrangeDenoms<SW> den{};
+    float pre[SW], suf[SW];
+    pre[0] = 1.f;
+#pragma unroll
+    for (int k = 1; k < SW; ++k) pre[k] = pre[k - 1] * (u - float(k - 1));
+    suf[SW - 1] = 1.f;
+#pragma unroll
+    for (int k = SW - 2; k >= 0; --k) suf[k] = suf[k + 1] * (u - float(k + 1));
+#pragma unroll
+    for (int k = 0; k < SW; ++k) w[k] = pre[k] * suf[k] * den.v[k];
 }
 
 template <int SW>
