@@ -230,6 +230,7 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
         TRY(dev_alloc(h, &p, (size_t)cap * L * sizeof(dbl4))); v.hist[b] = (dbl4*)p;
         if (v.precision == DMFE_FP32_COMPENSATED) {
             TRY(dev_alloc(h, &p, (size_t)cap * L * sizeof(float4))); v.hist32[b] = (float4*)p;
+            if (b == 0) { TRY(dev_alloc(h, &p, L * sizeof(float4))); v.vrow32 = (float4*)p; }
         }
         if (v.precision == DMFE_DOUBLE_FLOAT) {
             TRY(dev_alloc(h, &p, (size_t)cap * L * sizeof(df8))); v.histdf[b] = (df8*)p;
@@ -419,6 +420,7 @@ unsigned long long dmfe_footprint(const dmfe_params* pin) {
         add(cap * 8);
         add(cap * L * sizeof(dbl4));
         if (p.precision == DMFE_FP32_COMPENSATED) add(cap * L * sizeof(float4));
+        if (p.precision == DMFE_FP32_COMPENSATED && b == 0) add(L * sizeof(float4));
         if (p.precision == DMFE_DOUBLE_FLOAT) add(cap * L * sizeof(df8));
         if (p.precision == DMFE_FP64) add(cap * L * sizeof(dbl8));
     }

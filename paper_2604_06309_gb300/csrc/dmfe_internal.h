@@ -155,6 +155,7 @@ struct SolverView {
     dfrow* rowdf;         // [L] stage row prepared for the double-float kernel
     dfslice* slicedf;     // [cap + 1] (entry n: the stage time, for a stage beyond the last slice)
     df8* vrowdf;          // [L] double-float path: virtual slice at the stage time (see prep)
+    float4* vrow32;       // [L] FP32 path: the same in FP32
     int* cell;            // [L] slice of time theta_m t
     B1Desc* b1;           // [L] per-stage B1 time weights
     int hi_chunk;         // summation indices per work unit

@@ -79,6 +79,12 @@ __device__ __forceinline__ void stage_prep_body(const SolverView& v, const doubl
 #pragma unroll
             for (int k = 0; k < 4; ++k) d.wd[k] = df_from_d(d.w[k]);
             v.b1[q] = d;
+            if (v.vrow32 && ext) {
+                // FP32 path: the extension as a virtual slice, as for double-float below
+                const dbl4 e = v.hist[act][(size_t)(n - 1) * L + q];
+                v.vrow32[q] = make_float4((float)Cq, (float)(2.0 * (Cq - e.x) / hx - e.y), (float)Rq,
+                                          (float)(2.0 * (Rq - e.z) / hx - e.w));
+            }
             if (v.hcoef[act] && ext) {
                 // FP64 path: the quadratic extension through the last slice and this stage
                 // row as a virtual interval n-1 = [t_last, t] in monomial form (c3 = 0)

@@ -298,33 +298,32 @@ __device__ __forceinline__ void hi_f32_body(const SolverView& v, const double* _
     const double t = from_state ? st->t_stage : t_arg;
     const float4* __restrict__ H = v.hist32[act];
     const double* __restrict__ ht = v.ht[act];
+    // slices, and for a stage beyond the last slice the virtual slice n at the stage time
+    // (the prep kernel's quadratic extension in Hermite form): all pairs take one path
+    const bool ext = t > ht[n - 1];
+    const int nsl = ext ? n + 1 : n;
+    const int kmax = nsl - 2;
+    const float4* __restrict__ VR = v.vrow32;
     float4* srow = reinterpret_cast<float4*>(smraw);               // [L] {K, D, C, R}
-    double* sht = reinterpret_cast<double*>(srow + L);              // [cap] slice times
-    float* sv = reinterpret_cast<float*>(sht + v.cap);              // [cap] (t - t_k)/t
-    float* sinv = sv + v.cap;                                       // [cap] 1/(v_k - v_{k+1})
-    float* sdt = sinv + v.cap;                                      // [cap] t_{k+1} - t_k
-    int* scell = reinterpret_cast<int*>(sdt + v.cap);               // [L]
+    float* sv = reinterpret_cast<float*>(srow + L);                 // [cap + 1] (t - t_k)/t
+    float* sinv = sv + v.cap + 1;                                   // [cap + 1] 1/(v_k - v_{k+1})
+    float* sdt = sinv + v.cap + 1;                                  // [cap + 1] t_{k+1} - t_k
+    int* scell = reinterpret_cast<int*>(sdt + v.cap + 1);           // [L]
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         double C = row[i], R = row[L + i];
         srow[i] = make_float4((float)(fp2(v.poly, C) * R), (float)fp1(v.poly, C), (float)C, (float)R);
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double tk = ht[i];
-        sht[i] = tk;
+    for (int i = threadIdx.x; i < nsl; i += blockDim.x) {
+        const double tk = i < n ? ht[i] : t;
         sv[i] = (float)((t - tk) / t);
-        if (i + 1 < n) {
-            double tk1 = ht[i + 1];
+        if (i + 1 < nsl) {
+            const double tk1 = i + 1 < n ? ht[i + 1] : t;
             sinv[i] = (float)(t / (tk1 - tk));
             sdt[i] = (float)(tk1 - tk);
         }
     }
     for (int m = threadIdx.x; m < L; m += blockDim.x) scell[m] = v.cell[m];
     __syncthreads();
-    const double tl = sht[n - 1];
-    const bool ext = t > tl;
-    const double hx = t - tl;
-    const float vlast = sv[n - 1];
-    const float hx32 = (float)hx;
     const int lane = threadIdx.x & 31;
     const float* __restrict__ om32 = v.omega32;
     const float* __restrict__ nu32 = v.nu32;
@@ -395,15 +394,12 @@ __device__ __forceinline__ void hi_f32_body(const SolverView& v, const double* _
                 const float u = omj * om32[i];
                 int a0, a1;
                 float w0, w1, w2, w3;
-                if (ext && u < vlast) {
-                    float q = (vlast - u) / vlast;
-                    a0 = n - 1; a1 = -1;
-                    w0 = 1.f - q * q; w1 = hx32 * (q - q * q); w2 = q * q; w3 = 0.f;
-                } else if (n == 1) {
-                    a0 = 0; a1 = 0; w0 = 1.f; w1 = 0.f; w2 = 0.f; w3 = 0.f;
+                if (kmax < 0) {
+                    // a single stored slice and the stage at its time
+                    a0 = 0; a1 = -1; w0 = 1.f; w1 = 0.f; w2 = 0.f; w3 = 0.f;
                 } else {
                     int k = scell[pp2 >> FIX_FRAC_BITS];
-                    while (k < n - 2 && sv[k + 1] >= u) ++k;
+                    while (k < kmax && sv[k + 1] >= u) ++k;
                     while (k > 0 && sv[k] < u) --k;
                     float sg = (sv[k] - u) * sinv[k];
                     float hh = sdt[k];
@@ -426,17 +422,11 @@ __device__ __forceinline__ void hi_f32_body(const SolverView& v, const double* _
                     c0 += w[k] * q.x; dc0 += w[k] * q.y; r0 += w[k] * q.z; dr0 += w[k] * q.w;
                 }
                 if (a1 >= 0) {
-                    const float4* __restrict__ s1 = H + (size_t)a1 * L + b;
+                    const float4* __restrict__ s1 = (a1 < n ? H + (size_t)a1 * L : VR) + b;
 #pragma unroll
                     for (int k = 0; k < SW; ++k) {
                         float4 q = s1[k];
                         c1 += w[k] * q.x; dc1 += w[k] * q.y; r1 += w[k] * q.z; dr1 += w[k] * q.w;
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < SW; ++k) {
-                        float4 q = srow[b + k];
-                        c1 += w[k] * q.z; r1 += w[k] * q.w;
                     }
                 }
                 CB2 = w0 * c0 + w1 * dc0 + w2 * c1 + w3 * dc1;
@@ -502,8 +492,7 @@ __global__ void __launch_bounds__(HI_THREADS, 1) k_batch_hi(const BatchTable* __
 size_t hi_smem_bytes(const SolverView& v) {
     if (v.precision == DMFE_FP64)
         return (size_t)v.L * sizeof(dbl4) + (size_t)(v.cap + 1) * 2 * sizeof(double) + (size_t)v.L * sizeof(int);
-    return (size_t)v.L * sizeof(float4) + (size_t)v.cap * (sizeof(double) + 3 * sizeof(float)) +
-           (size_t)v.L * sizeof(int);
+    return (size_t)v.L * sizeof(float4) + (size_t)(v.cap + 1) * 3 * sizeof(float) + (size_t)v.L * sizeof(int);
 }
 
 template <int SW>
