@@ -202,9 +202,36 @@ def _run_ours(args, rank, world, dev, stream):
         row = torch.tensor(np.concatenate([C[-1], R[-1]]), dtype=torch.float64, device="cuda")
         # a stage time just beyond the last slice, as for every stage after the first
         t_stage = float(times[-1]) * (1.0 + 1e-3)
-        for _ in range(args.warmup + args.steps):
+        kt = []
+        for k in range(args.warmup + args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
             sv.history_integrals_dev(t_stage, row.data_ptr(), S.data_ptr(), stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= args.warmup:
+                kt.append(e0.elapsed_time(e1) * 1e-3)
         torch.cuda.synchronize()
+        if rank == 0:
+            k_avg = float(np.mean(kt))
+            pairs = L * L
+            hist_b = {"fp64": 64 * (n0 - 1) * L, "df": 32 * n0 * L, "fp32": 16 * n0 * L}[args.precision]
+            tab_b = 3 * pairs * {"fp64": 40, "df": 8, "fp32": 4}[args.precision]
+            hbm, src = peaks()
+            per_pair = {"fp64": FLOP_PER_PAIR_S4, "df": DF_FP32_FLOP_PER_PAIR_S4}.get(args.precision)
+            flops = pairs * per_pair if per_pair else None
+            print(json.dumps({
+                "metric": "history-integral launches/s", "value": 1.0 / k_avg, "unit": "launches/s",
+                "n_gpus": 1, "higher_is_better": True, "dtype": DTYPES[args.precision], "data": "synthetic",
+                "config": {"workload": "dmfe_history_integrals_dev on a frozen seeded history: L=%d, %d slices on "
+                                       "geometric times 1e-2..9e4, s=4, stage time 0.1%% beyond the last slice, "
+                                       "L2 flushed before each launch" % (L, n0)},
+                "kernel_ms": k_avg * 1e3, "algorithmic_bytes": hist_b + tab_b,
+                "achieved_gbs": (hist_b + tab_b) / k_avg / 1e9,
+                "hbm_frac_of_%s" % src: (hist_b + tab_b) / k_avg / 1e9 / hbm,
+                "gflops": flops / k_avg / 1e9 if flops else None,
+                "pair_evals_per_s": pairs / k_avg}))
         return None
 
     # ---- state: the quench solved from t = 0 until the slice store is full (steady
