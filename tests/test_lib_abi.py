@@ -76,3 +76,64 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(built):
     p.grid_t_max = 2.0
     assert lib.dmfe_create(ctypes.byref(p), ctypes.byref(h)) == dmfe.DMFE_ERR_ARG
     assert not h.value
+
+
+def test_every_field_offset_matches_c(tmp_path):
+    """Offsets of every field of the four public structures, C against ctypes."""
+    from paper_2604_06309_gb300 import dmfe
+    structs = [("dmfe_params", dmfe.dmfe_params), ("dmfe_stats_t", dmfe.dmfe_stats_t),
+               ("dmfe_result", dmfe.dmfe_result), ("dmfe_server_stats_t", dmfe.dmfe_server_stats_t)]
+    lines = []
+    for cname, ct in structs:
+        lines.append('printf("%%zu\\n", sizeof(%s));' % cname)
+        for f, _ in ct._fields_:
+            lines.append('printf("%%zu\\n", offsetof(%s, %s));' % (cname, f))
+    prog = tmp_path / "off.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "dmfe.h"\nint main(void){%s return 0;}\n'
+                    % "".join(lines))
+    exe = tmp_path / "off"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    want = []
+    for _, ct in structs:
+        want.append(ctypes.sizeof(ct))
+        want += [getattr(ct, f).offset for f, _ in ct._fields_]
+    assert got == want
+
+
+def test_defaults_and_host_side_validation_without_gpu(built):
+    """dmfe_default_params, dmfe_footprint and the parameter checks of dmfe_create run on
+    the host only (no device call happens before a parameter is rejected)."""
+    from paper_2604_06309_gb300 import dmfe
+    lib = dmfe.load()
+    p = dmfe.dmfe_params()
+    lib.dmfe_default_params(ctypes.byref(p))
+    assert (p.L, p.s, p.precision, p.sparsify, p.integrator, p.rk_switch_dt, p.hi_chunk, p.interp, p.fh_d) == \
+        (513, 4, 0, 1, 0, 0.0, 0, 0, 3)
+    assert p.dt0 == 1e-4 and p.dt_min == 1e-12 and p.grid_t_max == 1e5
+
+    def params(**kw):
+        prm, keep = dmfe.make_params({3: 0.25, 4: 0.25}, 0.5, kw.pop("L", 129), kw.pop("grid_t_max", 1e3), **kw)
+        return prm, keep
+
+    # footprint: grows with L and the store; FP64 (weight tables, interval coefficients) >
+    # double-float (positions, replica) > FP32 (packed positions, FP32 replica)
+    fp = lambda **kw: lib.dmfe_footprint(ctypes.byref(params(**kw)[0]))
+    assert fp(L=257) > fp(L=129) > 0
+    assert fp(L=129, history_cap=400) > fp(L=129)
+    assert fp(precision="fp64") > fp(precision="df") > fp(precision="fp32")
+    h = ctypes.c_void_p()
+    bad = [dict(L=8), dict(s=5), dict(history_cap=8), dict(dt0=0.0), dict(hi_chunk=16), dict(fh_d=4, interp="fh_index")]
+    for kw in bad:
+        prm, keep = params(**kw)
+        rc = lib.dmfe_create(ctypes.byref(prm), ctypes.byref(h))
+        assert rc in (-1, -8), (kw, rc)
+        assert fp(**kw) == 0 if rc == -1 else True
+    for prec in ("df", "fp32"):          # the rational and theta-space stencils need FP64
+        prm, keep = params(precision=prec, interp="fh_index")
+        assert lib.dmfe_create(ctypes.byref(prm), ctypes.byref(h)) == -8
+    prm, keep = params()
+    prm.integrator = 7
+    assert lib.dmfe_create(ctypes.byref(prm), ctypes.byref(h)) == -1
+    prm, keep = params(grid_t_max=2.0)   # gamma = -W_{-1}(-1/t_max) needs t_max > e
+    assert lib.dmfe_create(ctypes.byref(prm), ctypes.byref(h)) == -1
