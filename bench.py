@@ -444,6 +444,18 @@ def run_aging(args):
             break
         _, _, _, mu, E = sv.get_row()
         rec.append((float(tc), E, time.perf_counter() - t0, st["steps_accepted"] + st["steps_rejected"]))
+    # fluctuation-dissipation ratio X = R(t, t') / d_t' C(t, t') at the last time over the
+    # aging regime t' << t (Sec. 4.4); at T = 0 it tends to x_th = sqrt(f''(1))/f'(1) -
+    # 1/sqrt(f''(1)) for pure models
+    tf = rec[-1][0] if rec else 0.0
+    fdr = []
+    if tf > 0:
+        for th in (0.02, 0.05, 0.1, 0.2, 0.3):
+            tp, dtp = th * tf, 1e-3 * th * tf
+            cp, cm = sv.get_C([tf, tf], [tp + dtp, tp - dtp])
+            r = sv.get_R([tf], [tp])[0]
+            c = sv.get_C([tf], [tp])[0]
+            fdr.append({"theta": th, "C": float(c), "X": float(r * 2 * dtp / (cp - cm))})
     sv.close()
     t = np.array([r[0] for r in rec])
     dE = np.array([r[1] for r in rec]) - eth
@@ -455,7 +467,11 @@ def run_aging(args):
                                    "tol %g, integrator %s" % (args.coefs, args.T, args.L, args.L, args.tol,
                                                               args.integrator), "E_th": eth},
             "trace": [{"t": r[0], "E": r[1], "dE": float(d), "local_exponent": float(e), "wall_s": r[2],
-                       "steps": r[3]} for r, d, e in zip(rec, dE, slope)]}
+                       "steps": r[3]} for r, d, e in zip(rec, dE, slope)],
+            "fdr_at_last_time": fdr,
+            "x_th_pure_T0": float(np.sqrt(sum(c * p * (p - 1) for p, c in coefs.items())) /
+                                  sum(c * p for p, c in coefs.items()) -
+                                  1.0 / np.sqrt(sum(c * p * (p - 1) for p, c in coefs.items())))}
 
 
 def run_solve(args):
