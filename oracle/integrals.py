@@ -78,13 +78,14 @@ class Grid:
 
     CACHE_MAX_L = 1024
 
-    def __init__(self, L, t_max, s=4, alpha=0.0, delta=0.0, interp="lagrange_index", fh_d=3):
+    def __init__(self, L, t_max, s=4, alpha=0.0, delta=0.0, interp="lagrange_index", fh_d=3, log_r=False):
         from . import grid as g
         from .quadrature import spline_weights
         from .interp import SCHEMES
         if interp not in SCHEMES:
             raise ValueError("unknown interpolation scheme %r" % interp)
         self.interp, self.fh_d = interp, int(fh_d)
+        self.log_r = bool(log_r)  # logarithmic interpolation of the response history
         self.L, self.s = int(L), int(s)
         self.t_max, self.alpha, self.delta = float(t_max), float(alpha), float(delta)
         self.gamma = g.gamma_from_tmax(t_max)
@@ -160,11 +161,33 @@ def _gather_row(row, b, w):
     return sum(w[..., k] * row[b + k] for k in range(w.shape[-1]))
 
 
-def lookup(hist, tau, b, w, t_cur, C_cur, R_cur):
+def _positive(rows, n, b, w):
+    """True where every stencil value rows[n, b + k] (or rows[n, b]) is positive."""
+    if w is None:
+        return rows[n, b] > 0
+    return np.all(np.stack([rows[n, b + k] > 0 for k in range(w.shape[-1])]), axis=0)
+
+
+def _positive_row(row, b, w):
+    if w is None:
+        return row[b] > 0
+    return np.all(np.stack([row[b + k] > 0 for k in range(w.shape[-1])]), axis=0)
+
+
+def _safe_log(x):
+    return np.log(np.where(x > 0, x, 1.0))
+
+
+def lookup(hist, tau, b, w, t_cur, C_cur, R_cur, log_r=False):
     """(Cf, Rf) at times tau and theta positions (b, w) from the history (Sec. 3.3).
 
     b, w: stencil in the theta index (w None: on-grid column b). tau, b and w must
     broadcast together. tau <= t_cur is required.
+
+    log_r (the optional logarithmic interpolation of the response history, App. A):
+    where every stencil value of R on the slices involved is positive, R is
+    interpolated as exp of the same interpolant applied to log R with the scaled
+    derivative R'/R; elsewhere the linear interpolation is kept.
     """
     tau = np.asarray(tau, dtype=float)
     tau, b = np.broadcast_arrays(tau, b)
@@ -173,17 +196,21 @@ def lookup(hist, tau, b, w, t_cur, C_cur, R_cur):
     ext = (t_cur > tl) & (tau > tl)
     outC = np.empty(tau.shape)
     outR = np.empty(tau.shape)
+    if log_r:
+        lR, ldR = _safe_log(hist.R), hist.dR / np.where(hist.R > 0, hist.R, 1.0)
+        lRc = _safe_log(np.asarray(R_cur, dtype=float))
     if np.any(ext):
         bb = b[ext]
         ww = None if w is None else np.broadcast_to(w, b.shape + w.shape[-1:])[ext]
         h = t_cur - tl
         sg = tau[ext] - tl
+        quad = lambda y0, d0, y1: y0 + d0 * sg + (y1 - y0 - d0 * h) / (h * h) * sg * sg
         for rows, drows, cur, out in ((hist.C, hist.dC, C_cur, outC), (hist.R, hist.dR, R_cur, outR)):
-            y0 = _gather(rows, N - 1, bb, ww)
-            d0 = _gather(drows, N - 1, bb, ww)
-            y1 = _gather_row(cur, bb, ww)
-            c = (y1 - y0 - d0 * h) / (h * h)
-            out[ext] = y0 + d0 * sg + c * sg * sg
+            out[ext] = quad(_gather(rows, N - 1, bb, ww), _gather(drows, N - 1, bb, ww), _gather_row(cur, bb, ww))
+        if log_r:
+            pos = _positive(hist.R, N - 1, bb, ww) & _positive_row(np.asarray(R_cur), bb, ww)
+            lv = np.exp(quad(_gather(lR, N - 1, bb, ww), _gather(ldR, N - 1, bb, ww), _gather_row(lRc, bb, ww)))
+            outR[ext] = np.where(pos, lv, outR[ext])
     inn = ~ext
     if np.any(inn):
         bb = b[inn]
@@ -192,14 +219,19 @@ def lookup(hist, tau, b, w, t_cur, C_cur, R_cur):
         if N == 1:
             outC[inn] = _gather(hist.C, 0, bb, ww)
             outR[inn] = _gather(hist.R, 0, bb, ww)
+            if log_r:
+                outR[inn] = np.where(_positive(hist.R, 0, bb, ww), np.exp(_gather(lR, 0, bb, ww)), outR[inn])
         else:
             n = np.clip(np.searchsorted(hist.t, ti, side="right") - 1, 0, N - 2)
             h = hist.t[n + 1] - hist.t[n]
             sig = (ti - hist.t[n]) / h
-            for rows, drows, out in ((hist.C, hist.dC, outC), (hist.R, hist.dR, outR)):
-                y0, d0 = _gather(rows, n, bb, ww), _gather(drows, n, bb, ww)
-                y1, d1 = _gather(rows, n + 1, bb, ww), _gather(drows, n + 1, bb, ww)
-                out[inn] = hermite(y0, d0, y1, d1, h, sig)
+            herm = lambda rows, drows: hermite(_gather(rows, n, bb, ww), _gather(drows, n, bb, ww),
+                                              _gather(rows, n + 1, bb, ww), _gather(drows, n + 1, bb, ww), h, sig)
+            outC[inn] = herm(hist.C, hist.dC)
+            outR[inn] = herm(hist.R, hist.dR)
+            if log_r:
+                pos = _positive(hist.R, n, bb, ww) & _positive(hist.R, n + 1, bb, ww)
+                outR[inn] = np.where(pos, np.exp(herm(lR, ldR)), outR[inn])
     return outC, outR
 
 
@@ -232,9 +264,9 @@ def history_integrals(model, grid, hist, t, C, R, js=None, j_chunk=256):
         C_A1, R_A1 = _gather_row(C, b1, w1), _gather_row(R, b1, w1)
         K_A2, R_A2 = _gather_row(K, b2, w2), _gather_row(R, b2, w2)
         # B1: on-grid theta_i at time theta_j t
-        C_B1, R_B1 = lookup(hist, thj * t, cols[None, :], None, t, C, R)
+        C_B1, R_B1 = lookup(hist, thj * t, cols[None, :], None, t, C, R, grid.log_r)
         # B2: theta position psi_ij at time phi2_ij t
-        C_B2, R_B2 = lookup(hist, phi2 * t, b3, w3, t, C, R)
+        C_B2, R_B2 = lookup(hist, phi2 * t, b3, w3, t, C, R, grid.log_r)
         fpp1, fp1 = model.fpp(C_B1), model.fp(C_B1)
         fpp2, fp2 = model.fpp(C_B2), model.fp(C_B2)
         terms = (K_A1 * C_B1, K_A2 * C_B2, D_A1 * R_B1, K_A2 * R_B2,

@@ -261,13 +261,13 @@ class Solver:
 
     def __init__(self, coefs, T, L, grid_t_max, s=4, beta0=0.0, alpha=0.0, delta=0.0,
                  history_cap=None, dt0=1e-4, dt_min=1e-12, sparsify=True, integrator="auto",
-                 switch_dt=0.0, interp="lagrange_index", fh_d=3):
+                 switch_dt=0.0, interp="lagrange_index", fh_d=3, log_r=False):
         """integrator: "dp5" (Dormand-Prince throughout), "ssprk104" (SSPRK(10,4)
         throughout) or "auto" (Dormand-Prince, then SSPRK(10,4) once dt reaches
         switch_dt; switch_dt = 0 takes the stability estimate switch_dt_auto)."""
         from .model import Model
         self.model = Model(coefs, T, beta0)
-        self.grid = Grid(L, grid_t_max, s, alpha, delta, interp=interp, fh_d=fh_d)
+        self.grid = Grid(L, grid_t_max, s, alpha, delta, interp=interp, fh_d=fh_d, log_r=log_r)
         self.cap = int(history_cap if history_cap is not None else L)
         if self.cap < 16:
             raise ValueError("history_cap must be at least 16")
@@ -380,13 +380,24 @@ def get_two_time(grid, hist, t, tp, which):
     b, w = grid.stencil_at(x, om)
     Y, dY = (hist.C, hist.dC) if which == "C" else (hist.R, hist.dR)
     N = hist.N
+    g = lambda rows, m: sum(w[..., k] * rows[m, b + k] for k in range(grid.s))
+    positive = lambda m: np.all(np.stack([Y[m, b + k] > 0 for k in range(grid.s)]), axis=0)
+    use_log = which == "R" and grid.log_r
+    if use_log:
+        lY = np.log(np.where(Y > 0, Y, 1.0))
+        ldY = dY / np.where(Y > 0, Y, 1.0)
     if N == 1:
-        val = sum(w[..., k] * Y[0, b + k] for k in range(grid.s))
+        val = g(Y, 0)
+        if use_log:
+            val = np.where(positive(0), np.exp(g(lY, 0)), val)
     else:
         n = np.clip(np.searchsorted(hist.t, big, side="right") - 1, 0, N - 2)
         h = hist.t[n + 1] - hist.t[n]
         sig = (big - hist.t[n]) / h
-        g = lambda rows, m: sum(w[..., k] * rows[m, b + k] for k in range(grid.s))
         val = hermite(g(Y, n), g(dY, n), g(Y, n + 1), g(dY, n + 1), h, sig)
+        if use_log:
+            # logarithmic interpolation of the response where the stencil is positive
+            lval = np.exp(hermite(g(lY, n), g(ldY, n), g(lY, n + 1), g(ldY, n + 1), h, sig))
+            val = np.where(positive(n) & positive(n + 1), lval, val)
     out[ok] = val[ok]
     return out

@@ -152,3 +152,69 @@ def test_planted_mistakes_are_caught_by_the_p2_pin(mutation):
     _, dCx, _, dRx = cf.p2_fields(t, G.theta, G.omega)
     err = max(np.max(np.abs(dC[:-1] - dCx[:-1])), np.max(np.abs(dR[:-1] - dRx[:-1])))
     assert err > 1e-3
+
+
+# ---- logarithmic interpolation of the response history (App. A)
+def _exp_history(L, s, sign_flip=False):
+    """R(t_n, x) = exp(a + b x + c t_n) on the grid index x: log R is linear in t and in x,
+    so the logarithmic interpolation reproduces it exactly and the linear one does not."""
+    G = Grid(L, 100.0, s=s, log_r=True)
+    t = np.array([0.0, 0.5, 1.1, 1.8, 2.6])
+    x = np.arange(L, dtype=float)
+    a, bb, c = -0.3, -0.05, -0.7
+    R = np.exp(a + bb * x[None, :] + c * t[:, None])
+    dR = c * R
+    C = 0.5 * R
+    if sign_flip:
+        R[2, 10:14] *= -1.0
+        dR[2, 10:14] *= -1.0
+    return G, History(t, C, 0.5 * dR, R, dR), (a, bb, c)
+
+
+def test_log_r_reproduces_exponential_response():
+    from oracle.integrals import lookup
+    L, s = 65, 6
+    G, H, (a, bb, c) = _exp_history(L, s)
+    rng = np.random.default_rng(8)
+    xq = rng.uniform(0, L - 1, 300)
+    tq = rng.uniform(0.0, 2.6, 300)
+    b, w = G.stencil_at(xq, None)
+    _, R_log = lookup(H, tq, b, w, 2.6, H.C[-1], H.R[-1], log_r=True)
+    _, R_lin = lookup(H, tq, b, w, 2.6, H.C[-1], H.R[-1], log_r=False)
+    exact = np.exp(a + bb * xq + c * tq)
+    assert np.max(np.abs(R_log - exact) / exact) < 1e-12
+    assert np.max(np.abs(R_lin - exact) / exact) > 1e-6      # the linear path is only approximate
+    # beyond the last slice: the quadratic extension in log R, exact for log R linear in t
+    t_cur = 3.0
+    row = np.exp(a + bb * np.arange(L) + c * t_cur)
+    tq2 = rng.uniform(2.6, 3.0, 100)
+    xq2 = rng.uniform(0, L - 1, 100)
+    b2, w2 = G.stencil_at(xq2, None)
+    _, R2 = lookup(H, tq2, b2, w2, t_cur, 0.5 * row, row, log_r=True)
+    assert np.max(np.abs(R2 - np.exp(a + bb * xq2 + c * tq2)) / R2) < 1e-12
+
+
+def test_log_r_falls_back_where_the_stencil_is_not_positive():
+    from oracle.integrals import lookup
+    L, s = 65, 4
+    G, H, _ = _exp_history(L, s, sign_flip=True)
+    xq = np.array([11.3, 40.2, 12.0])
+    tq = np.array([1.4, 1.4, 0.8])       # all in the intervals that touch slice 2 (t = 1.1)
+    b, w = G.stencil_at(xq, None)
+    _, R_log = lookup(H, tq, b, w, 2.6, H.C[-1], H.R[-1], log_r=True)
+    _, R_lin = lookup(H, tq, b, w, 2.6, H.C[-1], H.R[-1], log_r=False)
+    assert R_log[0] == R_lin[0] and R_log[2] == R_lin[2]     # stencils touching the negative values
+    assert R_log[1] != R_lin[1]                               # a positive stencil takes the log path
+
+
+def test_log_r_two_time_lookup():
+    from oracle import grid as gm
+    from oracle.solver import get_two_time
+    L, s = 65, 6
+    G, H, (a, bb, c) = _exp_history(L, s)
+    t = np.array([2.6, 2.0, 1.3, 0.7])
+    tp = np.array([1.0, 0.3, 1.2, 0.1])
+    th, om = tp / t, (t - tp) / t
+    x = gm.frac_index(th, om, L, G.gamma, G.alpha, G.delta)
+    got = get_two_time(G, H, t, tp, "R")
+    assert np.max(np.abs(got - np.exp(a + bb * x + c * t)) / got) < 1e-12
