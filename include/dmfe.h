@@ -102,6 +102,10 @@ typedef struct {
                                    dmfe_create returns DMFE_ERR_UNSUPPORTED              */
     int           fh_d;         /* Floater-Hormann blending degree, 0 <= fh_d <= s-1
                                    (default 3; fh_d = s-1 is the polynomial interpolant)  */
+    int           log_r;        /* 1: interpolate the response history in log R (with the
+                                   scaled derivative R'/R) wherever the stencil's values
+                                   are positive, linearly elsewhere (App. A); DMFE_FP64
+                                   only (else DMFE_ERR_UNSUPPORTED). Default 0            */
 } dmfe_params;
 
 /* Per-solve counters. */

@@ -125,6 +125,9 @@ int validate(const dmfe_params* p) {
     if (p->s != 4 && p->s != 6 && p->s != 8 && p->s != 10) return DMFE_ERR_UNSUPPORTED;
     // the other schemes' weights live in the FP64 stencil tables
     if (p->interp != DMFE_INTERP_LAGRANGE_INDEX && p->precision != DMFE_FP64) return DMFE_ERR_UNSUPPORTED;
+    // the logarithmic response interpolation is built into the FP64 path's coefficient tables
+    if (p->log_r != 0 && p->log_r != 1) return DMFE_ERR_ARG;
+    if (p->log_r && p->precision != DMFE_FP64) return DMFE_ERR_UNSUPPORTED;
     return DMFE_OK;
 }
 
@@ -180,6 +183,7 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
     v.rk_switch_dt = switch_dt_for(&h->p);
     v.interp = pin->interp;
     v.fh_d = pin->fh_d;
+    v.log_r = pin->log_r ? 1 : 0;
     build_poly(h->powers, h->coefs, v.poly);
     v.gamma = host_gamma_from_tmax(pin->grid_t_max);
     v.ga = std::atan(std::exp(-v.gamma));
@@ -237,6 +241,9 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
         }
         if (v.precision == DMFE_FP64) {
             TRY(dev_alloc(h, &p, (size_t)cap * L * sizeof(dbl8))); v.hcoef[b] = (dbl8*)p;
+        }
+        if (pin->log_r) {
+            TRY(dev_alloc(h, &p, (size_t)cap * L * sizeof(dbl4))); v.lcoef[b] = (dbl4*)p;
         }
     }
     TRY(dev_alloc(h, &p, sizeof(DevState))); v.st = (DevState*)p;
@@ -423,6 +430,7 @@ unsigned long long dmfe_footprint(const dmfe_params* pin) {
         if (p.precision == DMFE_FP32_COMPENSATED && b == 0) add(L * sizeof(float4));
         if (p.precision == DMFE_DOUBLE_FLOAT) add(cap * L * sizeof(df8));
         if (p.precision == DMFE_FP64) add(cap * L * sizeof(dbl8));
+        if (p.log_r) add(cap * L * sizeof(dbl4));
     }
     add(sizeof(DevState)); add(4 * L * 8);
     add(2ull * kMaxPrepBlocks * 8); add(kCtlGrid * 8); add(4);
@@ -830,7 +838,7 @@ int dmfe_sync(dmfe_solver* h) {
 
 // ---- checkpoint format: magic, version, parameters, f, device state, history (FP64).
 static const char kMagic[8] = {'D', 'M', 'F', 'E', 'C', 'K', 'P', '2'};
-static const int kCkpVersion = 2;  // 2: integrator fields in the parameters and the state
+static const int kCkpVersion = 3;  // 2: integrator fields; 3: log-R flag in the parameters
 
 int dmfe_checkpoint(dmfe_solver* h, const char* path) {
     if (!h || !path) return DMFE_ERR_ARG;

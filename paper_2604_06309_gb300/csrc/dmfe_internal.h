@@ -125,6 +125,7 @@ struct SolverView {
     double rk_switch_dt;  // controller step of the switch to SSPRK(10,4) (+inf: never)
     int interp, fh_d;     // theta-stencil scheme (DMFE_INTERP_*) and Floater-Hormann degree
     int hi_threads;       // block size of a single solve's history-integral launch
+    int log_r;            // 1: logarithmic interpolation of the response history
     double T, beta0;
     double gamma, ga, gD, alpha, delta;  // grid: gamma, atan(e^-gamma), atan(e^gamma) - atan(e^-gamma)
     Poly poly;
@@ -147,6 +148,7 @@ struct SolverView {
     float4* hist32[2];    // [cap][L] FP32 replica (FP32 path)
     df8* histdf[2];       // [cap][L] double-float replica (double-float path)
     dbl8* hcoef[2];       // [cap][L] FP64 path: row k = monomial coefficients of interval k
+    dbl4* lcoef[2];       // [cap][L] log-R mode: the same for log R (x = NaN: R not positive)
     const df* q1;         // [L*L] double-float fractional index (double-float path)
     const df* q2;
     const df* q3;

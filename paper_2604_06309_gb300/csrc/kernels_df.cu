@@ -93,6 +93,16 @@ __device__ __forceinline__ void stage_prep_body(const SolverView& v, const doubl
                 c.c0 = e.x; c.c1 = hx * e.y; c.c2 = Cq - e.x - hx * e.y; c.c3 = 0.0;
                 c.r0 = e.z; c.r1 = hx * e.w; c.r2 = Rq - e.z - hx * e.w; c.r3 = 0.0;
                 v.hcoef[act][(size_t)(n - 1) * L + q] = c;
+                if (v.lcoef[act]) {
+                    // log-R mode: the quadratic in log R through (log R_last, R'_last/R_last)
+                    // and log of the stage row, where both are positive
+                    dbl4 l{nan(""), 0.0, 0.0, 0.0};
+                    if (e.z > 0.0 && Rq > 0.0) {
+                        const double l0 = log(e.z), l1 = hx * e.w / e.z;
+                        l = dbl4{l0, l1, log(Rq) - l0 - l1, 0.0};
+                    }
+                    v.lcoef[act][(size_t)(n - 1) * L + q] = l;
+                }
             }
             if (v.rowdf) {
                 const double C = row[q], R = row[L + q];

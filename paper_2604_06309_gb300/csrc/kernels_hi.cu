@@ -106,6 +106,7 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
     const double t = from_state ? st->t_stage : t_arg;
     const dbl4* __restrict__ H = v.hist[act];
     const dbl8* __restrict__ HC = v.hcoef[act];
+    const dbl4* __restrict__ LC = v.lcoef[act];  // log-R mode only (else NULL)
     const double* __restrict__ ht = v.ht[act];
     // Slice times with the stage time appended when the stage lies beyond the last slice:
     // the quadratic extension is then the virtual interval n-1 = [t_last, t], whose
@@ -166,6 +167,10 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
                 const dbl8 c = HC[(size_t)b1.a0 * L + i];
                 CB1 = c.c0 + s1 * (c.c1 + s1 * (c.c2 + s1 * c.c3));
                 RB1 = c.r0 + s1 * (c.r1 + s1 * (c.r2 + s1 * c.r3));
+                if (LC) {
+                    const dbl4 l = LC[(size_t)b1.a0 * L + i];
+                    if (!isnan(l.x)) RB1 = exp(l.x + s1 * (l.y + s1 * (l.z + s1 * l.w)));
+                }
             } else {
                 dbl4 h0 = H[(size_t)b1.a0 * L + i];
                 CB1 = b1.w0 * h0.x + b1.w1 * h0.y;
@@ -240,16 +245,33 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
                         CB2 += w[m] * (c.c0 + sg * (c.c1 + sg * (c.c2 + sg * c.c3)));
                         RB2 += w[m] * (c.r0 + sg * (c.r1 + sg * (c.r2 + sg * c.r3)));
                     }
+                    if (LC) {
+                        // log-R mode: the same interpolant on log R; a NaN (some node's R not
+                        // positive) propagates through the sum and keeps the linear value
+                        const dbl4* __restrict__ Q = LC + (size_t)k * L + b;
+                        double lr = 0.0;
+#pragma unroll
+                        for (int m = 0; m < SW; ++m) {
+                            const dbl4 l = Q[m];
+                            lr += w[m] * (l.x + sg * (l.y + sg * (l.z + sg * l.w)));
+                        }
+                        if (!isnan(lr)) RB2 = exp(lr);
+                    }
                 } else {
                     // a single stored slice and the stage at its time
                     CB2 = 0.0;
                     RB2 = 0.0;
+                    bool pos = true;
+                    double lr = 0.0;
 #pragma unroll
                     for (int m = 0; m < SW; ++m) {
                         const dbl4 q = H[b + m];
                         CB2 += w[m] * q.x;
                         RB2 += w[m] * q.z;
+                        pos = pos && q.z > 0.0;
+                        lr += w[m] * (q.z > 0.0 ? log(q.z) : 0.0);
                     }
+                    if (LC && pos) RB2 = exp(lr);
                 }
             }
             const double f1a = fp1(v.poly, CB1), f2a = fp2(v.poly, CB1);

@@ -305,6 +305,15 @@ __device__ __forceinline__ dbl8 interval_coef(const dbl4& a, const dbl4& b, doub
     return c;
 }
 
+// Monomial coefficients of the cubic Hermite interpolant of log R between history points a
+// and b (log-R mode, App. A): values log R, derivatives R'/R. x = NaN where either R is not
+// positive (the kernels then interpolate R itself).
+__device__ __forceinline__ dbl4 interval_logcoef(const dbl4& a, const dbl4& b, double h) {
+    if (!(a.z > 0.0 && b.z > 0.0)) return dbl4{nan(""), 0.0, 0.0, 0.0};
+    const double la = log(a.z), lb = log(b.z), da = a.w / a.z, db = b.w / b.z, dl = lb - la;
+    return dbl4{la, h * da, 3.0 * dl - h * (2.0 * da + db), -2.0 * dl + h * (da + db)};
+}
+
 // Write slice `slot` = (t, Y, dY) to buffer `act`: FP64 master, the replica of the
 // precision, and (FP64 path) the interval coefficients between slots slot-1 and slot.
 __device__ void append_slice(const SolverView& v, int act, int slot, double t, const double* Y,
@@ -314,6 +323,7 @@ __device__ void append_slice(const SolverView& v, int act, int slot, double t, c
     float4* H32 = v.hist32[act] ? v.hist32[act] + (size_t)slot * L : nullptr;
     df8* HD = v.histdf[act] ? v.histdf[act] + (size_t)slot * L : nullptr;
     dbl8* HC = (v.hcoef[act] && slot >= 1) ? v.hcoef[act] + (size_t)(slot - 1) * L : nullptr;
+    dbl4* LC = (v.lcoef[act] && slot >= 1) ? v.lcoef[act] + (size_t)(slot - 1) * L : nullptr;
     const double hprev = slot >= 1 ? t - v.ht[act][slot - 1] : 0.0;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         const dbl4 e{Y[i], dY[i], Y[L + i], dY[L + i]};
@@ -321,6 +331,7 @@ __device__ void append_slice(const SolverView& v, int act, int slot, double t, c
         if (H32) H32[i] = make_float4((float)e.x, (float)e.y, (float)e.z, (float)e.w);
         if (HD) HD[i] = df8{df_from_d(e.x), df_from_d(e.y), df_from_d(e.z), df_from_d(e.w)};
         if (HC) HC[i] = interval_coef(H[(long long)i - L], e, hprev);
+        if (LC) LC[i] = interval_logcoef(H[(long long)i - L], e, hprev);
     }
     if (threadIdx.x == 0) v.ht[act][slot] = t;
 }
@@ -665,6 +676,9 @@ __device__ __forceinline__ void sp_compact_body(const SolverView& v, int cta, in
             while (p > 0 && !v.keep[p]) --p;
             v.hcoef[nxt][dst - L] = interval_coef(v.hist[act][(size_t)p * L + i], v.hist[act][q],
                                                   v.ht[act][k] - v.ht[act][p]);
+            if (v.lcoef[act])
+                v.lcoef[nxt][dst - L] = interval_logcoef(v.hist[act][(size_t)p * L + i], v.hist[act][q],
+                                                         v.ht[act][k] - v.ht[act][p]);
         }
         if (i == 0) v.ht[nxt][v.newidx[k]] = v.ht[act][k];
     }
@@ -747,7 +761,26 @@ __global__ void k_lookup(SolverView v, int nq, const double* tq, const double* t
         }
         return acc;
     };
-    if (n == 1) { out[q] = val(0, false); return; }
+    // log-R mode for R: the same interpolation of log R and R'/R where the stencil's R is
+    // positive on the slices involved (App. A)
+    const bool logr = which == 1 && v.log_r;
+    auto positive = [&](int sl) {
+        for (int k = 0; k < s; ++k)
+            if (!(H[(size_t)sl * L + b + k].z > 0.0)) return false;
+        return true;
+    };
+    auto lval = [&](int sl, bool deriv) {
+        double acc = 0.0;
+        for (int k = 0; k < s; ++k) {
+            const dbl4 e = H[(size_t)sl * L + b + k];
+            acc += w[k] * (deriv ? e.w / e.z : log(e.z));
+        }
+        return acc;
+    };
+    if (n == 1) {
+        out[q] = (logr && positive(0)) ? exp(lval(0, false)) : val(0, false);
+        return;
+    }
     int lo = 0, hi = n - 2;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -755,8 +788,14 @@ __global__ void k_lookup(SolverView v, int nq, const double* tq, const double* t
     }
     const double hh = ht[lo + 1] - ht[lo];
     const double sg = (big - ht[lo]) / hh, o = 1.0 - sg;
-    out[q] = (1.0 + 2.0 * sg) * o * o * val(lo, false) + sg * o * o * hh * val(lo, true) +
-             sg * sg * (3.0 - 2.0 * sg) * val(lo + 1, false) + sg * sg * (sg - 1.0) * hh * val(lo + 1, true);
+    const double h00 = (1.0 + 2.0 * sg) * o * o, h10 = sg * o * o * hh, h01 = sg * sg * (3.0 - 2.0 * sg),
+                 h11 = sg * sg * (sg - 1.0) * hh;
+    if (logr && positive(lo) && positive(lo + 1)) {
+        out[q] = exp(h00 * lval(lo, false) + h10 * lval(lo, true) + h01 * lval(lo + 1, false) +
+                     h11 * lval(lo + 1, true));
+        return;
+    }
+    out[q] = h00 * val(lo, false) + h10 * val(lo, true) + h01 * val(lo + 1, false) + h11 * val(lo + 1, true);
 }
 
 __global__ void k_refresh_replica(SolverView v) {
@@ -771,6 +810,8 @@ __global__ void k_refresh_replica(SolverView v) {
         const int k = (int)(q / v.L);
         if (v.hcoef[act] && k + 1 < st->n)
             v.hcoef[act][q] = interval_coef(e, v.hist[act][q + v.L], v.ht[act][k + 1] - v.ht[act][k]);
+        if (v.lcoef[act] && k + 1 < st->n)
+            v.lcoef[act][q] = interval_logcoef(e, v.hist[act][q + v.L], v.ht[act][k + 1] - v.ht[act][k]);
     }
 }
 
@@ -870,7 +911,7 @@ int launch_lookup(const SolverView& v, int n, const double* t, const double* tp,
 }
 
 int launch_refresh_replica(const SolverView& v, cudaStream_t s) {
-    if (!v.hist32[0] && !v.histdf[0] && !v.hcoef[0]) return DMFE_OK;
+    if (!v.hist32[0] && !v.histdf[0] && !v.hcoef[0] && !v.lcoef[0]) return DMFE_OK;
     k_refresh_replica<<<grid_for((long long)v.cap * v.L, 256), 256, 0, s>>>(v);
     DMFE_CUDA_TRY(cudaGetLastError());
     return DMFE_OK;

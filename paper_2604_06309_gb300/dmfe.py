@@ -47,7 +47,7 @@ class dmfe_params(ctypes.Structure):
                 ("L", _i), ("s", _i), ("grid_t_max", _d), ("alpha", _d), ("delta", _d),
                 ("history_cap", _i), ("dt0", _d), ("dt_min", _d), ("precision", _i),
                 ("sparsify", _i), ("stream", _p), ("integrator", _i), ("rk_switch_dt", _d), ("hi_chunk", _i),
-                ("interp", _i), ("fh_d", _i)]
+                ("interp", _i), ("fh_d", _i), ("log_r", _i)]
 
 
 class dmfe_stats_t(ctypes.Structure):
@@ -156,7 +156,7 @@ def _f64(a, n=None):
 
 def make_params(coefs, T, L, grid_t_max, s=4, beta0=0.0, alpha=0.0, delta=0.0, history_cap=None, dt0=1e-4,
                 dt_min=1e-12, precision="fp64", sparsify=True, stream=None, integrator="auto", switch_dt=0.0,
-                hi_chunk=0, interp="lagrange_index", fh_d=3):
+                hi_chunk=0, interp="lagrange_index", fh_d=3, log_r=False):
     """A dmfe_params structure; the returned tuple keeps the coefficient arrays alive."""
     lib = load()
     terms = sorted((int(p), float(c)) for p, c in dict(coefs).items())
@@ -179,6 +179,7 @@ def make_params(coefs, T, L, grid_t_max, s=4, beta0=0.0, alpha=0.0, delta=0.0, h
     prm.hi_chunk = int(hi_chunk)
     prm.interp = INTERPS[interp]
     prm.fh_d = int(fh_d)
+    prm.log_r = 1 if log_r else 0
     return prm, (pw, cf)
 
 
@@ -297,7 +298,8 @@ class Solver:
 
     def __init__(self, coefs, T, L, grid_t_max, s=4, beta0=0.0, alpha=0.0, delta=0.0,
                  history_cap=None, dt0=1e-4, dt_min=1e-12, precision="fp64", sparsify=True,
-                 stream=None, integrator="auto", switch_dt=0.0, hi_chunk=0, interp="lagrange_index", fh_d=3):
+                 stream=None, integrator="auto", switch_dt=0.0, hi_chunk=0, interp="lagrange_index", fh_d=3,
+                 log_r=False):
         """integrator: "auto" (Dormand-Prince, then SSPRK(10,4) once the step reaches
         switch_dt; 0 = the stability estimate), "dp5" or "ssprk104" (Sec. 3.5)."""
         lib = load()
@@ -307,7 +309,7 @@ class Solver:
         prm, keep = make_params(coefs, T, L, grid_t_max, s=s, beta0=beta0, alpha=alpha, delta=delta,
                                 history_cap=history_cap, dt0=dt0, dt_min=dt_min, precision=precision,
                                 sparsify=sparsify, stream=stream, integrator=integrator, switch_dt=switch_dt,
-                                hi_chunk=hi_chunk, interp=interp, fh_d=fh_d)
+                                hi_chunk=hi_chunk, interp=interp, fh_d=fh_d, log_r=log_r)
         _check(lib.dmfe_create(ctypes.byref(prm), ctypes.byref(self.h)), "dmfe_create")
         self._sizes()
 

@@ -108,8 +108,8 @@ def test_defaults_and_host_side_validation_without_gpu(built):
     lib = dmfe.load()
     p = dmfe.dmfe_params()
     lib.dmfe_default_params(ctypes.byref(p))
-    assert (p.L, p.s, p.precision, p.sparsify, p.integrator, p.rk_switch_dt, p.hi_chunk, p.interp, p.fh_d) == \
-        (513, 4, 0, 1, 0, 0.0, 0, 0, 3)
+    assert (p.L, p.s, p.precision, p.sparsify, p.integrator, p.rk_switch_dt, p.hi_chunk, p.interp, p.fh_d,
+            p.log_r) == (513, 4, 0, 1, 0, 0.0, 0, 0, 3, 0)
     assert p.dt0 == 1e-4 and p.dt_min == 1e-12 and p.grid_t_max == 1e5
 
     def params(**kw):
@@ -122,6 +122,9 @@ def test_defaults_and_host_side_validation_without_gpu(built):
     assert fp(L=257) > fp(L=129) > 0
     assert fp(L=129, history_cap=400) > fp(L=129)
     assert fp(precision="fp64") > fp(precision="df") > fp(precision="fp32")
+    # log-R mode: one table of four log-R coefficients per stored interval and buffer
+    # (history_cap defaults to L; allocations are counted in 512-byte granules)
+    assert 0 <= fp(log_r=True) - fp() - 2 * 129 * 129 * 32 < 2 * 512
     h = ctypes.c_void_p()
     bad = [dict(L=8), dict(s=5), dict(history_cap=8), dict(dt0=0.0), dict(hi_chunk=16), dict(fh_d=4, interp="fh_index")]
     for kw in bad:
@@ -132,6 +135,11 @@ def test_defaults_and_host_side_validation_without_gpu(built):
     for prec in ("df", "fp32"):          # the rational and theta-space stencils need FP64
         prm, keep = params(precision=prec, interp="fh_index")
         assert lib.dmfe_create(ctypes.byref(prm), ctypes.byref(h)) == -8
+        prm, keep = params(precision=prec, log_r=True)   # so does the log-R interpolation
+        assert lib.dmfe_create(ctypes.byref(prm), ctypes.byref(h)) == -8
+    prm, keep = params()
+    prm.log_r = 2
+    assert lib.dmfe_create(ctypes.byref(prm), ctypes.byref(h)) == -1
     prm, keep = params()
     prm.integrator = 7
     assert lib.dmfe_create(ctypes.byref(prm), ctypes.byref(h)) == -1
