@@ -105,7 +105,9 @@ typedef struct {
     int           log_r;        /* 1: interpolate the response history in log R (with the
                                    scaled derivative R'/R) wherever the stencil's values
                                    are positive, linearly elsewhere (App. A); DMFE_FP64
-                                   only (else DMFE_ERR_UNSUPPORTED). Default 0            */
+                                   single solves only (else DMFE_ERR_UNSUPPORTED from
+                                   dmfe_create, dmfe_batch_add, dmfe_server_submit).
+                                   Default 0                                              */
 } dmfe_params;
 
 /* Per-solve counters. */
@@ -252,7 +254,8 @@ int dmfe_batch_create(int max_slots, int max_L, int max_cap, int precision, int 
 void dmfe_batch_destroy(dmfe_batch* b);
 /* Admit a solve into a free slot: creates its solver (allocates; synchronous), targets
  * t_max with tolerance tol. *slot receives the slot. DMFE_ERR_CAPACITY: no free slot;
- * DMFE_ERR_ARG: parameters outside the batch's bounds or precision/stencil mismatch. */
+ * DMFE_ERR_ARG: parameters outside the batch's bounds or precision/stencil mismatch;
+ * DMFE_ERR_UNSUPPORTED: log_r set (log-R interpolation is for single solves). */
 int dmfe_batch_add(dmfe_batch* b, const dmfe_params* p, double t_max, double tol, int* slot);
 /* Release a slot (synchronises, frees its solver). */
 int dmfe_batch_remove(dmfe_batch* b, int slot);
@@ -291,7 +294,8 @@ typedef struct {
 int dmfe_server_start(int max_slots, int max_L, int max_cap, int precision, int s,
                       unsigned long long hbm_budget, int steps_per_round, dmfe_server** out);
 /* Queue a request (parameters copied; thread-safe). *id receives its id. DMFE_ERR_ARG if
- * it can never be admitted (bounds, precision, footprint above the budget). */
+ * it can never be admitted (bounds, precision, footprint above the budget);
+ * DMFE_ERR_UNSUPPORTED for log_r (as dmfe_batch_add). */
 int dmfe_server_submit(dmfe_server* srv, const dmfe_params* p, double t_max, double tol, long long* id);
 /* Move up to max_out finished results into out (thread-safe); *n receives the count. */
 int dmfe_server_poll(dmfe_server* srv, dmfe_result* out, int max_out, int* n);

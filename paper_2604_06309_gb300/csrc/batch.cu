@@ -170,6 +170,8 @@ int dmfe_batch_add(dmfe_batch* b, const dmfe_params* p, double t_max, double tol
     const int cap = p->history_cap ? p->history_cap : p->L;
     if (p->precision != b->precision || p->s != b->s || p->L > b->max_L || cap > b->max_cap) return DMFE_ERR_ARG;
     if (!(tol > 0.0) || !(t_max <= p->grid_t_max * (1.0 + 1e-12))) return DMFE_ERR_ARG;
+    // the batched kernel is compiled without the log-R reads (they cost it registers)
+    if (p->log_r) return DMFE_ERR_UNSUPPORTED;
     int k = 0;
     while (k < b->max_slots && b->slots[k]) ++k;
     if (k == b->max_slots) return DMFE_ERR_CAPACITY;

@@ -94,7 +94,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 // ------------------------------------------------------------------ FP64 variant
 // Body shared by the single-instance and batched kernels: processes units [ub, ue) of
 // solver v with the warps of this CTA (shared memory is reloaded for v).
-template <int SW>
+// LOGR: compiled with the log-R reads (taken where the solver has log-R tables); without
+// it the default kernel carries none of that code.
+template <int SW, bool LOGR>
 __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* __restrict__ row, double t_arg,
                                             int from_state, double* __restrict__ S, int ub, int ue) {
     extern __shared__ __align__(32) unsigned char smraw[];
@@ -106,7 +108,7 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
     const double t = from_state ? st->t_stage : t_arg;
     const dbl4* __restrict__ H = v.hist[act];
     const dbl8* __restrict__ HC = v.hcoef[act];
-    const dbl4* __restrict__ LC = v.lcoef[act];  // log-R mode only (else NULL)
+    const dbl4* __restrict__ LC = LOGR ? v.lcoef[act] : nullptr;  // log-R mode only
     const double* __restrict__ ht = v.ht[act];
     // Slice times with the stage time appended when the stage lies beyond the last slice:
     // the quadratic extension is then the virtual interval n-1 = [t_last, t], whose
@@ -479,12 +481,12 @@ __device__ __forceinline__ void hi_f32_body(const SolverView& v, const double* _
     }
 }
 
-template <int SW>
+template <int SW, bool LOGR>
 __global__ void __launch_bounds__(HI_THREADS, 1) k_hi_f64(SolverView v, const double* __restrict__ row,
                                                        double t_arg, int from_state, double* __restrict__ S) {
     int ub, ue;
     hi_unit_block(v.L, v.hi_chunk, &ub, &ue);
-    hi_f64_body<SW>(v, row, t_arg, from_state, S, ub, ue);
+    hi_f64_body<SW, LOGR>(v, row, t_arg, from_state, S, ub, ue);
 }
 
 template <int SW>
@@ -506,7 +508,8 @@ __global__ void __launch_bounds__(HI_THREADS, 1) k_batch_hi(const BatchTable* __
         __syncthreads();
         const SolverView& v = sview;
         const double* row = v.Y + (size_t)(stg & 1) * 2 * v.L;
-        if (PREC == DMFE_FP64) hi_f64_body<SW>(v, row, 0.0, stg, v.S, lb, le);
+        // (batch slots have no log-R mode: dmfe_batch_add refuses it)
+        if (PREC == DMFE_FP64) hi_f64_body<SW, false>(v, row, 0.0, stg, v.S, lb, le);
         else hi_f32_body<SW>(v, row, 0.0, stg, v.S, lb, le);
     });
 }
@@ -518,16 +521,18 @@ size_t hi_smem_bytes(const SolverView& v) {
 }
 
 template <int SW>
-void* hi_kernel(int precision) {
-    return precision == DMFE_FP64 ? (void*)k_hi_f64<SW> : (void*)k_hi_f32<SW>;
+void* hi_kernel(int precision, bool log_r) {
+    if (precision != DMFE_FP64) return (void*)k_hi_f32<SW>;
+    return log_r ? (void*)k_hi_f64<SW, true> : (void*)k_hi_f64<SW, false>;
 }
 
 void* hi_kernel_for(const SolverView& v) {
+    const bool lr = v.log_r != 0;
     switch (v.s) {
-        case 4: return hi_kernel<4>(v.precision);
-        case 6: return hi_kernel<6>(v.precision);
-        case 8: return hi_kernel<8>(v.precision);
-        case 10: return hi_kernel<10>(v.precision);
+        case 4: return hi_kernel<4>(v.precision, lr);
+        case 6: return hi_kernel<6>(v.precision, lr);
+        case 8: return hi_kernel<8>(v.precision, lr);
+        case 10: return hi_kernel<10>(v.precision, lr);
     }
     return nullptr;
 }

@@ -81,3 +81,19 @@ def test_log_r_needs_fp64():
         with pytest.raises(DMFEError) as e:
             Solver(MIXED_34, 0.5, 33, 100.0, precision=prec, log_r=True)
         assert e.value.code == -8
+
+
+def test_batches_and_servers_refuse_log_r():
+    need_gpu()
+    from paper_2604_06309_gb300 import Batch, DMFEError, Server
+    b = Batch(2, 65, 32)
+    with pytest.raises(DMFEError) as e:
+        b.add(MIXED_34, 0.5, 65, 100.0, 1.0, 1e-8, history_cap=32, log_r=True)
+    assert e.value.code == -8
+    b.add(MIXED_34, 0.5, 65, 100.0, 1.0, 1e-8, history_cap=32)     # the slot is still free
+    b.close()
+    srv = Server(2, 65, 32, hbm_budget=1 << 30)
+    with pytest.raises(DMFEError) as e:
+        srv.submit(MIXED_34, 0.5, 65, 100.0, 1.0, 1e-8, history_cap=32, log_r=True)
+    assert e.value.code == -8
+    srv.stop()
