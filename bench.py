@@ -93,9 +93,15 @@ def parse():
     ap.add_argument("--coefs", default="3:0.5", help="aging: f(q) as power:coefficient,...")
     ap.add_argument("--T", type=float, default=0.0, help="aging: bath temperature")
     ap.add_argument("--tol", type=float, default=1e-12, help="aging: RK tolerance")
+    ap.add_argument("--log-r", action="store_true",
+                    help="with --kernel-only, FP64: logarithmic interpolation of the response history "
+                         "(App. A)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the double-float and FP32-compensated variants of the same workload")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.log_r and not (args.kernel_only and args.precision == "fp64"):
+        ap.error("--log-r measures the FP64 history-integral kernel: use it with --kernel-only")
+    return args
 
 
 def peaks():
@@ -190,8 +196,9 @@ def _run_ours(args, rank, world, dev, stream):
     from paper_2604_06309_gb300.inputs import synthetic_history
     L = args.L
     n0, times = workload(L)
+    log_r = bool(getattr(args, "log_r", False))
     sv = Solver(COEFS, T_BATH, L, GRID_T_MAX, s=4, history_cap=L, precision=args.precision,
-                stream=stream.cuda_stream, integrator=getattr(args, "integrator", "auto"))
+                stream=stream.cuda_stream, integrator=getattr(args, "integrator", "auto"), log_r=log_r)
     S = torch.empty((10, L), dtype=torch.float64, device="cuda")
     flush = torch.empty(int(256 * 2 ** 20), dtype=torch.uint8, device="cuda")
 
@@ -217,16 +224,20 @@ def _run_ours(args, rank, world, dev, stream):
             k_avg = float(np.mean(kt))
             pairs = L * L
             hist_b = {"fp64": 64 * (n0 - 1) * L, "df": 32 * n0 * L, "fp32": 16 * n0 * L}[args.precision]
+            if log_r:
+                hist_b += 32 * (n0 - 1) * L   # the log-R coefficients of every interval
             tab_b = 3 * pairs * {"fp64": 40, "df": 8, "fp32": 4}[args.precision]
             hbm, src = peaks()
             per_pair = {"fp64": FLOP_PER_PAIR_S4, "df": DF_FP32_FLOP_PER_PAIR_S4}.get(args.precision)
-            flops = pairs * per_pair if per_pair else None
+            # (log-R mode: two exponentials per pair, no flop count stated)
+            flops = pairs * per_pair if per_pair and not log_r else None
             print(json.dumps({
                 "metric": "history-integral launches/s", "value": 1.0 / k_avg, "unit": "launches/s",
                 "n_gpus": 1, "higher_is_better": True, "dtype": DTYPES[args.precision], "data": "synthetic",
                 "config": {"workload": "dmfe_history_integrals_dev on a frozen seeded history: L=%d, %d slices on "
                                        "geometric times 1e-2..9e4, s=4, stage time 0.1%% beyond the last slice, "
-                                       "L2 flushed before each launch" % (L, n0)},
+                                       "L2 flushed before each launch%s" %
+                                       (L, n0, ", log-R interpolation" if log_r else ""), "log_r": log_r},
                 "kernel_ms": k_avg * 1e3, "algorithmic_bytes": hist_b + tab_b,
                 "achieved_gbs": (hist_b + tab_b) / k_avg / 1e9,
                 "hbm_frac_of_%s" % src: (hist_b + tab_b) / k_avg / 1e9 / hbm,
