@@ -112,6 +112,27 @@ def test_p2_energy_against_closed_form():
     g.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "df"])
+def test_p2_closed_form_on_the_benchmark_grid(precision):
+    """The full benchmark grid (L = history_cap = 2049, theta grid for t_max = 1e5, s = 4,
+    the timed launch configuration) against the exact p = 2 solution (Sec. 4.2)."""
+    need_gpu()
+    from paper_2604_06309_gb300 import Solver
+    g = Solver({2: 0.5}, 0.0, 2049, 1e5, s=4, history_cap=2049, precision=precision)
+    assert g.integrate(5.0, 1e-10) == 0
+    _, _, _, _, E = g.get_row()
+    # the oracle on the same theta grid family gives |dE| = 4.6e-6 / 2.9e-7 and max |dC|
+    # = 3.4e-5 / 2.2e-6 at L = 129 / 257 (fourth order in 1/L); L = 2049 is three
+    # halvings further
+    assert abs(E - cf.p2_E(5.0)) < 1e-8
+    rng = np.random.default_rng(5)
+    t = rng.uniform(0.5, 5.0, 64)
+    tp = t * rng.uniform(0.0, 1.0, 64)
+    assert np.max(np.abs(g.get_C(t, tp) - cf.p2_C(t, tp))) < 1e-7
+    assert np.max(np.abs(g.get_R(t, tp) - cf.p2_R(t, tp))) < 1e-7
+    g.close()
+
+
 def test_two_time_lookup_matches_oracle():
     need_gpu()
     from paper_2604_06309_gb300 import Solver
