@@ -26,6 +26,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -124,8 +125,8 @@ class Clocks:
 
     def __init__(self, idx):
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench.csv"
+        # the raw samples (the JSON line carries their summary); DMFE_CLOCKS_LOG keeps them
+        self.path = os.environ.get("DMFE_CLOCKS_LOG") or os.path.join(tempfile.gettempdir(), "clocks_bench.csv")
         try:
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(
