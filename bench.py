@@ -40,11 +40,12 @@ GRID_T_MAX = 1e5
 TOL = 1e-8
 # Algorithmic operations per (i, j) pair at stencil width 4, counted from the kernel
 # source (FMA = 2 flops). The Lagrange weights of the three stencils are read from the
-# per-grid tables, not computed per pair. FP64 kernel: A1 32, A2 16, B1 12 (Horner on the
-# interval's monomial Hermite coefficients), B2 (stage time 3, interval coordinate 2, a
-# 4-point stencil of 8 coefficients 64, Horner 12), f' and f'' at two points for the (3+4)
-# model 20, nine weighted products and sums 27.
-FLOP_PER_PAIR_S4 = 32 + 16 + 12 + 81 + 20 + 27
+# per-grid tables, not computed per pair; the A1 and A2 weights carry the quadrature weight
+# nu_i. FP64 kernel: A1 32, A2 16, B1 12 (Horner on the interval's monomial Hermite
+# coefficients), B2 (stage time 2, interval coordinate 2, a 4-point stencil of 8
+# coefficients 64, Horner 12), f' and f'' at two points for the (3+4) model 20, nine
+# weighted products and sums 23.
+FLOP_PER_PAIR_S4 = 32 + 16 + 12 + 80 + 20 + 23
 # Double-float kernel, FP32 flops of the double-float arithmetic: Lagrange weights from the
 # stored positions 3 x 118, B1 110, A1 220, A2 110, B2 713, f' and f'' 210, products and
 # sums 226.

@@ -142,7 +142,8 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
     for (int u = ub + (threadIdx.x >> 5); u < ue; u += (int)(blockDim.x >> 5)) {
         int j, i0, i1;
         hi_unit_range(u, L, chunk, &j, &i0, &i1);
-        const double thj = theta[j], omj = omega[j];
+        // the stage time of B2, tau2 = phi2 t = theta_j t + (omega_j t) theta_i, by one FMA
+        const double thj_t = theta[j] * t, omj_t = omega[j] * t;
         TimeW b1;
         double s1;
         {
@@ -220,8 +221,7 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
             // ---- B2: theta position psi on the slices around phi2 t
             double CB2, RB2;
             {
-                const double thi = theta[i];
-                const double tau2 = (thj + omj * thi) * t;
+                const double tau2 = fma(omj_t, theta[i], thj_t);
                 const long long taub = tbits(tau2);
                 const unsigned char* e = w3r + (size_t)i * WTS;
                 const int b = *reinterpret_cast<const int*>(e);
@@ -278,18 +278,17 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
             }
             const double f1a = fp1(v.poly, CB1), f2a = fp2(v.poly, CB1);
             const double f1b = fp1(v.poly, CB2), f2b = fp2(v.poly, CB2);
-            // the weight nu_i folded into factors shared by several sums
-            const double nui = nu[i];
-            const double nCB1 = nui * CB1, nRB1 = nui * RB1, nKA2 = nui * KA2, nRA2 = nui * RA2;
-            acc[0] += KA1 * nCB1;
-            acc[1] += nKA2 * CB2;
-            acc[2] += DA1 * nRB1;
-            acc[3] += nKA2 * RB2;
-            acc[4] += (f2a * CA1) * nRB1;
-            acc[5] += (nui * f1a) * RA1;
-            acc[6] += f1b * nRA2;
-            acc[7] += (f2b * RB2) * nRA2;
-            acc[8] += (f2a * CB1 + f1a) * nRB1;
+            // the weight nu_i is in the A1 and A2 stencil weights (KA1, DA1, CA1, RA1, KA2,
+            // RA2 carry it); only the last sum, which has no A factor, multiplies by it
+            acc[0] += KA1 * CB1;
+            acc[1] += KA2 * CB2;
+            acc[2] += DA1 * RB1;
+            acc[3] += KA2 * RB2;
+            acc[4] += (f2a * CA1) * RB1;
+            acc[5] += f1a * RA1;
+            acc[6] += f1b * RA2;
+            acc[7] += (f2b * RB2) * RA2;
+            acc[8] += (f2a * CB1 + f1a) * (nu[i] * RB1);
             if (i == 0) c_at_0 = CB1;
         }
         double sums[9];

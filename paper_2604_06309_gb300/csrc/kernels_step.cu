@@ -142,15 +142,19 @@ __device__ void stencil_weights(const SolverView& v, int b, double x, double om,
 }
 
 // Stencil entry of a fractional index x (point complement om): base b = clamp(floor(x) -
-// s/2 + 1, 0, L - s) and the s FP64 weights of the solver's scheme.
-__device__ void write_entry(const SolverView& v, unsigned char* base, size_t idx, double x, double om) {
+// s/2 + 1, 0, L - s) and the s FP64 weights of the solver's scheme, times `scale`.
+__device__ void write_entry(const SolverView& v, unsigned char* base, size_t idx, double x, double om,
+                            double scale = 1.0) {
     const int L = v.L, s = v.s;
     int b = (int)floor(x) - s / 2 + 1;
     b = b < 0 ? 0 : (b > L - s ? L - s : b);
     unsigned char* e = base + idx * (size_t)(8 + 8 * s);
     reinterpret_cast<int*>(e)[0] = b;
     reinterpret_cast<int*>(e)[1] = 0;
-    stencil_weights(v, b, x, om, reinterpret_cast<double*>(e + 8));
+    double* w = reinterpret_cast<double*>(e + 8);
+    stencil_weights(v, b, x, om, w);
+    if (scale != 1.0)
+        for (int k = 0; k < s; ++k) w[k] *= scale;
 }
 
 __global__ void k_tables(SolverView v, double* x1, double* x2, double* x3, uint32_t* p1, uint32_t* p2,
@@ -177,8 +181,10 @@ __global__ void k_tables(SolverView v, double* x1, double* x2, double* x3, uint3
             q3[idx] = df_from_d(c);
         }
         if (v.wt1) {
-            write_entry(v, (unsigned char*)v.wt1, idx, a, oph1);
-            write_entry(v, (unsigned char*)v.wt2, idx, b, oph2);
+            // the A1 and A2 stencils (current row at phi1, phi2) carry the quadrature weight
+            // nu_i of their summation index: every product they enter is weighted by it
+            write_entry(v, (unsigned char*)v.wt1, idx, a, oph1, v.nu[i]);
+            write_entry(v, (unsigned char*)v.wt2, idx, b, oph2, v.nu[i]);
             write_entry(v, (unsigned char*)v.wt3, idx, c, ops);
         }
         if (p1) {
