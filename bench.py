@@ -54,7 +54,7 @@ DF_FP32_FLOP_PER_PAIR_S4 = 354 + 110 + 220 + 110 + 713 + 210 + 226
 # one ncu capture per precision (dram__bytes_read.sum + dram__bytes_write.sum of the first
 # launch inside the timed steps; profiles/traffic_k_hi_L2049_bench_state.md). Set to None
 # whenever the kernel changes until it is measured again.
-TRAFFIC_BYTES = {"fp64": None, "df": 218971136 + 3391744, "fp32": 85981696 + 2500352}
+TRAFFIC_BYTES = {"fp64": 708939520 + 3044608, "df": 218971136 + 3391744, "fp32": 85981696 + 2500352}
 # Nominal per-GPU peaks derived from the unit counts and the 2.07 GHz maximum SM clock:
 # FP64 1.25 TFLOP/s (2 FMA lanes per SM); FP32 152 SMs x 128 lanes x 2 x 2.07e9.
 FP64_PEAK_GFLOPS = 1250.0
