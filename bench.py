@@ -79,7 +79,7 @@ def parse():
                     help="only launch the history-integral kernel (for profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="step",
-                    choices=["step", "batch", "serve", "solve", "aging", "capacity", "quench"],
+                    choices=["step", "batch", "serve", "solve", "aging", "capacity", "quench", "sparsify"],
                     help="step: the headline configuration; batch: 256 independent solves stepped "
                          "together; serve: Poisson-arrival requests with continuous batching")
     ap.add_argument("--window", type=float, default=30.0, help="seconds of batched or served work")
@@ -559,6 +559,41 @@ def batch_requests(n, seed=20260406, Ls=BATCH_LS, tmax_range=(1e3, 1e6)):
     return out
 
 
+def run_sparsify(args):
+    """One sparsification pass (Sec. 3.6) over a full store of L - 6 seeded slices, timed
+    with CUDA events around the call (residuals, selection, compaction, the interval
+    coefficients of the kept slices, and the read-back of the removed mask)."""
+    import torch
+    from paper_2604_06309_gb300 import Solver
+    from paper_2604_06309_gb300.inputs import synthetic_history
+    L = args.L
+    n0, times = workload(L)
+    stream = torch.cuda.Stream()
+    sv = Solver(COEFS, T_BATH, L, GRID_T_MAX, s=4, history_cap=L, precision=args.precision,
+                stream=stream.cuda_stream)
+    C, dC, R, dR = synthetic_history(20260406, times, sv.theta, sv.omega)
+    ts, removed = [], 0
+    for k in range(args.warmup + args.steps):
+        sv.set_history(times, C, dC, R, dR)
+        sv.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mask = sv.sparsify(TOL)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        removed = int(mask.sum())
+    sv.close()
+    avg = float(np.mean(ts))
+    return {"metric": "sparsification passes/s", "value": 1.0 / avg, "unit": "passes/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": DTYPES[args.precision], "data": "synthetic",
+            "config": {"workload": "one sparsification pass over %d seeded slices on geometric times 1e-2..9e4, "
+                                   "L=%d, tol %g" % (n0, L, TOL)},
+            "pass_ms": avg * 1e3, "slices_removed": removed,
+            "history_bytes": 32 * n0 * L}
+
+
 def run_batch(args):
     """Config 4: all requests in one batch, stepped for a fixed wall-clock window."""
     import torch
@@ -760,6 +795,9 @@ def main():
         print(json.dumps(line))
         return
 
+    if args.workload == "sparsify":
+        print(json.dumps(run_sparsify(args)))
+        return
     if args.workload == "batch":
         r = run_batch(args)
         line = {"metric": "instance-stages/s", "value": r["instance_stages_per_s"], "unit": "instance-stages/s",
