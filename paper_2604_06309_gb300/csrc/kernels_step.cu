@@ -599,6 +599,8 @@ __device__ __forceinline__ void sp_residual_body(const SolverView& v, int from_s
         const dbl4* b = H + (size_t)n * L;
         const dbl4* c = H + (size_t)(n + 1) * L;
         double acc = 0.0;
+        // unrolled so that several iterations' loads are in flight (the sum order is kept)
+#pragma unroll 4
         for (int i = lane; i < L; i += 32) {
             const dbl4 A = a[i], B = b[i], Cc = c[i];
             const double wC = herm_int(A.x, A.y, B.x, B.y, h1) + herm_int(B.x, B.y, Cc.x, Cc.y, h2);
@@ -615,7 +617,10 @@ __device__ __forceinline__ void sp_residual_body(const SolverView& v, int from_s
 
 // Greedy scan of Sec. 3.6 (remove n if eps < tol/10, then skip n+1), forced removal of the
 // smallest residual when nothing qualifies, and the compaction map. Single thread: the
-// scan is sequential by definition and runs once per pass.
+// scan is sequential by definition and runs once per pass. It visits every candidate with
+// a skip flag (rather than stepping by two after a removal), so the loads of the residuals
+// do not wait on the decisions and the unrolled loop keeps several in flight; the map
+// (kept slices before each slice) is formed in the same pass.
 __device__ __forceinline__ void sp_select_body(const SolverView& v, int from_step, double tol_arg) {
     DevState* st = v.st;
     if (!sp_active(st, from_step) || threadIdx.x != 0) return;
@@ -627,32 +632,44 @@ __device__ __forceinline__ void sp_select_body(const SolverView& v, int from_ste
         if (from_step) st->status = DMFE_ERR_CAPACITY;
         return;
     }
-    for (int k = 0; k < N; ++k) v.keep[k] = 1;
+    const double thr = tol / 10.0;
+    const double* __restrict__ eps = v.eps_sp;
     int removed = 0;
     double mx = st->max_eps_sparse;
-    for (int k = 1; k <= last;) {
-        if (v.eps_sp[k] < tol / 10.0) {
-            v.keep[k] = 0;
-            ++removed;
-            mx = fmax(mx, v.eps_sp[k]);
-            k += 2;
-        } else {
-            ++k;
-        }
+    v.keep[0] = 1;
+    v.newidx[0] = 0;
+    int c = 1;
+    bool skip = false;
+#pragma unroll 8
+    for (int k = 1; k <= last; ++k) {
+        const double e = eps[k];
+        const bool rm = !skip && e < thr;
+        v.keep[k] = rm ? 0 : 1;
+        v.newidx[k] = c;
+        c += rm ? 0 : 1;
+        removed += rm ? 1 : 0;
+        mx = rm ? fmax(mx, e) : mx;
+        skip = rm;
+    }
+    for (int k = last + 1; k < N; ++k) {
+        v.keep[k] = 1;
+        v.newidx[k] = c++;
     }
     if (removed == 0) {
+        // every slice was kept, so newidx[k] = k; removing m shifts the slices after it
         int m = 1;
-        for (int k = 2; k <= last; ++k)
-            if (v.eps_sp[k] < v.eps_sp[m]) m = k;
+        double em = eps[1];
+#pragma unroll 8
+        for (int k = 2; k <= last; ++k) {
+            const double e = eps[k];
+            if (e < em) { em = e; m = k; }
+        }
         v.keep[m] = 0;
+        for (int k = m + 1; k < N; ++k) v.newidx[k] = k - 1;
+        c = N - 1;
         removed = 1;
-        mx = fmax(mx, v.eps_sp[m]);
+        mx = fmax(mx, em);
         st->forced_removals += 1;
-    }
-    int c = 0;
-    for (int k = 0; k < N; ++k) {
-        v.newidx[k] = c;
-        c += v.keep[k];
     }
     st->max_eps_sparse = mx;
     st->sparsify_passes += 1;
