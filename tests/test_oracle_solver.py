@@ -170,6 +170,39 @@ def test_sparsify_greedy_skip_and_forced_removal():
     assert H3.t[1 + np.argmin(e3[1:H3.N - 11])] not in H4.t
 
 
+def test_sparsify_selection_equals_the_run_parity_rule():
+    """The greedy remove-n-skip-n+1 scan of Sec. 3.6 restated without a scan: within every
+    maximal run of consecutive removable candidates (eps < tol/10, 1 <= n <= N-12) the
+    removed slices are the run's first, third, fifth, ... members. Random breaks of a
+    cubic history give random run patterns."""
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        H = _cubic_history()
+        broken = rng.choice(np.arange(1, H.N - 1), size=rng.integers(1, 8), replace=False)
+        H.C[broken] += 1e-3
+        eps = S.sparsify_residuals(H)
+        last = H.N - 12
+        ok = np.zeros(H.N, dtype=bool)
+        ok[1:last + 1] = eps[1:last + 1] < 1e-9
+        expect = []
+        n = 1
+        while n <= last:
+            if not ok[n]:
+                n += 1
+                continue
+            e = n
+            while e + 1 <= last and ok[e + 1]:
+                e += 1
+            expect += list(range(n, e + 1, 2))
+            n = e + 1
+        H2, _ = S.sparsify_pass(H, 1e-8)
+        got = sorted(np.where(~np.isin(H.t, H2.t))[0])
+        if expect:
+            assert got == expect
+        else:   # nothing removable: one forced removal
+            assert len(got) == 1
+
+
 def test_rejection_reverts_and_halves():
     sv = S.Solver({3: 0.5}, 0.8, L=33, grid_t_max=10.0, dt0=0.5, history_cap=100)
     assert sv.integrate(1.0, 1e-10) == S.OK
