@@ -146,6 +146,14 @@ void dmfe_destroy(dmfe_solver* h);
 /* Grid of Eq. (theta) and the quadrature weights nu of Sec. 3.4 (host arrays of L). */
 int dmfe_grid(dmfe_solver* h, double* theta, double* omega, double* nu);
 
+/* The same grid without a solver or a device (host code only): theta_i of Eq. (theta)
+ * for gamma = -W_{-1}(-1/grid_t_max) and the trade-offs alpha, delta; omega_i = 1 -
+ * theta_i computed without cancellation; nu_i of Sec. 3.4. Caller-owned host arrays of L
+ * (any may be NULL). DMFE_ERR_ARG for L outside [16, 8192], grid_t_max <= e, alpha outside
+ * [0, 1] or delta < 0 (the ranges of dmfe_params). */
+int dmfe_theta_grid(int L, double grid_t_max, double alpha, double delta, double* theta, double* omega,
+                    double* nu);
+
 /* Fractional stencil positions of kernel (a), FP64, [L][L] each, row j = output index:
  * x1 for phi1 = theta_i theta_j, x2 for phi2 = theta_j + (1 - theta_j) theta_i,
  * x3 for psi = theta_j / phi2 (Sec. 3.3). Any pointer may be NULL. */

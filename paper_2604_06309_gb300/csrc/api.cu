@@ -471,6 +471,20 @@ int dmfe_grid(dmfe_solver* h, double* theta, double* omega, double* nu) {
     return DMFE_OK;
 }
 
+int dmfe_theta_grid(int L, double grid_t_max, double alpha, double delta, double* theta, double* omega,
+                    double* nu) {
+    if (L < 16 || L > 8192) return DMFE_ERR_ARG;
+    if (!(grid_t_max > 2.718281828459046) || !std::isfinite(grid_t_max)) return DMFE_ERR_ARG;
+    if (!(alpha >= 0.0 && alpha <= 1.0) || !(delta >= 0.0) || !std::isfinite(delta)) return DMFE_ERR_ARG;
+    std::vector<double> th, om, w;
+    host_theta_grid(L, host_gamma_from_tmax(grid_t_max), alpha, delta, th, om);
+    if (nu) TRY(host_spline_weights(th, w));
+    if (theta) std::memcpy(theta, th.data(), L * sizeof(double));
+    if (omega) std::memcpy(omega, om.data(), L * sizeof(double));
+    if (nu) std::memcpy(nu, w.data(), L * sizeof(double));
+    return DMFE_OK;
+}
+
 int dmfe_tables(dmfe_solver* h, double* x1, double* x2, double* x3) {
     if (!h) return DMFE_ERR_ARG;
     const size_t LL = (size_t)h->v.L * h->v.L;

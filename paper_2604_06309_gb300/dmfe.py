@@ -91,6 +91,7 @@ _SIGS = {
     "dmfe_history_integrals_dev": (_i, [_p, _d, _p, _p, _p]),
     "dmfe_rhs": (_i, [_p, _d, _dp, _dp, _dp, _dp, _dp, _dp]),
     "dmfe_sparsify": (_i, [_p, _d, _ip]),
+    "dmfe_theta_grid": (_i, [_i, _d, _d, _d, _dp, _dp, _dp]),
     "dmfe_stats": (_i, [_p, ctypes.POINTER(dmfe_stats_t)]),
     "dmfe_checkpoint": (_i, [_p, ctypes.c_char_p]),
     "dmfe_restore": (_i, [ctypes.c_char_p, _p, ctypes.POINTER(_p)]),
@@ -247,6 +248,14 @@ def footprint(coefs, T, L, grid_t_max, **kw):
     """Device bytes a solver with these parameters allocates."""
     prm, keep = make_params(coefs, T, L, grid_t_max, **kw)
     return int(load().dmfe_footprint(ctypes.byref(prm)))
+
+
+def theta_grid(L, grid_t_max, alpha=0.0, delta=0.0):
+    """(theta, omega, nu) of Eq. (theta) and Sec. 3.4 from the library's host code."""
+    theta, omega, nu = np.empty(L), np.empty(L), np.empty(L)
+    _check(load().dmfe_theta_grid(int(L), float(grid_t_max), float(alpha), float(delta), _ptr(theta),
+                                  _ptr(omega), _ptr(nu)), "dmfe_theta_grid")
+    return theta, omega, nu
 
 
 class Server:

@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -145,3 +146,30 @@ def test_defaults_and_host_side_validation_without_gpu(built):
     assert lib.dmfe_create(ctypes.byref(prm), ctypes.byref(h)) == -1
     prm, keep = params(grid_t_max=2.0)   # gamma = -W_{-1}(-1/t_max) needs t_max > e
     assert lib.dmfe_create(ctypes.byref(prm), ctypes.byref(h)) == -1
+
+
+@pytest.mark.parametrize("L,t_max,alpha,delta", [(33, 10.0, 0.0, 0.0), (129, 100.0, 0.0, 0.0),
+                                                  (257, 1e4, 0.5, 0.2), (2049, 1e5, 0.0, 0.0),
+                                                  (4097, 1e7, 0.0, 0.0)])
+def test_host_grid_matches_oracle_without_gpu(built, L, t_max, alpha, delta):
+    """The library's host code for Eq. (theta) and the weights of Sec. 3.4 (the grid every
+    solver is built on), called through dmfe_theta_grid on the CPU, against the oracle."""
+    from oracle import grid as og, quadrature as oq
+    from paper_2604_06309_gb300 import theta_grid
+    th, om, nu = theta_grid(L, t_max, alpha, delta)
+    ref_th, ref_om = og.theta_grid(L, og.gamma_from_tmax(t_max), alpha, delta)
+    # numpy's and the C library's exp/atan may differ by an ulp or two; theta takes a few
+    # of them through the quotient of Eq. (theta)
+    assert np.max(np.abs(th - ref_th)) < 2e-15
+    assert np.max(np.abs(om - ref_om) / np.maximum(ref_om, 1e-300)) < 1e-14
+    ref_nu = oq.spline_weights(ref_th)
+    assert np.max(np.abs(nu - ref_nu)) < 1e-13 * max(1.0, np.max(np.abs(ref_nu)) * L)
+
+
+def test_host_grid_rejects_bad_arguments(built):
+    from paper_2604_06309_gb300 import DMFEError, theta_grid
+    for args in [(8, 100.0), (129, 2.0), (129, 100.0, 1.5), (129, 100.0, 0.0, -1.0)]:
+        with pytest.raises(DMFEError) as e:
+            theta_grid(*args)
+        assert e.value.code == -1
+
