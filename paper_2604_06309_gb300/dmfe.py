@@ -309,8 +309,12 @@ class Solver:
                  history_cap=None, dt0=1e-4, dt_min=1e-12, precision="fp64", sparsify=True,
                  stream=None, integrator="auto", switch_dt=0.0, hi_chunk=0, interp="lagrange_index", fh_d=3,
                  log_r=False):
-        """integrator: "auto" (Dormand-Prince, then SSPRK(10,4) once the step reaches
-        switch_dt; 0 = the stability estimate), "dp5" or "ssprk104" (Sec. 3.5)."""
+        """The fields of dmfe_params (include/dmfe.h). precision: "fp64", "df" (double-float)
+        or "fp32" (FP32 with compensated sums). integrator: "auto" (Dormand-Prince, then
+        SSPRK(10,4) once the step reaches switch_dt; 0 = the stability estimate), "dp5" or
+        "ssprk104" (Sec. 3.5). interp: "lagrange_index", "fh_index", "lagrange_theta" or
+        "fh_theta" with Floater-Hormann degree fh_d (Sec. 3.3; all but the first FP64 only).
+        log_r: interpolate the response history in log R where positive (App. A; FP64)."""
         lib = load()
         self._lib = lib
         self.h = _p()
