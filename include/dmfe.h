@@ -223,7 +223,8 @@ int dmfe_rhs(dmfe_solver* h, double t, const double* C_row, const double* R_row,
 
 /* One sparsification pass (Sec. 3.6) on the stored history with tolerance tol, as
  * dmfe_integrate runs it when the store is full. removed (may be NULL, size
- * history_cap) receives 1 for each slice index that was removed. */
+ * history_cap) receives 1 for each slice index that was removed. The candidates are
+ * slices 1 .. n-12, so with n <= 12 stored slices nothing is removed (DMFE_OK). */
 int dmfe_sparsify(dmfe_solver* h, double tol, int* removed);
 
 int dmfe_stats(dmfe_solver* h, dmfe_stats_t* out);
@@ -321,16 +322,22 @@ int dmfe_server_stop(dmfe_server* srv);
  * tol, forced removal of the smallest residual when none qualifies) for a history held
  * by the caller in device memory: t_dev [n] slice times (t[0] = 0, increasing) and
  * C_dev, dC_dev, R_dev, dR_dev row-major [n][L]. removed_dev [n] (device) receives 1 for
- * each slice to remove, else 0. Stream-ordered on `stream` (NULL: the legacy default
- * stream); it does not synchronise. Nothing is allocated: the residuals go to one
- * fixed device array of DMFE_NOALLOC_MAX_SLICES doubles that every GPU loading the
- * library holds until exit. The first call on each device looks up that array's device
- * address (with the device current); make that first call before any stream capture.
- * All calls share the array and it keeps the last call's contents (every value a call
- * reads is written earlier in the same call), so calls that overlap on the GPU -- on
- * different streams, or from different host threads -- race and must be serialised.
+ * each slice to remove, else 0. The candidates are slices 1 .. n-12 (the first slice, the
+ * last one and the ten-slice rollback window are kept), so for n <= 12 nothing is removed
+ * and DMFE_OK is returned -- as dmfe_sparsify does for such a history. Stream-ordered on
+ * `stream` (NULL: the legacy default stream); it does not synchronise. Nothing is
+ * allocated: the residuals go to one fixed device array of DMFE_NOALLOC_MAX_SLICES doubles
+ * that every GPU loading the library holds until exit. A call looks up that array's
+ * device address (with the device current) unless `stream` is capturing, in which case it
+ * uses the address found by an earlier call on the same device: make one call on each
+ * device before capturing one (and again after a device reset). All calls share the array
+ * and it keeps the last call's contents (every value a call reads is written earlier in
+ * the same call), so calls that overlap on the GPU -- on different streams, or from
+ * different host threads -- race and must be serialised.
  * Returns DMFE_ERR_ARG for NULL pointers, n < 1, L < 1, tol <= 0 or
- * n > DMFE_NOALLOC_MAX_SLICES, DMFE_ERR_CUDA if a launch fails. */
+ * n > DMFE_NOALLOC_MAX_SLICES; DMFE_ERR_UNSUPPORTED for a device ordinal >= 64;
+ * DMFE_ERR_CUDA if the address lookup or a launch fails, or if the first call on a device
+ * is made while capturing. */
 #define DMFE_NOALLOC_MAX_SLICES 16384
 int dmfe_sparsify_select_noalloc(const double* t_dev, const double* C_dev, const double* dC_dev,
                                  const double* R_dev, const double* dR_dev, int n, int L,

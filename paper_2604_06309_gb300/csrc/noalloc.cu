@@ -11,8 +11,10 @@
 // The per-slice residuals need scratch memory beyond the inputs and outputs. It lives in
 // one file-scope device array of fixed size, g_sp_scratch, which every GPU that loads
 // this library holds until the process exits. Host code cannot use the array's name as
-// a device address; the first call on each device looks the address up with
-// cudaGetSymbolAddress (with that device current) and caches it.
+// a device address: every call made outside stream capture looks the address up with
+// cudaGetSymbolAddress (with the device current) and caches it per device; a call inside a
+// capture uses the cached address. A device reset reloads the module (the array may move),
+// and the next call outside capture picks up the new address.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -27,13 +29,16 @@ constexpr int kMaxDevices = 64;
 double* g_scratch_addr[kMaxDevices] = {};
 std::mutex g_scratch_mutex;
 
-// Device address of g_sp_scratch on the current device (looked up once per device).
-int scratch_address(double** out) {
+// Device address of g_sp_scratch on the current device: looked up again unless `stream`
+// is capturing (then the address cached by an earlier call on this device is used).
+int scratch_address(cudaStream_t stream, double** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return DMFE_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return DMFE_ERR_UNSUPPORTED;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) return DMFE_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone || !g_scratch_addr[dev]) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_sp_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
@@ -109,10 +114,10 @@ extern "C" int dmfe_sparsify_select_noalloc(const double* t_dev, const double* C
     if (!t_dev || !C_dev || !dC_dev || !R_dev || !dR_dev || !removed_dev) return DMFE_ERR_ARG;
     if (n < 1 || L < 1 || !(tol > 0.0)) return DMFE_ERR_ARG;
     if (n > DMFE_NOALLOC_MAX_SLICES) return DMFE_ERR_ARG;  // beyond the fixed scratch array
-    double* eps = nullptr;
-    int rc = scratch_address(&eps);
-    if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double* eps = nullptr;
+    int rc = scratch_address(s, &eps);
+    if (rc) return rc;
     const int warps_per_cta = 8;
     int ctas = (n + warps_per_cta - 1) / warps_per_cta;
     ctas = ctas < 1 ? 1 : (ctas > 2048 ? 2048 : ctas);

@@ -29,7 +29,7 @@ def _history(L, seed, n_dense):
 
 def _existing_entry(L, hist, tol):
     from paper_2604_06309_gb300 import Solver
-    sv = Solver(MIXED_34, 0.5, L, 1e3, history_cap=len(hist[0]))
+    sv = Solver(MIXED_34, 0.5, L, 1e3, history_cap=max(16, len(hist[0])))
     sv.set_history(*hist)
     removed = sv.sparsify(tol)
     sv.close()
@@ -61,6 +61,25 @@ def test_noalloc_matches_dmfe_sparsify_on_two_calls_in_a_row():
         assert got.shape == expect.shape
         assert np.array_equal(got, expect)
         assert 0 < got.sum() < len(got)
+
+
+def test_noalloc_forced_removal_and_short_history_match_dmfe_sparsify():
+    """Two branches the greedy rule does not reach: with tol = 1e-30 no residual
+    qualifies and both entries force-remove the candidate with the smallest residual;
+    with n <= 12 slices there are no candidates and both remove nothing."""
+    torch = need_gpu()
+    from paper_2604_06309_gb300 import dmfe
+    lib = dmfe.load()
+    L = 65
+    hist = _history(L, 33, 60)      # 121 slices
+    expect = _existing_entry(L, hist, 1e-30)
+    got = _noalloc_entry(torch, lib, L, hist, 1e-30)
+    assert np.array_equal(got, expect)
+    assert got.sum() == 1 and 1 <= int(np.argmax(got)) <= len(got) - 12
+    short = tuple(a[:12] for a in _history(L, 34, 0))
+    expect = _existing_entry(L, short, 1e-8)
+    got = _noalloc_entry(torch, lib, L, short, 1e-8)
+    assert np.array_equal(got, expect) and got.sum() == 0
 
 
 def test_noalloc_rejects_sizes_beyond_its_fixed_scratch():
