@@ -91,6 +91,9 @@ def parse():
     ap.add_argument("--checkpoints", default="1e2,1e3,1e4,1e5", help="solve: times at which to record")
     ap.add_argument("--compare", default="", help="solve: further precisions compared with --precision")
     ap.add_argument("--time-limit", type=float, default=900.0, help="solve: wall seconds per precision")
+    ap.add_argument("--time-limits", default="",
+                    help="solve: per-precision wall seconds, e.g. fp64:1500,df:900 (others: --time-limit)")
+    ap.add_argument("--out", default="", help="solve, aging: also write the JSON result to this file")
     ap.add_argument("--serve-tmax", default="10,100", help="serve: t_max range of the requests (log-uniform)")
     ap.add_argument("--coefs", default="3:0.5", help="aging: f(q) as power:coefficient,...")
     ap.add_argument("--T", type=float, default=0.0, help="aging: bath temperature")
@@ -422,8 +425,12 @@ def run_pure3_quench():
             "rk_steps_per_s": steps / wall, "stages": st["stages"], "sparsify_passes": st["sparsify_passes"]}
 
 
-SOLVE_PAIRS = [(1.0, 0.0), (1.0, 0.5), (1.0, 0.9), (1.0, 0.99), (1.0, 0.999), (0.5, 0.25), (0.9, 0.45),
-               (0.99, 0.5), (0.3, 0.0), (0.7, 0.69)]
+# (t, t') sample points of a checkpoint tc, as multiples of tc: the last slice's row at
+# sixteen ratios t'/t from 0 to 1 - 1e-4, and two-time values between stored slices
+SOLVE_PAIRS = ([(1.0, r) for r in (0.0, 1e-4, 1e-3, 0.01, 0.05, 0.1, 0.2, 0.3, 0.5, 0.7, 0.8, 0.9, 0.97, 0.99,
+                                   0.999, 0.9999)] +
+               [(0.5, 0.25), (0.9, 0.45), (0.99, 0.5), (0.3, 0.0), (0.7, 0.69), (0.1, 0.01), (0.5, 0.49),
+                (0.25, 0.2)])
 
 
 def energy_threshold(coefs):
@@ -432,6 +439,29 @@ def energy_threshold(coefs):
     f1 = sum(c * p for p, c in coefs.items())
     f2 = sum(c * p * (p - 1) for p, c in coefs.items())
     return (f - f1) / np.sqrt(f2) - f * np.sqrt(f2) / f1
+
+
+def exponent_fit(t, slope, t_min=1.0):
+    """Sec. 4.3: the local exponent t d/dt log(E - E_th) converges to -alpha = -2/3 for pure
+    models, and its deviation is a series in t^(-1/3). Least-squares fits over t >= t_min of
+    (a) slope + 2/3 = sum_{i=1..3} a_i t^(-i/3) (the paper's form, limit fixed) and
+    (b) slope = -alpha + sum_{i=1..3} a_i t^(-i/3) (limit free: alpha is then an estimate)."""
+    t, slope = np.asarray(t, float), np.asarray(slope, float)
+    m = (t >= t_min) & np.isfinite(slope)
+    if m.sum() < 6:
+        return None
+    tt, y = t[m], slope[m]
+    basis = np.stack([tt ** (-k / 3.0) for k in (1, 2, 3)], axis=1)
+    a, *_ = np.linalg.lstsq(basis, y + 2.0 / 3.0, rcond=None)
+    ra = y + 2.0 / 3.0 - basis @ a
+    free = np.concatenate([np.ones((len(tt), 1)), basis], axis=1)
+    b, *_ = np.linalg.lstsq(free, y, rcond=None)
+    rb = y - free @ b
+    return {"t_range": [float(tt[0]), float(tt[-1])], "points": int(m.sum()),
+            "fixed_limit": {"alpha": 2.0 / 3.0, "a": [float(x) for x in a],
+                            "rms_residual": float(np.sqrt(np.mean(ra ** 2)))},
+            "free_limit": {"alpha": float(-b[0]), "a": [float(x) for x in b[1:]],
+                           "rms_residual": float(np.sqrt(np.mean(rb ** 2)))}}
 
 
 def run_aging(args):
@@ -443,7 +473,7 @@ def run_aging(args):
     eth = energy_threshold(coefs)
     sv = Solver(coefs, args.T, args.L, args.t_max, s=4, history_cap=args.L, precision=args.precision,
                 integrator=args.integrator)
-    times = np.exp(np.linspace(np.log(1.0), np.log(args.t_max), 41))
+    times = np.exp(np.linspace(np.log(1.0), np.log(args.t_max), 81))
     rec, t0 = [], time.perf_counter()
     for tc in times:
         while True:
@@ -474,6 +504,7 @@ def run_aging(args):
     dE = np.array([r[1] for r in rec]) - eth
     slope = np.gradient(np.log(dE), np.log(t)) if len(t) > 2 else np.array([])
     return {"metric": "local energy exponent", "value": float(slope[-1]) if len(slope) else None,
+            "exponent_fit": exponent_fit(t, slope),
             "unit": "t d log(E - E_th) / dt", "n_gpus": 1, "higher_is_better": False,
             "dtype": DTYPES[args.precision], "data": "synthetic",
             "config": {"workload": "quench of f=%s to T=%g from a random initial state, L=%d, %d-slice store, "
@@ -493,8 +524,10 @@ def run_solve(args):
     from paper_2604_06309_gb300 import Solver
     cps = [float(x) for x in args.checkpoints.split(",") if float(x) <= args.t_max]
     precs = [args.precision] + [p for p in args.compare.split(",") if p and p != args.precision]
+    limits = {a: float(b) for a, b in (x.split(":") for x in args.time_limits.split(",") if x)}
     runs = {}
     for prec in precs:
+        limit = limits.get(prec, args.time_limit)
         sv = Solver(COEFS, T_BATH, args.L, args.t_max, s=4, history_cap=args.L, precision=prec,
                     integrator=args.integrator)
         t0 = time.perf_counter()
@@ -505,7 +538,7 @@ def run_solve(args):
                 st = sv.stats()
                 if st["status"] != 0:
                     raise RuntimeError("%s: device status %d at t = %g" % (prec, st["status"], st["t"]))
-                if st["t"] >= tc or time.perf_counter() - t0 > args.time_limit:
+                if st["t"] >= tc or time.perf_counter() - t0 > limit:
                     break
             wall = time.perf_counter() - t0
             if st["t"] < tc:
@@ -522,7 +555,7 @@ def run_solve(args):
                         "dt": st["dt"], "method": "ssprk104" if st["method"] == 2 else "dp5",
                         "t_switch": st["t_switch"], "E": E, "mu": mu,
                         "C": sv.get_C(t, tp).tolist(), "R": sv.get_R(t, tp).tolist()})
-        runs[prec] = {"checkpoints": rec, "truncated": truncated}
+        runs[prec] = {"checkpoints": rec, "truncated": truncated, "time_limit_s": limit}
         sv.close()
         torch.cuda.synchronize()
     base = runs[precs[0]]["checkpoints"]
@@ -537,8 +570,8 @@ def run_solve(args):
             "n_gpus": 1, "higher_is_better": True, "dtype": DTYPES[args.precision], "data": "synthetic",
             "config": {"workload": "(3+4)-spin T=0.5 quench from t=0 to %g, theta grid L=%d (t_max %g), "
                                    "%d-slice store, s=4, tol 1e-8, integrator %s; wall clock through the C ABI, "
-                                   "truncated at %g s per precision"
-                                   % (args.t_max, args.L, args.t_max, args.L, args.integrator, args.time_limit),
+                                   "truncated at the time limit of each precision"
+                                   % (args.t_max, args.L, args.t_max, args.L, args.integrator),
                        "sample_pairs": SOLVE_PAIRS},
             "runs": runs}
 
@@ -812,11 +845,12 @@ def main():
     if args.workload == "serve":
         print(json.dumps(run_serving(args)))
         return
-    if args.workload == "solve":
-        print(json.dumps(run_solve(args)))
-        return
-    if args.workload == "aging":
-        print(json.dumps(run_aging(args)))
+    if args.workload in ("solve", "aging"):
+        r = run_solve(args) if args.workload == "solve" else run_aging(args)
+        if args.out:
+            with open(args.out, "w") as f:
+                json.dump(r, f)
+        print(json.dumps(r))
         return
     if args.workload == "capacity":
         print(json.dumps(run_capacity(args)))
