@@ -17,8 +17,16 @@ e2e: the same through the public C ABI from the host: per step dmfe_step(1) and 
 dmfe_get_row read of the new row (device -> host), synchronised.
 roofline: the history-integral kernel, timed alone with CUDA events on the same state.
 
---impl reference runs the FP64 CPU oracle on the same workload (a bounded sample of
-output rows per step, scaled to whole steps).
+--impl reference runs the FP64 CPU oracle on the same workload's shape: per step, six
+whole stages of history integrals on a frozen seeded history, rows split over all host
+cores.
+
+The default run adds, at one GPU: the double-float and FP32 variants and SSPRK(10,4)
+steps of the same workload; the small pure 3-spin quench end to end; the measured FP64
+and FP32 FMA rates (the arithmetic roofline denominators); the kernel alone at L = 4097 in
+each precision; short windows of the 256-solve batch in double-float and FP64; a batch of
+small solves that all complete; the scaled serving-capacity run; the oracle on the host
+cores (--no-extras skips the batch, capacity and L = 4097 parts).
 """
 
 import argparse
@@ -50,15 +58,15 @@ FLOP_PER_PAIR_S4 = 32 + 16 + 12 + 80 + 20 + 23
 # stored positions 3 x 118, B1 110, A1 220, A2 110, B2 713, f' and f'' 210, products and
 # sums 226.
 DF_FP32_FLOP_PER_PAIR_S4 = 354 + 110 + 220 + 110 + 713 + 210 + 226
-# DRAM bytes (read + write) of one history-integral launch at this workload's state, from
-# one ncu capture per precision (dram__bytes_read.sum + dram__bytes_write.sum of the first
-# launch inside the timed steps; profiles/traffic_k_hi_L2049_bench_state.md). Set to None
-# whenever the kernel changes until it is measured again.
-TRAFFIC_BYTES = {"fp64": 708939520 + 3044608, "df": 218971136 + 3391744, "fp32": 85981696 + 2500352}
-# Nominal per-GPU peaks derived from the unit counts and the 2.07 GHz maximum SM clock:
-# FP64 1.25 TFLOP/s (2 FMA lanes per SM); FP32 152 SMs x 128 lanes x 2 x 2.07e9.
-FP64_PEAK_GFLOPS = 1250.0
-FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
+# DRAM bytes (read + write) of one history-integral launch at this workload's state come
+# from ncu captures recorded by paper_2604_06309_gb300.traffic (null once a kernel source
+# has changed since its capture).
+# Nominal per-GPU peaks from the unit counts and the 2.07 GHz maximum SM clock, reported
+# beside the measured ones: FP64 1.25 TFLOP/s (2 FMA lanes per SM); FP32 152 SMs x 128
+# lanes x 2 x 2.07e9.
+FP64_NOMINAL_GFLOPS = 1250.0
+FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.07
+_ALU_PEAKS = {}
 LAUNCHES_PER_STEP = 24  # step graph (begin, 6 x [prep, integrals, stage end], 4 sparsify) + begin
 # Lengths of the real stability intervals (|R(-x)| <= 1 on [0, x]) of Dormand-Prince 5
 # and SSPRK(10,4); with the Jacobian bound 4 sqrt(f''(1)) of Sec. 3.5 they give the
@@ -103,6 +111,8 @@ def parse():
                          "(App. A)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the double-float and FP32-compensated variants of the same workload")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batch, capacity and L = 4097 kernel measurements of the default run")
     args = ap.parse_args()
     if args.log_r and not (args.kernel_only and args.precision == "fp64"):
         ap.error("--log-r measures the FP64 history-integral kernel: use it with --kernel-only")
@@ -116,6 +126,26 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def alu_peak(precision):
+    """(GFLOP/s, source) of the pipe that bounds the precision's kernel: the FMA rate
+    measured on this GPU by dmfe_fma_rate (FP64 for the FP64 kernel, FP32 for the
+    double-float and FP32 kernels), measured once per process; nominal if that fails."""
+    bits = 64 if precision == "fp64" else 32
+    if bits not in _ALU_PEAKS:
+        try:
+            from paper_2604_06309_gb300 import fma_rate
+            _ALU_PEAKS[bits] = (fma_rate(bits), "measured (dmfe_fma_rate: FMA chains, CUDA events, burst)")
+        except Exception as e:  # noqa: BLE001
+            _ALU_PEAKS[bits] = ((FP64_NOMINAL_GFLOPS if bits == 64 else FP32_NOMINAL_GFLOPS),
+                                "nominal (measurement failed: %s)" % e)
+    return _ALU_PEAKS[bits]
+
+
+def traffic(precision):
+    from paper_2604_06309_gb300.traffic import lookup
+    return lookup(precision)
 
 
 def workload(L):
@@ -183,6 +213,57 @@ def whole_job_rate(world, steps, max_time):
     return world * steps / max_time
 
 
+def kernel_only(sv, args, L, n0, times, rank, stream, S, flush):
+    """The history-integral kernel alone on a frozen seeded history (its cost depends on
+    the slice-time layout, not on the values): L - 6 slices on geometric times 1e-2 .. 9e4,
+    a stage time 0.1 % beyond the last slice, L2 flushed before each launch."""
+    import torch
+    from paper_2604_06309_gb300.inputs import synthetic_history
+    log_r = bool(getattr(args, "log_r", False))
+    C, dC, R, dR = synthetic_history(20260406 + rank, times, sv.theta, sv.omega)
+    sv.set_history(times, C, dC, R, dR)
+    row = torch.tensor(np.concatenate([C[-1], R[-1]]), dtype=torch.float64, device="cuda")
+    t_stage = float(times[-1]) * (1.0 + 1e-3)
+    kt = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sv.history_integrals_dev(t_stage, row.data_ptr(), S.data_ptr(), stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            kt.append(e0.elapsed_time(e1) * 1e-3)
+    torch.cuda.synchronize()
+    k_avg = float(np.mean(kt))
+    pairs = L * L
+    hist_b = {"fp64": 64 * (n0 - 1) * L, "df": 32 * n0 * L, "fp32": 16 * n0 * L}[args.precision]
+    if log_r:
+        hist_b += 32 * (n0 - 1) * L   # the log-R coefficients of every interval
+    tab_b = 3 * pairs * {"fp64": 40, "df": 8, "fp32": 4}[args.precision]
+    hbm, src = peaks()
+    per_pair = {"fp64": FLOP_PER_PAIR_S4, "df": DF_FP32_FLOP_PER_PAIR_S4}.get(args.precision)
+    # (log-R mode: two exponentials per pair, no flop count stated)
+    flops = pairs * per_pair if per_pair and not log_r else None
+    out = {
+        "metric": "history-integral launches/s", "value": 1.0 / k_avg, "unit": "launches/s",
+        "n_gpus": 1, "higher_is_better": True, "dtype": DTYPES[args.precision], "data": "synthetic",
+        "config": {"workload": "dmfe_history_integrals_dev on a frozen seeded history: L=%d, %d slices on "
+                               "geometric times 1e-2..9e4, s=4, stage time 0.1%% beyond the last slice, "
+                               "L2 flushed before each launch%s" %
+                               (L, n0, ", log-R interpolation" if log_r else ""), "log_r": log_r},
+        "kernel_ms": k_avg * 1e3, "algorithmic_bytes": hist_b + tab_b, "history_bytes": hist_b,
+        "table_bytes": tab_b, "achieved_gbs": (hist_b + tab_b) / k_avg / 1e9,
+        "hbm_frac_of_%s" % src: (hist_b + tab_b) / k_avg / 1e9 / hbm,
+        "gflops": flops / k_avg / 1e9 if flops else None,
+        "pair_evals_per_s": pairs / k_avg}
+    if flops:
+        peak, psrc = alu_peak(args.precision)
+        out["alu_frac"] = {"of": "FP64" if args.precision == "fp64" else "FP32", "peak_gflops": peak,
+                           "peak_source": psrc, "frac": flops / k_avg / 1e9 / peak}
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2604_06309_gb300 import Solver
@@ -208,46 +289,8 @@ def _run_ours(args, rank, world, dev, stream):
     flush = torch.empty(int(256 * 2 ** 20), dtype=torch.uint8, device="cuda")
 
     if args.kernel_only:
-        # frozen seeded history (the kernel's cost depends on the slice-time layout only)
-        C, dC, R, dR = synthetic_history(20260406 + rank, times, sv.theta, sv.omega)
-        sv.set_history(times, C, dC, R, dR)
-        row = torch.tensor(np.concatenate([C[-1], R[-1]]), dtype=torch.float64, device="cuda")
-        # a stage time just beyond the last slice, as for every stage after the first
-        t_stage = float(times[-1]) * (1.0 + 1e-3)
-        kt = []
-        for k in range(args.warmup + args.steps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            sv.history_integrals_dev(t_stage, row.data_ptr(), S.data_ptr(), stream.cuda_stream)
-            e1.record(stream)
-            e1.synchronize()
-            if k >= args.warmup:
-                kt.append(e0.elapsed_time(e1) * 1e-3)
-        torch.cuda.synchronize()
         if rank == 0:
-            k_avg = float(np.mean(kt))
-            pairs = L * L
-            hist_b = {"fp64": 64 * (n0 - 1) * L, "df": 32 * n0 * L, "fp32": 16 * n0 * L}[args.precision]
-            if log_r:
-                hist_b += 32 * (n0 - 1) * L   # the log-R coefficients of every interval
-            tab_b = 3 * pairs * {"fp64": 40, "df": 8, "fp32": 4}[args.precision]
-            hbm, src = peaks()
-            per_pair = {"fp64": FLOP_PER_PAIR_S4, "df": DF_FP32_FLOP_PER_PAIR_S4}.get(args.precision)
-            # (log-R mode: two exponentials per pair, no flop count stated)
-            flops = pairs * per_pair if per_pair and not log_r else None
-            print(json.dumps({
-                "metric": "history-integral launches/s", "value": 1.0 / k_avg, "unit": "launches/s",
-                "n_gpus": 1, "higher_is_better": True, "dtype": DTYPES[args.precision], "data": "synthetic",
-                "config": {"workload": "dmfe_history_integrals_dev on a frozen seeded history: L=%d, %d slices on "
-                                       "geometric times 1e-2..9e4, s=4, stage time 0.1%% beyond the last slice, "
-                                       "L2 flushed before each launch%s" %
-                                       (L, n0, ", log-R interpolation" if log_r else ""), "log_r": log_r},
-                "kernel_ms": k_avg * 1e3, "algorithmic_bytes": hist_b + tab_b,
-                "achieved_gbs": (hist_b + tab_b) / k_avg / 1e9,
-                "hbm_frac_of_%s" % src: (hist_b + tab_b) / k_avg / 1e9 / hbm,
-                "gflops": flops / k_avg / 1e9 if flops else None,
-                "pair_evals_per_s": pairs / k_avg}))
+            print(json.dumps(kernel_only(sv, args, L, n0, times, rank, stream, S, flush)))
         return None
 
     # ---- state: the quench solved from t = 0 until the slice store is full (steady
@@ -333,8 +376,8 @@ def _run_ours(args, rank, world, dev, stream):
 
 
 class OracleSample:
-    """The oracle on the same workload: one stage of history integrals on a sample of
-    output rows, scaled to a whole step (6 stages x L rows)."""
+    """The oracle on the workload's shape: the history integrals of one stage (every
+    output row) on a frozen seeded history of L - 6 slices, L = the workload's grid."""
 
     def __init__(self, L):
         from oracle import integrals as OI
@@ -348,20 +391,73 @@ class OracleSample:
         self.model = Model(COEFS, T_BATH)
         self.t, self.C, self.R = float(times[-1]), C[-1], R[-1]
 
-    def step_time(self, rows):
-        js = np.linspace(0, self.L - 1, rows).astype(int)
+    def rows(self, js):
+        return self.OI.history_integrals(self.model, self.G, self.H, self.t, self.C, self.R, js=js)
+
+
+_ORACLE = None
+
+
+def _oracle_init(L):
+    global _ORACLE
+    _ORACLE = OracleSample(L)
+
+
+def _oracle_rows(js):
+    _ORACLE.rows(js)
+    return len(js)
+
+
+class OraclePool:
+    """Whole oracle stages on the host cores: the output rows of a stage split into blocks
+    over `workers` single-threaded processes (started with spawn, before any GPU work of
+    theirs; each holds its own copy of the grid and the history)."""
+
+    def __init__(self, L, workers):
+        import multiprocessing as mp
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"
+        self.L, self.workers = L, workers
+        self.pool = mp.get_context("spawn").Pool(workers, initializer=_oracle_init, initargs=(L,))
+        self.pool.map(_oracle_rows, [[0]] * workers)  # every worker has built its state
+
+    def stages(self, n):
+        """Seconds for n whole stages (every output row of each)."""
+        parts = [p.tolist() for p in np.array_split(np.arange(self.L), 4 * self.workers)]
         t0 = time.perf_counter()
-        self.OI.history_integrals(self.model, self.G, self.H, self.t, self.C, self.R, js=js)
-        el = time.perf_counter() - t0
-        return el * (self.L / rows) * 6, el
+        for _ in range(n):
+            done = sum(self.pool.map(_oracle_rows, parts))
+            assert done == self.L
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
-def cpu_baseline(L, rows=512):
-    o = OracleSample(L)
-    per_step, el = o.step_time(rows)
-    return {"value": 1.0 / per_step, "unit": "RK steps/s", "cores": 1, "kind": "oracle",
-            "sample": "history integrals of %d of %d output rows for one stage (%.1f s of CPU), "
-                      "scaled to all rows and 6 stages per step" % (rows, L, el)}
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(L):
+    """The oracle timed on whole stages: one Dormand-Prince step (6 stages, every output
+    row) on all host cores, and one stage on one core, on the workload's shape."""
+    cores = host_cores()
+    allc = OraclePool(L, cores)
+    t_step = allc.stages(6)
+    allc.close()
+    one = OraclePool(L, 1)
+    t_stage1 = one.stages(1)
+    one.close()
+    return {"value": 1.0 / t_step, "unit": "RK steps/s", "cores": cores, "kind": "oracle",
+            "sample": "one whole step: 6 stages of history integrals over all %d output rows on a frozen "
+                      "seeded history of %d slices (the workload's shape), rows split over %d processes "
+                      "(%.1f s)" % (L, L - 6, cores, t_step),
+            "one_thread": {"value": 1.0 / (6 * t_stage1), "unit": "RK steps/s", "cores": 1,
+                           "sample": "one whole stage on one core (%.1f s), times 6 stages" % t_stage1}}
 
 
 DTYPES = {"fp64": "f64", "fp32": "f32+f64", "df": "f32x2 (double-float)+f64"}
@@ -369,29 +465,33 @@ VARIANT_NAMES = {"fp64": "fp64", "df": "double_float", "fp32": "fp32_compensated
 
 
 def roofline(precision, res):
+    """The history-integral kernel against the resource that bounds it: the FP64 pipe (FP64
+    kernel), the FP32 pipes (double-float kernel; FP32 flops of its arithmetic), HBM (FP32
+    kernel). Peaks: measured on this GPU (FMA loop; MEASURED_PEAKS.json for HBM)."""
     hbm, src = peaks()
     bh, bt, bio = res["bytes"]
     k = res["k_avg"]
     pairs = res["pairs"]
-    if precision == "fp64":
-        ach = pairs * FLOP_PER_PAIR_S4 / k / 1e9
-        return {"kernel": "k_hi_f64 (history integrals)", "bound": "alu", "achieved": ach,
-                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": ach / FP64_PEAK_GFLOPS,
-                "traffic": TRAFFIC_BYTES["fp64"],
-                "peak_source": "nominal FP64 (unit counts x clock)", "algorithmic_bytes": bh + bt + bio,
-                "hbm_frac_of_%s" % src: (bh + bt + bio) / k / 1e9 / hbm, "kernel_ms": k * 1e3}
-    if precision == "df":
-        ach = pairs * DF_FP32_FLOP_PER_PAIR_S4 / k / 1e9
-        return {"kernel": "k_hi_df (history integrals)", "bound": "alu", "achieved": ach,
-                "peak": FP32_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": ach / FP32_PEAK_GFLOPS,
-                "traffic": TRAFFIC_BYTES["df"],
-                "peak_source": "nominal FP32 (unit counts x clock)", "algorithmic_bytes": bh + bt + bio,
-                "fp64_equivalent_gflops": pairs * FLOP_PER_PAIR_S4 / k / 1e9,
-                "hbm_frac_of_%s" % src: (bh + bt + bio) / k / 1e9 / hbm, "kernel_ms": k * 1e3}
-    ach = (bh + bt + bio) / k / 1e9
-    return {"kernel": "k_hi_f32 (history integrals)", "bound": "hbm", "achieved": ach, "peak": hbm,
-            "unit": "GB/s", "frac": ach / hbm, "traffic": TRAFFIC_BYTES["fp32"], "peak_source": src,
-            "algorithmic_bytes": bh + bt + bio, "history_bytes": bh, "table_bytes": bt, "kernel_ms": k * 1e3}
+    alg = bh + bt + bio
+    common = {"traffic": traffic(precision), "algorithmic_bytes": alg, "history_bytes": bh, "table_bytes": bt,
+              "io_bytes": bio, "hbm_frac_of_%s" % src: alg / k / 1e9 / hbm, "kernel_ms": k * 1e3}
+    if precision in ("fp64", "df"):
+        per_pair = FLOP_PER_PAIR_S4 if precision == "fp64" else DF_FP32_FLOP_PER_PAIR_S4
+        peak, psrc = alu_peak(precision)
+        ach = pairs * per_pair / k / 1e9
+        out = {"kernel": "k_hi_%s (history integrals)" % ("f64" if precision == "fp64" else "df"), "bound": "alu",
+               "achieved": ach, "peak": peak, "unit": "GFLOP/s", "frac": ach / peak, "peak_source": psrc,
+               "flops_per_pair": per_pair,
+               "nominal_peak": FP64_NOMINAL_GFLOPS if precision == "fp64" else FP32_NOMINAL_GFLOPS}
+        if precision == "df":
+            out["fp64_equivalent_gflops"] = pairs * FLOP_PER_PAIR_S4 / k / 1e9
+        out.update(common)
+        return out
+    ach = alg / k / 1e9
+    out = {"kernel": "k_hi_f32 (history integrals)", "bound": "hbm", "achieved": ach, "peak": hbm,
+           "unit": "GB/s", "frac": ach / hbm, "peak_source": src}
+    out.update(common)
+    return out
 
 
 def solver_info(res):
@@ -689,6 +789,55 @@ def run_batch(args):
     return res
 
 
+def run_batch_complete(args, precision, n_req=64, Ls=(129, 257), tmax_range=(1e2, 1e3), seed=20260406,
+                       window=90.0, single_window=30.0):
+    """Completed solves/s of a batch (config 4's mix of T and lambda on small grids with
+    t_max log-uniform in [1e2, 1e3], so that every member finishes): all n_req solves admitted
+    at once into one batch and stepped until each reaches its t_max; against the same
+    requests solved one at a time by the plain FP64 solver (one dmfe_integrate each, for a
+    fixed wall window), with E compared on every request finished by both."""
+    import torch
+    from paper_2604_06309_gb300 import Batch, Solver
+    reqs = batch_requests(n_req, seed=seed + 3, Ls=Ls, tmax_range=tmax_range)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = Batch(n_req, max(Ls), max(Ls), precision=precision, stream=stream.cuda_stream)
+        for r in reqs:
+            b.add(r["coefs"], r["T"], r["L"], r["t_max"], r["t_max"], TOL, history_cap=r["L"])
+        t0 = time.perf_counter()
+        running = n_req
+        while running > 0 and time.perf_counter() - t0 < window:
+            b.step(16)
+            status, _, running = b.poll()
+        wall = time.perf_counter() - t0
+        status, tcur, running = b.poll()
+        E = {}
+        for k in range(n_req):
+            if status[k] == 1:
+                E[k] = b.solver(k).get_row()[4]
+        b.close()
+    done = len(E)
+    seq, t1 = {}, time.perf_counter()
+    for k, r in enumerate(reqs):
+        if time.perf_counter() - t1 > single_window:
+            break
+        sv = Solver(r["coefs"], r["T"], r["L"], r["t_max"], history_cap=r["L"], precision="fp64")
+        if sv.integrate(r["t_max"], TOL) == 0:
+            seq[k] = sv.get_row()[4]
+        sv.close()
+    seq_wall = time.perf_counter() - t1
+    both = [k for k in seq if k in E]
+    rate, seq_rate = done / wall, len(seq) / seq_wall
+    return {"workload": "%d solves, T~U[0.3,1], lambda~U[0,1], L=cap~U{%s}, t_max~logU[%g,%g], tol 1e-8, "
+                        "one batch stepped until all finish" % (n_req, ",".join(map(str, Ls)), *tmax_range),
+            "precision": precision, "completed": done, "failed": int(sum(1 for x in status[:n_req] if -100 < x < 0)),
+            "wall_s": wall, "completed_solves_per_s": rate,
+            "single_fp64_completed": len(seq), "single_fp64_wall_s": seq_wall,
+            "single_fp64_solves_per_s": seq_rate, "gain_vs_single_fp64": rate / seq_rate if seq_rate else None,
+            "requests_compared": len(both),
+            "max_abs_dE_vs_single_fp64": max((abs(E[k] - seq[k]) for k in both), default=None)}
+
+
 def run_capacity(args, n_req=256, seed=20260406):
     """Solves/s of the serving loop when it is never idle: n_req requests of the scaled
     serving mix (L~U{65,129,257}, t_max~logU[10,100]) are all queued at once and served
@@ -805,6 +954,64 @@ def run_serving(args, rate=20.0, seed=20260406):
             "clocks": clk}
 
 
+def run_extras(args, rank):
+    """The default run's further measurements (one GPU): each guarded, so that one failure
+    is reported in the line instead of losing the headline."""
+    import torch
+    out = {}
+
+    def guarded(key, fn):
+        try:
+            out[key] = fn()
+        except Exception as e:  # noqa: BLE001
+            out[key] = {"error": "%s: %s" % (type(e).__name__, e)}
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
+    def k4097():
+        from paper_2604_06309_gb300 import Solver
+        res = {}
+        L = 4097
+        n0, times = workload(L)
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            S = torch.empty((10, L), dtype=torch.float64, device="cuda")
+            flush = torch.empty(int(256 * 2 ** 20), dtype=torch.uint8, device="cuda")
+            for prec in ("fp64", "df", "fp32"):
+                a2 = argparse.Namespace(**vars(args))
+                a2.precision, a2.log_r = prec, False
+                sv = Solver(COEFS, T_BATH, L, GRID_T_MAX, s=4, history_cap=L, precision=prec,
+                            stream=stream.cuda_stream)
+                r = kernel_only(sv, a2, L, n0, times, rank, stream, S, flush)
+                sv.close()
+                res[VARIANT_NAMES[prec]] = {k: r[k] for k in ("kernel_ms", "pair_evals_per_s", "algorithmic_bytes",
+                                                            "history_bytes", "table_bytes", "achieved_gbs",
+                                                            "gflops") if k in r}
+                res[VARIANT_NAMES[prec]].update({k: v for k, v in r.items() if k.startswith("hbm_frac")
+                                                 or k == "alu_frac"})
+        return res
+
+    def batch(prec, window):
+        a2 = argparse.Namespace(**vars(args))
+        a2.precision, a2.window = prec, window
+        r = run_batch(a2)
+        r.pop("clocks", None)
+        return r
+
+    guarded("kernel_only_L4097", k4097)
+    guarded("batch_config4_double_float", lambda: batch("df", 10.0))
+    guarded("batch_config4_fp64", lambda: batch("fp64", 10.0))
+    guarded("batch_completing_double_float", lambda: run_batch_complete(args, "df"))
+
+    def capacity():
+        a2 = argparse.Namespace(**vars(args))
+        a2.precision, a2.window = "df", 30.0
+        return run_capacity(a2)["capacity"]
+
+    guarded("capacity_double_float", capacity)
+    return out
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -816,14 +1023,18 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        o = OracleSample(args.L)
-        steps_t = [o.step_time(64)[0] for _ in range(args.warmup + args.steps)]
+        cores = host_cores()
+        pool = OraclePool(args.L, cores)
+        steps_t = [pool.stages(6) for _ in range(args.warmup + args.steps)]
+        pool.close()
         v = 1.0 / float(np.mean(steps_t[args.warmup:]))
         line = {"impl": "reference", "metric": "RK steps/s", "value": v, "unit": "RK steps/s", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-                "cpu_baseline": {"value": v, "unit": "RK steps/s", "cores": 1, "kind": "oracle",
-                                 "sample": "per step: history integrals of 64 of %d output rows, one stage, scaled to 6 stages x all rows" % args.L},
+                "cpu_baseline": {"value": v, "unit": "RK steps/s", "cores": cores, "kind": "oracle",
+                                 "sample": "per step: 6 whole stages of history integrals (all %d output rows) on "
+                                           "a frozen seeded history of %d slices, rows split over %d processes"
+                                           % (args.L, args.L - 6, cores)},
                 "e2e": {"value": v, "unit": "RK steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -908,6 +1119,10 @@ def main():
         line["variants"] = variants
     if not args.no_variants and world == 1:
         line["pure3_quench"] = run_pure3_quench()
+    if not args.no_extras and world == 1:
+        line["alu_peaks_gflops"] = {"fp64": alu_peak("fp64")[0], "fp32": alu_peak("fp32")[0],
+                                    "source": alu_peak("fp64")[1]}
+        line["extras"] = run_extras(args, rank)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(L)
     print(json.dumps(line))

@@ -312,6 +312,17 @@ int dmfe_server_stats(dmfe_server* srv, dmfe_server_stats_t* out);
 /* Stop the worker (running solves are abandoned) and free everything. */
 int dmfe_server_stop(dmfe_server* srv);
 
+/* ---- measurement ------------------------------------------------------------------
+ * The paper has no counterpart: a measurement utility for the arithmetic rooflines of
+ * the history-integral kernels (FP64 kernel: FP64 pipe; double-float and FP32 kernels:
+ * FP32 pipes). Measures the fused multiply-add rate of the current device in FP64
+ * (bits = 64) or FP32 (bits = 32): independent FMA chains on four 256-thread CTAs per SM,
+ * one launch sized to about 80 ms, timed with CUDA events on a private stream, best of
+ * three; *gflops receives the rate in GFLOP/s (an FMA counts 2). Synchronous; allocates
+ * and frees a small output buffer; changes no clock or other setting of the GPU.
+ * DMFE_ERR_ARG for other bit widths or a NULL pointer, DMFE_ERR_OOM, DMFE_ERR_CUDA. */
+int dmfe_fma_rate(int bits, double* gflops);
+
 /* ---- allocation-free entry point -------------------------------------------------
  * The paper has no counterpart: this serves callers of the library that cannot call
  * cudaMalloc -- processes whose device memory another framework has reserved up front,

@@ -5,4 +5,4 @@ The computation lives in libdmfe.so (C ABI, include/dmfe.h); ``dmfe`` is its cty
 binding and ``inputs`` holds the seeded synthetic input generators.
 """
 
-from .dmfe import Batch, Server, Solver, DMFEError, footprint, load, theta_grid  # noqa: F401
+from .dmfe import Batch, Server, Solver, DMFEError, fma_rate, footprint, load, theta_grid  # noqa: F401

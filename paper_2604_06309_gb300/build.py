@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libdmfe.so")
 
-SOURCES = ["kernels_hi.cu", "kernels_df.cu", "kernels_step.cu", "api.cu", "host_grid.cpp", "noalloc.cu", "batch.cu", "server.cu", "graph.cu"]
+SOURCES = ["kernels_hi.cu", "kernels_df.cu", "kernels_step.cu", "api.cu", "host_grid.cpp", "noalloc.cu", "batch.cu", "server.cu", "graph.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + os.path.join(ROOT, "include")]

@@ -111,6 +111,7 @@ _SIGS = {
     "dmfe_server_stats": (_i, [_p, ctypes.POINTER(dmfe_server_stats_t)]),
     "dmfe_server_stop": (_i, [_p]),
     "dmfe_sparsify_select_noalloc": (_i, [_p, _p, _p, _p, _p, _i, _i, _d, _p, _p]),
+    "dmfe_fma_rate": (_i, [_i, _dp]),
 }
 
 _lib = None
@@ -248,6 +249,13 @@ def footprint(coefs, T, L, grid_t_max, **kw):
     """Device bytes a solver with these parameters allocates."""
     prm, keep = make_params(coefs, T, L, grid_t_max, **kw)
     return int(load().dmfe_footprint(ctypes.byref(prm)))
+
+
+def fma_rate(bits):
+    """Measured FP64 (bits = 64) or FP32 (bits = 32) FMA rate of the current device, GFLOP/s."""
+    g = _d()
+    _check(load().dmfe_fma_rate(int(bits), ctypes.byref(g)), "dmfe_fma_rate")
+    return g.value
 
 
 def theta_grid(L, grid_t_max, alpha=0.0, delta=0.0):
