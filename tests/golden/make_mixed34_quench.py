@@ -1,13 +1,17 @@
-"""Writes mixed34_T0.5_L2049.json: the oracle's solve of the mixed (3+4)-spin quench
-(f = (q^3 + q^4)/4, T = 0.5, random initial condition, Secs. 2.1 and 3.1-3.6) on the
-benchmark grid (L = 2049 for grid t_max = 1e5, s = 4, 2049-slice store, tolerance 1e-8),
-from t = 0 to t = 1, with the state at t = 0.1 and t = 1: slice times, counters, E, mu,
-every eighth column and the last 32 columns of the final C and R rows, and two-time values.
+"""Writes mixed34_T0.5_L<L>.json: the oracle's solve of the mixed (3+4)-spin quench
+(f = (q^3 + q^4)/4, T = 0.5, random initial condition, Secs. 2.1 and 3.1-3.6) on one of
+the benchmark grids, s = 4, a store of L slices, tolerance 1e-8, from t = 0:
+
+  L = 2049 (grid t_max 1e5): states at t = 0.1 and t = 1 (241 and 464 steps);
+  L = 4097 (grid t_max 1e7): states at t = 0.005 and t = 0.02 (a few dozen and ~110 steps).
+
+Each state holds the slice times, counters, E, mu, every eighth column and the last 32
+columns of the final C and R rows, and two-time values.
 
 Only the oracle is called. Its history integrals are split over output rows between
 worker processes (rows are independent; each row's sums are the oracle's own). Run from
-the repository root (about half an hour on 8 cores):
-    python tests/golden/make_mixed34_L2049.py [workers]
+the repository root (L = 2049: about an hour on 8 cores; L = 4097: about as long):
+    python tests/golden/make_mixed34_quench.py L [workers]
 """
 import json
 import multiprocessing as mp
@@ -22,8 +26,12 @@ sys.path.insert(0, ROOT)
 from oracle import integrals as OI  # noqa: E402
 from oracle import solver as OS  # noqa: E402
 
-CASE = dict(coefs={3: 0.25, 4: 0.25}, T=0.5, L=2049, grid_t_max=1e5, s=4, history_cap=2049, tol=1e-8)
-CHECKPOINTS = [0.1, 1.0]
+CASES = {
+    2049: (dict(coefs={3: 0.25, 4: 0.25}, T=0.5, L=2049, grid_t_max=1e5, s=4, history_cap=2049, tol=1e-8),
+           [0.1, 1.0]),
+    4097: (dict(coefs={3: 0.25, 4: 0.25}, T=0.5, L=4097, grid_t_max=1e7, s=4, history_cap=4097, tol=1e-8),
+           [0.005, 0.02]),
+}
 PAIRS = [(1.0, 0.0), (1.0, 0.5), (1.0, 0.9), (1.0, 0.99), (0.8, 0.3), (0.6, 0.59), (0.5, 0.1),
          (0.3, 0.0), (0.9, 0.45), (0.75, 0.7)]
 
@@ -40,8 +48,9 @@ def _rows(args):
 
 
 def main():
-    workers = int(sys.argv[1]) if len(sys.argv) > 1 else os.cpu_count()
-    c = CASE
+    L = int(sys.argv[1])
+    workers = int(sys.argv[2]) if len(sys.argv) > 2 else os.cpu_count()
+    c, checkpoints = CASES[L]
     pool = mp.get_context("spawn").Pool(workers)
 
     def parallel(model, grid, hist, t, C, R, js=None, j_chunk=256):
@@ -58,7 +67,7 @@ def main():
     cols = columns(c["L"])
     out = {"case": {k: (v if k != "coefs" else {str(p): q for p, q in v.items()}) for k, v in c.items()},
            "columns": cols, "checkpoints": []}
-    for tc in CHECKPOINTS:
+    for tc in checkpoints:
         st = sv.integrate(tc, c["tol"])
         assert st == OS.OK
         t = np.array([a * tc for a, _ in PAIRS])
@@ -74,7 +83,7 @@ def main():
         })
         print("t = %g: %d steps" % (tc, sv.stats["steps_accepted"]), flush=True)
     pool.close()
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "mixed34_T0.5_L2049.json")
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "mixed34_T0.5_L%d.json" % L)
     with open(path, "w") as f:
         json.dump(out, f, indent=0)
         f.write("\n")

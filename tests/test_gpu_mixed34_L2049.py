@@ -1,7 +1,7 @@
 """The benchmark solve itself -- the mixed (3+4)-spin quench, T = 0.5, on the L = 2049 grid
 for t_max = 1e5 with a 2049-slice store, s = 4, tol 1e-8 -- on the device from t = 0,
 compared at t = 0.1 and t = 1 with the oracle's solve stored in
-tests/golden/mixed34_T0.5_L2049.json (written by tests/golden/make_mixed34_L2049.py, which
+tests/golden/mixed34_T0.5_L2049.json (written by tests/golden/make_mixed34_quench.py 2049, which
 calls only the oracle): identical step decisions, and C, R, E, mu within 1e-9."""
 import json
 import os
