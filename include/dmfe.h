@@ -83,8 +83,9 @@ typedef struct {
     int           history_cap;  /* stored slices, >= 16 (default L)                        */
     double        dt0, dt_min;  /* initial and minimal step (defaults 1e-4, 1e-12)         */
     int           precision;    /* DMFE_FP64, DMFE_FP32_COMPENSATED or DMFE_DOUBLE_FLOAT   */
-    int           sparsify;     /* 1: sparsification pass whenever the store is full (default);
-                                   0: off (a full store ends the run with DMFE_ERR_CAPACITY) */
+    int           sparsify;     /* 1: sparsification round whenever the store is full (default);
+                                   0: off (a full store ends the run with DMFE_ERR_CAPACITY;
+                                   sparsify_every rounds still run)                       */
     void*         stream;       /* cudaStream_t for all work; NULL: the solver's own stream */
     int           integrator;   /* DMFE_RK_AUTO (default), DMFE_RK_DP5 or DMFE_RK_SSPRK104  */
     double        rk_switch_dt; /* DMFE_RK_AUTO: controller step at which SSPRK(10,4) takes
@@ -108,6 +109,17 @@ typedef struct {
                                    single solves only (else DMFE_ERR_UNSUPPORTED from
                                    dmfe_create, dmfe_batch_add, dmfe_server_submit).
                                    Default 0                                              */
+    int           sparsify_every; /* P > 0: a sparsification round also after every P-th
+                                   accepted step (after its slice is appended), besides the
+                                   rounds on a full store; 0 (default): full store only.
+                                   Such a round never forces a removal (Sec. 3.6)          */
+    int           sparsify_passes; /* passes per round, 1..8 (0 counts as 1; default 1): the
+                                   user's control of the degree of sparsification (Sec. 3.6,
+                                   last paragraph). Each pass repeats the scan on the history
+                                   the previous pass left. On a full store the first pass may
+                                   force a removal and the accepted slice is appended after
+                                   it, before the further passes. Batch slots and served
+                                   requests take 1 (else DMFE_ERR_UNSUPPORTED)              */
 } dmfe_params;
 
 /* Per-solve counters. */

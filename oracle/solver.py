@@ -224,8 +224,11 @@ def sparsify_residuals(hist):
     return eps
 
 
-def sparsify_pass(hist, tol, stats=None):
-    """One pass of Sec. 3.6 on a full store; returns the thinned history."""
+def sparsify_pass(hist, tol, stats=None, force=True):
+    """One pass of Sec. 3.6; returns (thinned history, whether the pass ran). A pass runs
+    when there is at least one candidate (slices 1 .. N-12). force: when no candidate
+    qualifies, remove the one with the smallest residual (a pass on a full store must
+    free a slot); without it such a pass removes nothing."""
     N = hist.N
     last = N - 12
     if last < 1:
@@ -243,7 +246,7 @@ def sparsify_pass(hist, tol, stats=None):
             n += 2
         else:
             n += 1
-    if removed == 0:
+    if removed == 0 and force:
         m = 1 + int(np.argmin(eps[1:last + 1]))
         keep[m] = False
         removed = 1
@@ -261,10 +264,17 @@ class Solver:
 
     def __init__(self, coefs, T, L, grid_t_max, s=4, beta0=0.0, alpha=0.0, delta=0.0,
                  history_cap=None, dt0=1e-4, dt_min=1e-12, sparsify=True, integrator="auto",
-                 switch_dt=0.0, interp="lagrange_index", fh_d=3, log_r=False):
+                 switch_dt=0.0, interp="lagrange_index", fh_d=3, log_r=False, sparsify_every=0,
+                 sparsify_passes=1):
         """integrator: "dp5" (Dormand-Prince throughout), "ssprk104" (SSPRK(10,4)
         throughout) or "auto" (Dormand-Prince, then SSPRK(10,4) once dt reaches
-        switch_dt; switch_dt = 0 takes the stability estimate switch_dt_auto)."""
+        switch_dt; switch_dt = 0 takes the stability estimate switch_dt_auto).
+
+        Sparsification (Sec. 3.6; the user sets the number of passes, reading R16): a
+        round of sparsify_passes passes runs whenever the store is full (sparsify=True)
+        and, if sparsify_every = P > 0, after every P-th accepted step. The first pass of
+        a full-store round may force a removal; the accepted slice is appended after it,
+        before the round's further passes. A periodic round runs after the append."""
         from .model import Model
         self.model = Model(coefs, T, beta0)
         self.grid = Grid(L, grid_t_max, s, alpha, delta, interp=interp, fh_d=fh_d, log_r=log_r)
@@ -274,6 +284,8 @@ class Solver:
         self.dt = float(dt0)
         self.dt_min = float(dt_min)
         self.sparsify = sparsify
+        self.sparsify_every = int(sparsify_every)
+        self.sparsify_passes = max(1, int(sparsify_passes))
         if integrator not in ("dp5", "ssprk104", "auto"):
             raise ValueError("integrator must be dp5, ssprk104 or auto")
         self.integrator = integrator
@@ -328,14 +340,20 @@ class Solver:
             else:
                 self.log.append((t0, h, eps, True))
                 self.stats["steps_accepted"] += 1
+                passes = 0
                 if self.hist.N >= self.cap:
                     if not self.sparsify:
                         return ERR_CAPACITY
                     self.hist, ran = sparsify_pass(self.hist, tol, self.stats)
                     if not ran:
                         return ERR_CAPACITY
+                    passes = self.sparsify_passes - 1
+                elif self.sparsify_every > 0 and self.stats["steps_accepted"] % self.sparsify_every == 0:
+                    passes = self.sparsify_passes
                 t1 = t0 + h if h < t_max - t0 else t_max
                 self.hist = self.hist.append(t1, y_new[:L], k7[:L], y_new[L:], k7[L:])
+                for _ in range(passes):
+                    self.hist, _ = sparsify_pass(self.hist, tol, self.stats, force=False)
                 if eps > tol:
                     self.dt *= 0.9
                 elif eps < 0.5 * tol:

@@ -128,6 +128,8 @@ int validate(const dmfe_params* p) {
     // the logarithmic response interpolation is built into the FP64 path's coefficient tables
     if (p->log_r != 0 && p->log_r != 1) return DMFE_ERR_ARG;
     if (p->log_r && p->precision != DMFE_FP64) return DMFE_ERR_UNSUPPORTED;
+    if (p->sparsify_every < 0 || p->sparsify_passes < 0 || p->sparsify_passes > kMaxSparsifyPasses)
+        return DMFE_ERR_ARG;
     return DMFE_OK;
 }
 
@@ -178,6 +180,8 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
     v.cap = cap;
     v.precision = pin->precision;
     v.sparsify = pin->sparsify ? 1 : 0;
+    v.sp_every = pin->sparsify_every;
+    v.sp_passes = pin->sparsify_passes < 1 ? 1 : pin->sparsify_passes;
     v.T = pin->T;
     v.beta0 = pin->beta0;
     v.rk_switch_dt = switch_dt_for(&h->p);
@@ -381,6 +385,8 @@ void dmfe_default_params(dmfe_params* p) {
     p->hi_chunk = 0;
     p->interp = DMFE_INTERP_LAGRANGE_INDEX;
     p->fh_d = 3;
+    p->sparsify_every = 0;
+    p->sparsify_passes = 1;
 }
 
 const char* dmfe_strerror(int code) {
@@ -628,6 +634,7 @@ int dmfe_set_history(dmfe_solver* h, int n, const double* t, const double* C, co
     s.done = 0;
     s.pending = 0;
     s.sp_ran = 0;
+    s.sp_left = 0;
     s.status = 0;
     DMFE_CUDA_TRY(cudaMemcpyAsync(h->v.hist[0], hist.data(), hist.size() * sizeof(dbl4), cudaMemcpyHostToDevice, h->stream));
     DMFE_CUDA_TRY(cudaMemcpyAsync(h->v.ht[0], t, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
@@ -852,7 +859,8 @@ int dmfe_sync(dmfe_solver* h) {
 
 // ---- checkpoint format: magic, version, parameters, f, device state, history (FP64).
 static const char kMagic[8] = {'D', 'M', 'F', 'E', 'C', 'K', 'P', '2'};
-static const int kCkpVersion = 3;  // 2: integrator fields; 3: log-R flag in the parameters
+static const int kCkpVersion = 4;  // 2: integrator fields; 3: log-R flag in the parameters;
+                                   // 4: sparsification policy and its round state
 
 int dmfe_checkpoint(dmfe_solver* h, const char* path) {
     if (!h || !path) return DMFE_ERR_ARG;
@@ -927,6 +935,7 @@ int dmfe_restore(const char* path, void* stream, dmfe_solver** out) {
     s.active = 0;
     s.pending = 0;
     s.sp_ran = 0;
+    s.sp_left = 0;
     *h->hstate = s;
     rc = DMFE_OK;
     if (cudaMemcpyAsync(h->v.hist[0], hist.data(), hist.size() * sizeof(dbl4), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||

@@ -172,6 +172,8 @@ int dmfe_batch_add(dmfe_batch* b, const dmfe_params* p, double t_max, double tol
     if (!(tol > 0.0) || !(t_max <= p->grid_t_max * (1.0 + 1e-12))) return DMFE_ERR_ARG;
     // the batched kernel is compiled without the log-R reads (they cost it registers)
     if (p->log_r) return DMFE_ERR_UNSUPPORTED;
+    // one copy of the pass kernels per batched step graph: one pass per round
+    if (p->sparsify_passes > 1) return DMFE_ERR_UNSUPPORTED;
     int k = 0;
     while (k < b->max_slots && b->slots[k]) ++k;
     if (k == b->max_slots) return DMFE_ERR_CAPACITY;

@@ -102,11 +102,12 @@ struct DevState {
     int method;          // integrator of the next step: 0 Dormand-Prince 5(4), 1 SSPRK(10,4)
     int rk;              // integrator of the step in progress (set by its first kernel)
     int nst;             // its number of stage evaluations (6 or 10)
-    int pad_;
+    int sp_left;         // sparsification passes left in the current round (set on accept)
     double t_switch;     // time of the switch to SSPRK(10,4), -1 if none
 };
 
 constexpr int kMaxStages = 10;  // stage evaluations per step of the longest method
+constexpr int kMaxSparsifyPasses = 8;  // passes per sparsification round (dmfe_params.sparsify_passes)
 constexpr int kDP5Stages = 6;   // stage evaluations per Dormand-Prince step
 
 #if defined(__CUDACC__)
@@ -121,7 +122,9 @@ __device__ __forceinline__ bool stage_off(const DevState* st, int stage) {
 // Everything a kernel needs about one solver (passed by value).
 struct SolverView {
     int L, s, cap, precision;
-    int sparsify;         // 1: pass when the store is full
+    int sparsify;         // 1: round when the store is full
+    int sp_every;         // > 0: a round after every sp_every-th accepted step
+    int sp_passes;        // passes per round (>= 1)
     double rk_switch_dt;  // controller step of the switch to SSPRK(10,4) (+inf: never)
     int interp, fh_d;     // theta-stencil scheme (DMFE_INTERP_*) and Floater-Hormann degree
     int hi_threads;       // block size of a single solve's history-integral launch

@@ -487,11 +487,15 @@ __device__ __forceinline__ void stage_end_body(const SolverView& v, int stg, int
             st->steps_accepted += 1;
             const double tnew = (h < st->t_target - t) ? t + h : st->t_target;
             if (n >= v.cap) {
-                if (v.sparsify) { st->pending = 1; st->t_pending = tnew; }
+                // a full store: a sparsification round whose first pass makes room for
+                // the new slice (appended when that pass finishes)
+                if (v.sparsify) { st->pending = 1; st->t_pending = tnew; st->sp_left = v.sp_passes; }
                 else st->status = DMFE_ERR_CAPACITY;
             } else {
                 s_append = n;
                 st->t_pending = tnew;
+                // the periodic round, after this step's append
+                if (v.sp_every > 0 && st->steps_accepted % v.sp_every == 0) st->sp_left = v.sp_passes;
             }
             if (eps > tol) st->dt *= 0.9;
             else if (eps < 0.5 * tol) st->dt *= 1.01;
@@ -577,8 +581,11 @@ __device__ __forceinline__ double herm_int(double y0, double d0, double y1, doub
     return 0.5 * h * (y0 + y1) + h * h * (d0 - d1) / 12.0;
 }
 
+// A pass of the step graph runs while the current round has passes left (a round is set
+// by the step decision: on a full store, or after every sp_every-th accepted step); an
+// explicit call (dmfe_sparsify) always runs.
 __device__ __forceinline__ bool sp_active(const DevState* st, int from_step) {
-    return from_step ? (st->pending != 0 && st->status == 0) : true;
+    return from_step ? (st->sp_left > 0 && st->status == 0) : true;
 }
 
 // eps_sparse(n) for candidates n = 1 .. N-12: one warp per candidate.
@@ -624,12 +631,16 @@ __device__ __forceinline__ void sp_residual_body(const SolverView& v, int from_s
 __device__ __forceinline__ void sp_select_body(const SolverView& v, int from_step, double tol_arg) {
     DevState* st = v.st;
     if (!sp_active(st, from_step) || threadIdx.x != 0) return;
+    if (from_step) st->sp_left -= 1;
+    // the first pass of a full-store round (and an explicit pass) must free a slot, so it
+    // may force a removal; the other passes remove only slices that qualify
+    const bool force = from_step ? st->pending != 0 : true;
     const int N = st->n;
     const int last = N - 12;
     const double tol = from_step ? st->tol : tol_arg;
     st->sp_ran = 0;
     if (last < 1) {
-        if (from_step) st->status = DMFE_ERR_CAPACITY;
+        if (from_step && force) st->status = DMFE_ERR_CAPACITY;
         return;
     }
     const double thr = tol / 10.0;
@@ -654,6 +665,12 @@ __device__ __forceinline__ void sp_select_body(const SolverView& v, int from_ste
     for (int k = last + 1; k < N; ++k) {
         v.keep[k] = 1;
         v.newidx[k] = c++;
+    }
+    if (removed == 0 && !force) {
+        // nothing qualifies and nothing is forced: the pass counts, the history stays
+        st->sparsify_passes += 1;
+        st->removed_count = 0;
+        return;
     }
     if (removed == 0) {
         // every slice was kept, so newidx[k] = k; removing m shifts the slices after it
@@ -917,7 +934,15 @@ int launch_step_tail(const SolverView& v, int grid_ctas, cudaStream_t s) {
     return launch_stages(v, grid_ctas, kDP5Stages + 1, kMaxStages, s);
 }
 
-int launch_step_sparsify(const SolverView& v, cudaStream_t s) { return launch_sparsify(v, true, 0.0, s); }
+// The passes of a sparsification round: sp_passes copies of the pass kernels, each doing
+// nothing unless the round still has passes left.
+int launch_step_sparsify(const SolverView& v, cudaStream_t s) {
+    for (int p = 0; p < (v.sp_passes > 0 ? v.sp_passes : 1); ++p) {
+        const int rc = launch_sparsify(v, true, 0.0, s);
+        if (rc) return rc;
+    }
+    return DMFE_OK;
+}
 
 int launch_step(const SolverView& v, int grid_ctas, cudaStream_t s) {
     int rc = launch_step_head(v, grid_ctas, 0, 0, s);

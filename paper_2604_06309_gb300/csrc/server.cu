@@ -190,6 +190,7 @@ int dmfe_server_submit(dmfe_server* srv, const dmfe_params* p, double t_max, dou
     if (p->precision != srv->precision || p->s != srv->s || p->L > srv->max_L || cap > srv->max_cap) return DMFE_ERR_ARG;
     if (!(tol > 0.0) || !(t_max <= p->grid_t_max * (1.0 + 1e-12))) return DMFE_ERR_ARG;
     if (p->log_r) return DMFE_ERR_UNSUPPORTED;  // as dmfe_batch_add
+    if (p->sparsify_passes > 1) return DMFE_ERR_UNSUPPORTED;
     Request rq;
     rq.p = *p;
     rq.pw.assign(p->powers, p->powers + p->n_terms);

@@ -47,7 +47,7 @@ class dmfe_params(ctypes.Structure):
                 ("L", _i), ("s", _i), ("grid_t_max", _d), ("alpha", _d), ("delta", _d),
                 ("history_cap", _i), ("dt0", _d), ("dt_min", _d), ("precision", _i),
                 ("sparsify", _i), ("stream", _p), ("integrator", _i), ("rk_switch_dt", _d), ("hi_chunk", _i),
-                ("interp", _i), ("fh_d", _i), ("log_r", _i)]
+                ("interp", _i), ("fh_d", _i), ("log_r", _i), ("sparsify_every", _i), ("sparsify_passes", _i)]
 
 
 class dmfe_stats_t(ctypes.Structure):
@@ -158,7 +158,7 @@ def _f64(a, n=None):
 
 def make_params(coefs, T, L, grid_t_max, s=4, beta0=0.0, alpha=0.0, delta=0.0, history_cap=None, dt0=1e-4,
                 dt_min=1e-12, precision="fp64", sparsify=True, stream=None, integrator="auto", switch_dt=0.0,
-                hi_chunk=0, interp="lagrange_index", fh_d=3, log_r=False):
+                hi_chunk=0, interp="lagrange_index", fh_d=3, log_r=False, sparsify_every=0, sparsify_passes=1):
     """A dmfe_params structure; the returned tuple keeps the coefficient arrays alive."""
     lib = load()
     terms = sorted((int(p), float(c)) for p, c in dict(coefs).items())
@@ -182,6 +182,8 @@ def make_params(coefs, T, L, grid_t_max, s=4, beta0=0.0, alpha=0.0, delta=0.0, h
     prm.interp = INTERPS[interp]
     prm.fh_d = int(fh_d)
     prm.log_r = 1 if log_r else 0
+    prm.sparsify_every = int(sparsify_every)
+    prm.sparsify_passes = int(sparsify_passes)
     return prm, (pw, cf)
 
 
@@ -316,13 +318,15 @@ class Solver:
     def __init__(self, coefs, T, L, grid_t_max, s=4, beta0=0.0, alpha=0.0, delta=0.0,
                  history_cap=None, dt0=1e-4, dt_min=1e-12, precision="fp64", sparsify=True,
                  stream=None, integrator="auto", switch_dt=0.0, hi_chunk=0, interp="lagrange_index", fh_d=3,
-                 log_r=False):
+                 log_r=False, sparsify_every=0, sparsify_passes=1):
         """The fields of dmfe_params (include/dmfe.h). precision: "fp64", "df" (double-float)
         or "fp32" (FP32 with compensated sums). integrator: "auto" (Dormand-Prince, then
         SSPRK(10,4) once the step reaches switch_dt; 0 = the stability estimate), "dp5" or
         "ssprk104" (Sec. 3.5). interp: "lagrange_index", "fh_index", "lagrange_theta" or
         "fh_theta" with Floater-Hormann degree fh_d (Sec. 3.3; all but the first FP64 only).
-        log_r: interpolate the response history in log R where positive (App. A; FP64)."""
+        log_r: interpolate the response history in log R where positive (App. A; FP64).
+        sparsify_every, sparsify_passes: a sparsification round also after every P-th
+        accepted step (0: only on a full store), and the passes per round (Sec. 3.6)."""
         lib = load()
         self._lib = lib
         self.h = _p()
@@ -330,7 +334,8 @@ class Solver:
         prm, keep = make_params(coefs, T, L, grid_t_max, s=s, beta0=beta0, alpha=alpha, delta=delta,
                                 history_cap=history_cap, dt0=dt0, dt_min=dt_min, precision=precision,
                                 sparsify=sparsify, stream=stream, integrator=integrator, switch_dt=switch_dt,
-                                hi_chunk=hi_chunk, interp=interp, fh_d=fh_d, log_r=log_r)
+                                hi_chunk=hi_chunk, interp=interp, fh_d=fh_d, log_r=log_r,
+                                sparsify_every=sparsify_every, sparsify_passes=sparsify_passes)
         _check(lib.dmfe_create(ctypes.byref(prm), ctypes.byref(self.h)), "dmfe_create")
         self._sizes()
 

@@ -79,6 +79,34 @@ def test_integrate_with_sparsification_and_rejections_matches_oracle(precision):
     g.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "df"])
+@pytest.mark.parametrize("every,passes", [(7, 1), (5, 2), (0, 3)])
+def test_sparsify_policy_matches_oracle_step_by_step(precision, every, passes):
+    """The user's control of sparsification (Sec. 3.6): rounds after every `every`-th
+    accepted step and `passes` passes per round. A large first step forces rejections and a
+    24-slice store also fills, so full-store rounds (first pass forced if needed, the slice
+    appended after it) mix with periodic ones."""
+    need_gpu()
+    g, o = _pair(MIXED_34, 0.5, 33, 100.0, cap=24, dt0=0.3, precision=precision, sparsify_every=every,
+                 sparsify_passes=passes)
+    assert g.integrate(2.0, 1e-8) == 0
+    assert o.integrate(2.0, 1e-8) == 0
+    assert o.stats["steps_rejected"] >= 1 and o.stats["sparsify_passes"] >= passes
+    _compare_runs(g, o)
+    g.close()
+
+
+def test_periodic_sparsification_without_full_store_rounds():
+    """sparsify = 0 with sparsify_every: only the periodic rounds run (no forced removals)."""
+    need_gpu()
+    g, o = _pair(PURE_3, 0.8, 33, 100.0, cap=400, sparsify=False, sparsify_every=4, sparsify_passes=2)
+    assert g.integrate(1.0, 1e-8) == 0
+    assert o.integrate(1.0, 1e-8) == 0
+    assert o.stats["sparsify_passes"] > 0 and o.stats["forced_removals"] == 0
+    _compare_runs(g, o)
+    g.close()
+
+
 def test_integrate_fp32_compensated_within_1e6():
     need_gpu()
     g, o = _pair(MIXED_34, 0.5, 65, 100.0, cap=128, precision="fp32")

@@ -45,13 +45,16 @@ def test_struct_layout_matches_c(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "dmfe.h"\n'
                     'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(dmfe_params), sizeof(dmfe_stats_t),'
-                    ' offsetof(dmfe_params, stream), offsetof(dmfe_stats_t, status), offsetof(dmfe_stats_t, precision));return 0;}\n')
+                    ' offsetof(dmfe_params, stream), offsetof(dmfe_stats_t, status), offsetof(dmfe_stats_t, precision));'
+                    'printf("%zu %zu\\n", offsetof(dmfe_params, sparsify_every), offsetof(dmfe_params, sparsify_passes));'
+                    'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     vals = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     assert vals == [ctypes.sizeof(dmfe.dmfe_params), ctypes.sizeof(dmfe.dmfe_stats_t),
                     dmfe.dmfe_params.stream.offset, dmfe.dmfe_stats_t.status.offset,
-                    dmfe.dmfe_stats_t.precision.offset]
+                    dmfe.dmfe_stats_t.precision.offset, dmfe.dmfe_params.sparsify_every.offset,
+                    dmfe.dmfe_params.sparsify_passes.offset]
 
 
 def test_strerror_without_gpu(built):

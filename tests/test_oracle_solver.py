@@ -203,6 +203,59 @@ def test_sparsify_selection_equals_the_run_parity_rule():
             assert len(got) == 1
 
 
+def test_two_passes_on_a_cubic_history_remove_alternate_survivors():
+    """Every residual of a history lying on one cubic is zero, so each pass of the greedy
+    scan removes the candidates 1, 3, 5, ... of the history it is given (candidates are
+    slices 1 .. N-12): ceil((N - 12) / 2) slices. A second pass (reading R16: passes are
+    repeated scans of the thinned history) does the same on the survivors."""
+    H = _cubic_history(N=40)
+    st = dict(sparsify_passes=0, slices_removed=0, forced_removals=0, max_eps_sparse=0.0)
+    H1, ran1 = S.sparsify_pass(H, 1e-8, st, force=False)
+    H2, ran2 = S.sparsify_pass(H1, 1e-8, st, force=False)
+    assert ran1 and ran2
+    r1 = -(-(H.N - 12) // 2)
+    assert H1.N == H.N - r1
+    r2 = -(-(H1.N - 12) // 2)
+    assert H2.N == H1.N - r2
+    assert np.array_equal(np.setdiff1d(H1.t, H2.t), H1.t[1:H1.N - 11:2])
+    assert st == dict(sparsify_passes=2, slices_removed=r1 + r2, forced_removals=0, max_eps_sparse=st["max_eps_sparse"])
+
+
+def test_a_pass_without_forcing_keeps_everything_when_nothing_qualifies():
+    H = _cubic_history()
+    H.C[1:-1] += np.random.default_rng(1).normal(scale=1e-2, size=H.C[1:-1].shape)
+    st = dict(sparsify_passes=0, slices_removed=0, forced_removals=0, max_eps_sparse=0.0)
+    H2, ran = S.sparsify_pass(H, 1e-8, st, force=False)
+    assert ran and H2.N == H.N and np.array_equal(H2.t, H.t)
+    assert st["sparsify_passes"] == 1 and st["slices_removed"] == 0 and st["forced_removals"] == 0
+    # a history without candidates (N <= 12): no pass
+    short = History(H.t[:12], H.C[:12], H.dC[:12], H.R[:12], H.dR[:12])
+    assert S.sparsify_pass(short, 1e-8, st, force=False)[1] is False
+
+
+def test_periodic_rounds_of_two_passes_stay_within_tolerance():
+    """sparsify_every = 5, two passes per round, a store that never fills: rounds run after
+    every fifth accepted step once there are candidates, and the solve stays close to the
+    same solve without sparsification (each removal changes the stored integrals by less
+    than tol / 10)."""
+    kw = dict(L=33, grid_t_max=10.0, history_cap=1000)
+    ref = S.Solver({3: 0.5}, 0.8, sparsify=False, **kw)
+    assert ref.integrate(1.0, 1e-8) == S.OK
+    sv = S.Solver({3: 0.5}, 0.8, sparsify_every=5, sparsify_passes=2, **kw)
+    assert sv.integrate(1.0, 1e-8) == S.OK
+    st = sv.stats
+    assert st["forced_removals"] == 0 and st["slices_removed"] > 0
+    assert sv.hist.N == st["steps_accepted"] + 1 - st["slices_removed"]
+    # rounds after steps 5, 10, ...; a pass runs once there are 13 stored slices
+    assert 0 < st["sparsify_passes"] <= 2 * (st["steps_accepted"] // 5)
+    assert st["sparsify_passes"] % 2 == 0
+    t = np.array([1.0, 1.0, 0.7, 0.5])
+    tp = np.array([0.2, 0.9, 0.3, 0.49])
+    assert np.max(np.abs(sv.get_C(t, tp) - ref.get_C(t, tp))) < 1e-7
+    assert np.max(np.abs(sv.get_R(t, tp) - ref.get_R(t, tp))) < 1e-7
+    assert abs(sv.E - ref.E) < 1e-7
+
+
 def test_rejection_reverts_and_halves():
     sv = S.Solver({3: 0.5}, 0.8, L=33, grid_t_max=10.0, dt0=0.5, history_cap=100)
     assert sv.integrate(1.0, 1e-10) == S.OK
