@@ -743,6 +743,10 @@ def run_batch(args):
         admit_s = time.perf_counter() - t0
         b.step(2)  # warm-up (graph capture, first touches)
         b.poll()
+        # work-unit size of the batched kernel, tuned on this batch (one step per candidate
+        # per round; the tuning steps are not timed)
+        tuned, tune_ms = b.autotune(1)
+        b.poll()
         st0 = [b.solver(k).stats() for k in range(len(reqs))]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
@@ -767,6 +771,7 @@ def run_batch(args):
         res = {"batched_steps": nsteps, "device_s": dev_s, "instance_stages_per_s": stages / dev_s,
                "pair_evals_per_s": pairs / dev_s, "completed": completed, "failed": failed,
                "completed_solves_per_s": completed / dev_s, "admission_s": admit_s, "clocks": clk,
+               "tuned_unit": tuned, "tune_ms_per_step": {str(k): v for k, v in tune_ms.items()},
                "max_t_reached": float(np.max(tcur[:len(reqs)]))}
         b.close()
         # one at a time on the same GPU, FP64: stage time of a single solve per grid size

@@ -141,6 +141,10 @@ typedef struct {
     int       step_graph;        /* 0: no step graph yet; 1: all stages inline (the SSPRK
                                     ones gate themselves off in Dormand-Prince steps);
                                     2: SSPRK stages in a conditional graph node        */
+    int       bounds_site;       /* library built with -DDMFE_CHECKED (libdmfe_checked.so):
+                                    site code of the first stencil-base or history-row
+                                    index that failed its bounds check (the access was
+                                    skipped or made in bounds instead); 0 otherwise     */
 } dmfe_stats_t;
 
 /* Fill p with defaults for the given f (pointers are kept, not copied). */
@@ -288,6 +292,20 @@ int dmfe_batch_step(dmfe_batch* b, int nsteps);
  * for a free slot) and t[k] (arrays of max_slots, may be NULL). Finished and failed slots
  * stop receiving work. *running receives the number of slots still integrating. */
 int dmfe_batch_poll(dmfe_batch* b, int* status, double* t, int* running);
+
+/* Autotuner of the batched history-integral kernel's work units (the batch form of
+ * dmfe_autotune; the paper has no counterpart). Tries the unit sizes 0 (one unit per output
+ * index, the default), 256, 512, 1024 and 2048 summation indices (a size >= a slot's L means
+ * one unit per index there) on every slot of the batch, each for `steps` real batched steps,
+ * in two interleaved rounds, and keeps the one with the smallest device time per step for
+ * all slots. The timed steps advance the solves, and changing a slot's unit size changes
+ * the summation order of its sums (rounding-level differences), so tune on a batch whose
+ * results are not kept, or before results matter; a fresh batch whose slots are added with
+ * dmfe_params.hi_chunk = *chunk (0: leave 0) then runs bitwise like solo solves with that
+ * unit size. *chunk (may be NULL) receives the choice and ms_per_step (may be NULL, 5
+ * entries) the best time per step of each candidate. Synchronous. */
+#define DMFE_BATCH_TUNE_CANDIDATES 5
+int dmfe_batch_autotune(dmfe_batch* b, int steps, int* chunk, double* ms_per_step);
 
 /* Device bytes a solver with these parameters allocates (dmfe_create), rounded up the way
  * large device allocations are; used for admission by footprint. 0 on invalid input. */

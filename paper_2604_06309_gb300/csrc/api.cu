@@ -359,6 +359,7 @@ double last_time(dmfe_solver* h) { return h->hstate->t; }
 }  // namespace
 
 const SolverView& solver_view(const dmfe_solver* h) { return h->v; }
+void solver_set_chunk(dmfe_solver* h, int chunk) { h->v.hi_chunk = chunk; }
 
 int solver_read_state(dmfe_solver* h, DevState* out) {
     TRY(read_state(h));
@@ -748,6 +749,7 @@ int dmfe_stats(dmfe_solver* h, dmfe_stats_t* o) {
     o->steps_rejected = s.steps_rejected;
     o->stages = s.stages;
     o->sparsify_passes = s.sparsify_passes;
+    o->bounds_site = s.bounds_site;
     o->slices_removed = s.slices_removed;
     o->forced_removals = s.forced_removals;
     o->n_slices = s.n;

@@ -219,6 +219,56 @@ int dmfe_batch_step(dmfe_batch* b, int nsteps) {
     return DMFE_OK;
 }
 
+// Work-unit sizes the batch autotuner tries for every slot (0: one unit per output index).
+static const int kBatchTuneChunks[DMFE_BATCH_TUNE_CANDIDATES] = {0, 256, 512, 1024, 2048};
+
+int dmfe_batch_autotune(dmfe_batch* b, int steps, int* chunk, double* ms_per_step) {
+    if (!b || steps < 1) return DMFE_ERR_ARG;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DMFE_CUDA_TRY(cudaEventCreate(&e0));
+    DMFE_CUDA_TRY(cudaEventCreate(&e1));
+    double best_ms[DMFE_BATCH_TUNE_CANDIDATES];
+    for (double& x : best_ms) x = 1e300;
+    auto apply = [&](int c) {
+        for (dmfe_solver* h : b->slots)
+            if (h) {
+                const int L = solver_view(h).L;
+                solver_set_chunk(h, (c == 0 || c >= L) ? L : c);
+            }
+        rebuild_table(b);
+    };
+    int rc = DMFE_OK;
+    // two interleaved rounds, the best of each candidate kept: the histories grow while the
+    // candidates are timed, and interleaving keeps that drift from favouring one of them
+    for (int round = 0; round < 2 && rc == DMFE_OK; ++round) {
+        for (int q = 0; q < DMFE_BATCH_TUNE_CANDIDATES && rc == DMFE_OK; ++q) {
+            apply(kBatchTuneChunks[q]);
+            rc = upload_table(b);
+            if (!rc) rc = build_graph(b);
+            if (rc) break;
+            cudaEventRecord(e0, b->stream);
+            for (int it = 0; it < steps; ++it)
+                if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) rc = DMFE_ERR_CUDA;
+            cudaEventRecord(e1, b->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = DMFE_ERR_CUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best_ms[q] = std::min(best_ms[q], (double)ms / steps);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    int best = 0;
+    for (int q = 1; q < DMFE_BATCH_TUNE_CANDIDATES; ++q)
+        if (best_ms[q] < best_ms[best]) best = q;
+    apply(kBatchTuneChunks[best]);
+    if (chunk) *chunk = kBatchTuneChunks[best];
+    if (ms_per_step)
+        for (int q = 0; q < DMFE_BATCH_TUNE_CANDIDATES; ++q) ms_per_step[q] = best_ms[q];
+    return DMFE_OK;
+}
+
 int dmfe_batch_poll(dmfe_batch* b, int* status, double* t, int* running) {
     if (!b) return DMFE_ERR_ARG;
     TRYB(upload_table(b));

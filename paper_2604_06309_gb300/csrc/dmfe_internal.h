@@ -75,6 +75,29 @@ __device__ __forceinline__ double fp2(const Poly& P, double q) { return poly_eva
 __device__ __forceinline__ float fp1(const Poly& P, float q) { return poly_eval(P.f1, P.deg1, q); }
 __device__ __forceinline__ float fp2(const Poly& P, float q) { return poly_eval(P.f2, P.deg2, q); }
 
+// f'(q) and f''(q) (FP32) at two points in one loop: the same Horner steps, in the same
+// order, as four separate fp1 / fp2 calls (f'' has degree deg1 - 1, so f' takes one step
+// more, peeled in front), with a quarter of the loop overhead and coefficient loads.
+__device__ __forceinline__ void fp12_pair(const Poly& P, float qa, float qb, float& f1a, float& f2a, float& f1b,
+                                          float& f2b) {
+    const int d1 = P.deg1;
+    f1a = f1b = P.f1[d1];
+    if (d1 == 0) {
+        f2a = f2b = P.f2[0];
+        return;
+    }
+    f2a = f2b = P.f2[d1 - 1];
+    f1a = fmaf(f1a, qa, P.f1[d1 - 1]);
+    f1b = fmaf(f1b, qb, P.f1[d1 - 1]);
+    for (int m = d1 - 2; m >= 0; --m) {
+        const float c1 = P.f1[m], c2 = P.f2[m];
+        f1a = fmaf(f1a, qa, c1);
+        f2a = fmaf(f2a, qa, c2);
+        f1b = fmaf(f1b, qb, c1);
+        f2b = fmaf(f2b, qb, c2);
+    }
+}
+
 // Step-control and history bookkeeping, resident in device memory. Kernels of the
 // integrate loop read and update it; the host reads it only to poll and report.
 struct DevState {
@@ -103,6 +126,8 @@ struct DevState {
     int rk;              // integrator of the step in progress (set by its first kernel)
     int nst;             // its number of stage evaluations (6 or 10)
     int sp_left;         // sparsification passes left in the current round (set on accept)
+    int bounds_site;     // checked builds: site code of the first failed bounds check (0: none)
+    int pad_;
     double t_switch;     // time of the switch to SSPRK(10,4), -1 if none
 };
 
@@ -111,6 +136,23 @@ constexpr int kMaxSparsifyPasses = 8;  // passes per sparsification round (dmfe_
 constexpr int kDP5Stages = 6;   // stage evaluations per Dormand-Prince step
 
 #if defined(__CUDACC__)
+// Bounds checks of the checked build (-DDMFE_CHECKED): every stencil base and history row
+// index of the history-integral and sparsification kernels is tested before its access. A
+// failed test records its site code in DevState::bounds_site (the first failure wins) and
+// the access is skipped or made at an in-bounds index instead; nothing traps. Without
+// DMFE_CHECKED the tests are `true`. Site codes: 1-5 FP64 kernel (B1 rows, A1, A2 and B2
+// stencil bases, B2 interval), 11-15 FP32 kernel, 21-24 double-float kernel, 31-32
+// sparsification (residual rows, compaction target).
+#ifdef DMFE_CHECKED
+__device__ __forceinline__ bool dmfe_in_bounds(DevState* st, bool ok, int site) {
+    if (!ok) atomicCAS(&st->bounds_site, 0, site);
+    return ok;
+}
+#define DMFE_IN_BOUNDS(st, cond, site) dmfe_in_bounds((st), (cond), (site))
+#else
+#define DMFE_IN_BOUNDS(st, cond, site) true
+#endif
+
 // Gate of the kernels of stage `stage` (>= 1) of a step: they do nothing once the solve
 // has stopped (error or target reached) or when the step's method has fewer stages.
 // stage == 0 marks an explicit call outside the step loop (never gated).
@@ -259,6 +301,7 @@ bool step_graph_plain();  // DMFE_STEP_GRAPH=plain: no conditional nodes (graph.
 // accessors of a solver's internals (api.cu)
 struct dmfe_solver;
 const SolverView& solver_view(const dmfe_solver* h);
+void solver_set_chunk(dmfe_solver* h, int chunk);  // a batch slot's work-unit size
 int solver_read_state(dmfe_solver* h, DevState* out);
 
 // ---- host grid (host_grid.cpp) ----

@@ -196,27 +196,47 @@ __device__ __forceinline__ void lagrange_df(df u, df (&w)[SW]) {
     }
 }
 
-template <int SW>
-__device__ __forceinline__ int base_of(float xhi, int L) {
-    int b = (int)floorf(xhi) - SW / 2 + 1;
-    b = b < 0 ? 0 : b;
-    return b > L - SW ? L - SW : b;
-}
+// floor(x) for 0 <= x < 2^23, as a float: adding 2^23 rounded down keeps the integer part
+// (the float spacing there is 1). Integer <-> float conversions are avoided on this path:
+// GB300 issues them on its FP64 unit.
+__device__ __forceinline__ float floor_nonneg(float x) { return __fsub_rn(__fadd_rd(x, 8388608.f), 8388608.f); }
+// an integer-valued float 0 <= f < 2^23 as an int (its bit pattern above 2^23)
+__device__ __forceinline__ int int_of(float f) { return __float_as_int(__fadd_rn(f, 8388608.f)) - 0x4B000000; }
 
-// Stencil position x (double-float) -> base b and the weights.
+// Stencil position x (double-float, 0 <= x <= L - 1) -> base b = clamp(floor(x.hi) - SW/2 + 1,
+// 0, L - SW) and the weights; *fl receives floor(x.hi). bmax = L - SW as a float.
 template <int SW>
-__device__ __forceinline__ int stencil_df(df x, int L, df (&w)[SW]) {
-    const int b = base_of<SW>(x.hi, L);
+__device__ __forceinline__ int stencil_df(df x, float bmax, df (&w)[SW], float* fl = nullptr) {
+    const float f = floor_nonneg(x.hi);
+    if (fl) *fl = f;
+    const float bf = fminf(fmaxf(__fsub_rn(f, (float)(SW / 2 - 1)), 0.f), bmax);
     // x.hi - b is exact (b is an integer within a few units of x.hi)
-    const df u = fast_two_sum(__fsub_rn(x.hi, (float)b), x.lo);
+    const df u = fast_two_sum(__fsub_rn(x.hi, bf), x.lo);
     lagrange_df<SW>(u, w);
-    return b;
+    return int_of(bf);
 }
 
-__device__ __forceinline__ df poly_df(const float* hi, const float* lo, int deg, df q) {
-    df v = df{hi[deg], lo[deg]};
-    for (int m = deg - 1; m >= 0; --m) v = df_fma(v, q, df{hi[m], lo[m]});
-    return v;
+// f'(q) and f''(q) in double-float at two points in one loop: the same Horner steps, in
+// the same order, as evaluating each polynomial alone (f'' has degree deg1 - 1, so f' takes
+// one step more, peeled in front), with a quarter of the loop overhead and loads.
+__device__ __forceinline__ void poly12_df_pair(const Poly& P, df qa, df qb, df& f1a, df& f2a, df& f1b, df& f2b) {
+    const int d1 = P.deg1;
+    f1a = f1b = df{P.f1[d1], P.g1[d1]};
+    if (d1 == 0) {
+        f2a = f2b = df{P.f2[0], P.g2[0]};
+        return;
+    }
+    f2a = f2b = df{P.f2[d1 - 1], P.g2[d1 - 1]};
+    const df c = df{P.f1[d1 - 1], P.g1[d1 - 1]};
+    f1a = df_fma(f1a, qa, c);
+    f1b = df_fma(f1b, qb, c);
+    for (int m = d1 - 2; m >= 0; --m) {
+        const df c1 = df{P.f1[m], P.g1[m]}, c2 = df{P.f2[m], P.g2[m]};
+        f1a = df_fma(f1a, qa, c1);
+        f2a = df_fma(f2a, qa, c2);
+        f1b = df_fma(f1b, qb, c1);
+        f2b = df_fma(f2b, qb, c2);
+    }
 }
 
 __device__ __forceinline__ double warp_sum_d(double x) {
@@ -262,11 +282,7 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
     const int lane = threadIdx.x & 31;
     const df* __restrict__ omdf = v.omega_df;
     const df* __restrict__ nudf = v.nu_df;
-    const float* f1 = v.poly.f1;
-    const float* g1 = v.poly.g1;
-    const float* f2 = v.poly.f2;
-    const float* g2 = v.poly.g2;
-    const int d1 = v.poly.deg1, d2 = v.poly.deg2;
+    const float bmax = (float)(L - SW);
 
     const int chunk = v.hi_chunk;
     for (int u_ = ub + (threadIdx.x >> 5); u_ < ue; u_ += (int)(blockDim.x >> 5)) {
@@ -279,6 +295,7 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
         {
             const B1Desc d = v.b1[j];
             a0 = d.a0; a1 = d.a1;
+            if (!DMFE_IN_BOUNDS(v.st, a0 >= 0 && a0 < n && a1 < n, 21)) { a0 = 0; a1 = -1; }
             bw0 = d.wd[0]; bw1 = d.wd[1]; bw2 = d.wd[2]; bw3 = d.wd[3];
         }
         // double-float positions (8 B per pair and stencil); the weights are formed here:
@@ -291,7 +308,17 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
 #pragma unroll
         for (int r = 0; r < 9; ++r) acc[r] = dacc{0.f, 0.f};
         df c_at_0 = df{0.f, 0.f};
-        for (int i = i0 + lane; i < i1; i += 32) {
+        // software pipeline: the three positions, omega_i and nu_i of the next index are
+        // loaded before this index's arithmetic
+        int i = i0 + lane;
+        df n1{0.f, 0.f}, n2{0.f, 0.f}, n3{0.f, 0.f}, nom{0.f, 0.f}, nnu{0.f, 0.f};
+        if (i < i1) { n1 = q1r[i]; n2 = q2r[i]; n3 = q3r[i]; nom = omdf[i]; nnu = nudf[i]; }
+        for (; i < i1; i += 32) {
+            const df x1 = n1, x2 = n2, x3 = n3, omi = nom, nui = nnu;
+            if (i + 32 < i1) {
+                const int in = i + 32;
+                n1 = q1r[in]; n2 = q2r[in]; n3 = q3r[in]; nom = omdf[in]; nnu = nudf[in];
+            }
             // ---- B1: on-grid column i at time theta_j t
             df CB1, RB1;
             {
@@ -317,7 +344,8 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
             df KA1, DA1, CA1, RA1;
             {
                 df w[SW];
-                const int b = stencil_df<SW>(q1r[i], L, w);
+                int b = stencil_df<SW>(x1, bmax, w);
+                if (!DMFE_IN_BOUNDS(v.st, b >= 0 && b <= L - SW, 22)) b = 0;
                 const dfrow q0 = srow[b];
                 dacc k = dacc_prod(w[0], q0.K), d = dacc_prod(w[0], q0.D);
                 dacc c = dacc_prod(w[0], q0.C), r = dacc_prod(w[0], q0.R);
@@ -333,10 +361,11 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
             }
             // ---- A2: current row at phi2
             df KA2, RA2;
-            const df x2 = q2r[i];
+            float fl2;  // floor of the phi2 position: its grid cell
             {
                 df w[SW];
-                const int b = stencil_df<SW>(x2, L, w);
+                int b = stencil_df<SW>(x2, bmax, w, &fl2);
+                if (!DMFE_IN_BOUNDS(v.st, b >= 0 && b <= L - SW, 23)) b = 0;
                 const dfrow q0 = srow[b];
                 dacc k = dacc_prod(w[0], q0.K), r = dacc_prod(w[0], q0.R);
 #pragma unroll
@@ -350,7 +379,7 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
             // ---- B2: theta position psi on the slices around phi2 t (complement form)
             df CB2, RB2;
             {
-                const df u = df_mul(omj, omdf[i]);  // 1 - phi2 = omega_j omega_i
+                const df u = df_mul(omj, omi);  // 1 - phi2 = omega_j omega_i
                 int s0, s1;
                 df tw0, tw1, tw2, tw3;
                 if (kmax < 0) {
@@ -358,7 +387,8 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
                     s0 = 0; s1 = -1;
                     tw0 = df{1.f, 0.f}; tw1 = df{0.f, 0.f}; tw2 = df{0.f, 0.f}; tw3 = df{0.f, 0.f};
                 } else {
-                    int k = scell[(int)floorf(x2.hi) < L ? (int)floorf(x2.hi) : L - 1];
+                    const int c2 = int_of(fl2);
+                    int k = scell[c2 < L ? c2 : L - 1];
                     while (k < kmax && df_ge(sv[k + 1], u)) ++k;
                     while (k > 0 && df_lt(sv[k], u)) --k;
                     const df sg = df_mul(df_sub(sv[k], u), sinv[k]);
@@ -381,7 +411,10 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
                     }
                 }
                 df w[SW];
-                const int b = stencil_df<SW>(q3r[i], L, w);
+                int b = stencil_df<SW>(x3, bmax, w);
+                if (!DMFE_IN_BOUNDS(v.st, b >= 0 && b <= L - SW && s0 >= 0 && s0 < n && s1 < nsl, 24)) {
+                    b = 0; s0 = 0; s1 = -1;
+                }
                 const df8* __restrict__ p0 = H + (size_t)s0 * L + b;
                 df c0, dc0, r0, dr0;
                 {
@@ -422,9 +455,8 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
                 CB2 = dacc_get(tc);
                 RB2 = dacc_get(tr);
             }
-            const df f1a = poly_df(f1, g1, d1, CB1), f2a = poly_df(f2, g2, d2, CB1);
-            const df f1b = poly_df(f1, g1, d1, CB2), f2b = poly_df(f2, g2, d2, CB2);
-            const df nui = nudf[i];
+            df f1a, f2a, f1b, f2b;
+            poly12_df_pair(v.poly, CB1, CB2, f1a, f2a, f1b, f2b);
             const df nRB1 = df_mul(nui, RB1);
             const df nRA2 = df_mul(nui, RA2);
             const df nKA2 = df_mul(nui, KA2);
@@ -470,8 +502,12 @@ __global__ void k_batch_prep(const BatchTable* __restrict__ bt, int stg) {
     stage_prep_body(v, v.Y + (size_t)(stg & 1) * 2 * v.L, 0.0, stg);
 }
 
+// 384-thread CTAs, as for the other batched kernels (with 512 threads the slot loop's live
+// state made this kernel spill 148 bytes a thread)
+constexpr int DF_BATCH_THREADS = 384;
+
 template <int SW>
-__global__ void __launch_bounds__(DF_THREADS, 1) k_batch_hi_df(const BatchTable* __restrict__ bt, int stg) {
+__global__ void __launch_bounds__(DF_BATCH_THREADS, 1) k_batch_hi_df(const BatchTable* __restrict__ bt, int stg) {
     __shared__ __align__(16) SolverView sview;
     batch_for_my_units(bt, stg, [&](int k, int lb, int le) {
         __syncthreads();  // the previous slot's shared-memory data are no longer read
@@ -564,7 +600,7 @@ int batch_hi_config_df(int sw, int max_L, int max_cap, int* grid_ctas, size_t* s
     if (sm > (size_t)max_optin) return DMFE_ERR_UNSUPPORTED;
     DMFE_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int per_sm = 0;
-    DMFE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, DF_THREADS, sm));
+    DMFE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, DF_BATCH_THREADS, sm));
     if (per_sm < 1) return DMFE_ERR_UNSUPPORTED;
     *grid_ctas = nsm * per_sm;
     *smem = sm;
@@ -573,10 +609,10 @@ int batch_hi_config_df(int sw, int max_L, int max_cap, int* grid_ctas, size_t* s
 
 int launch_batch_hi_df(const BatchTable* bt, int sw, int stg, int grid, size_t smem, cudaStream_t s) {
     switch (sw) {
-        case 4: k_batch_hi_df<4><<<grid, DF_THREADS, smem, s>>>(bt, stg); break;
-        case 6: k_batch_hi_df<6><<<grid, DF_THREADS, smem, s>>>(bt, stg); break;
-        case 8: k_batch_hi_df<8><<<grid, DF_THREADS, smem, s>>>(bt, stg); break;
-        case 10: k_batch_hi_df<10><<<grid, DF_THREADS, smem, s>>>(bt, stg); break;
+        case 4: k_batch_hi_df<4><<<grid, DF_BATCH_THREADS, smem, s>>>(bt, stg); break;
+        case 6: k_batch_hi_df<6><<<grid, DF_BATCH_THREADS, smem, s>>>(bt, stg); break;
+        case 8: k_batch_hi_df<8><<<grid, DF_BATCH_THREADS, smem, s>>>(bt, stg); break;
+        case 10: k_batch_hi_df<10><<<grid, DF_BATCH_THREADS, smem, s>>>(bt, stg); break;
         default: return DMFE_ERR_UNSUPPORTED;
     }
     DMFE_CUDA_TRY(cudaGetLastError());

@@ -73,6 +73,18 @@ __device__ __forceinline__ int stencil_base(int fl, int L) {
     return b > L - SW ? L - SW : b;
 }
 
+// Fixed-point position p (FIX_FRAC_BITS fraction bits) -> stencil base b and the offset
+// u = x - b. m = p - b 2^19 < 2^23, so the float with bit pattern 0x4B000000 + m is 2^23 + m
+// exactly and the subtraction gives float(m) exactly: the same value as a conversion, from
+// the integer and FP32 pipes (GB300 issues conversions on its FP64 unit).
+template <int SW>
+__device__ __forceinline__ int fix_stencil(uint32_t p, int L, float& u) {
+    const int b = stencil_base<SW>((int)(p >> FIX_FRAC_BITS), L);
+    const uint32_t m = p - ((uint32_t)b << FIX_FRAC_BITS);
+    u = (__int_as_float(0x4B000000u | m) - 8388608.0f) * (1.0f / (float)(1u << FIX_FRAC_BITS));
+    return b;
+}
+
 // Time weights: value = w0 Y[a0] + w1 dY[a0] + w2 Y[a1] + w3 dY[a1]; a1 < 0 means the
 // stage row (only its value is used, w3 = 0). FP64, shared by both variants (per j).
 struct TimeW {
@@ -155,6 +167,7 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
         // an interval of the history or the virtual extension interval (a1 < 0); else a
         // single stored slice at the stage time t = 0
         const bool b1_interior = b1.a1 == b1.a0 + 1 || b1.a1 < 0;
+        const bool b1ok = DMFE_IN_BOUNDS(v.st, b1.a0 >= 0 && b1.a0 < n && b1.a1 < n, 1);
         constexpr size_t WTS = 8 + 8 * SW;  // bytes per stencil entry
         const unsigned char* __restrict__ w1r = v.wt1 + (size_t)j * L * WTS;
         const unsigned char* __restrict__ w2r = v.wt2 + (size_t)j * L * WTS;
@@ -165,8 +178,9 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
         double c_at_0 = 0.0;
         for (int i = i0 + lane; i < i1; i += 32) {
             // ---- B1: on-grid column i at time theta_j t
-            double CB1, RB1;
-            if (b1_interior) {
+            double CB1 = 0.0, RB1 = 0.0;
+            if (!b1ok) {
+            } else if (b1_interior) {
                 const dbl8 c = HC[(size_t)b1.a0 * L + i];
                 CB1 = c.c0 + s1 * (c.c1 + s1 * (c.c2 + s1 * c.c3));
                 RB1 = c.r0 + s1 * (c.r1 + s1 * (c.r2 + s1 * c.r3));
@@ -196,10 +210,12 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
                 double w[SW];
 #pragma unroll
                 for (int k = 0; k < SW; ++k) w[k] = reinterpret_cast<const double*>(e + 8)[k];
+                if (DMFE_IN_BOUNDS(v.st, b >= 0 && b <= L - SW, 2)) {
 #pragma unroll
-                for (int k = 0; k < SW; ++k) {
-                    dbl4 q = srow[b + k];
-                    KA1 += w[k] * q.x; DA1 += w[k] * q.y; CA1 += w[k] * q.z; RA1 += w[k] * q.w;
+                    for (int k = 0; k < SW; ++k) {
+                        dbl4 q = srow[b + k];
+                        KA1 += w[k] * q.x; DA1 += w[k] * q.y; CA1 += w[k] * q.z; RA1 += w[k] * q.w;
+                    }
                 }
             }
             // ---- A2: current row at phi2
@@ -212,10 +228,12 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
                 double w[SW];
 #pragma unroll
                 for (int k = 0; k < SW; ++k) w[k] = reinterpret_cast<const double*>(e + 8)[k];
+                if (DMFE_IN_BOUNDS(v.st, b >= 0 && b <= L - SW, 3)) {
 #pragma unroll
-                for (int k = 0; k < SW; ++k) {
-                    dbl4 q = srow[b + k];
-                    KA2 += w[k] * q.x; RA2 += w[k] * q.w;
+                    for (int k = 0; k < SW; ++k) {
+                        dbl4 q = srow[b + k];
+                        KA2 += w[k] * q.x; RA2 += w[k] * q.w;
+                    }
                 }
             }
             // ---- B2: theta position psi on the slices around phi2 t
@@ -241,13 +259,14 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
                     const dbl8* __restrict__ P = HC + (size_t)k * L + b;
                     CB2 = 0.0;
                     RB2 = 0.0;
+                    const bool ok2 = DMFE_IN_BOUNDS(v.st, k >= 0 && k <= kmax && b >= 0 && b <= L - SW, 4);
 #pragma unroll
-                    for (int m = 0; m < SW; ++m) {
+                    for (int m = 0; m < (ok2 ? SW : 0); ++m) {
                         const dbl8 c = P[m];
                         CB2 += w[m] * (c.c0 + sg * (c.c1 + sg * (c.c2 + sg * c.c3)));
                         RB2 += w[m] * (c.r0 + sg * (c.r1 + sg * (c.r2 + sg * c.r3)));
                     }
-                    if (LC) {
+                    if (LC && ok2) {
                         // log-R mode: the same interpolant on log R; a NaN (some node's R not
                         // positive) propagates through the sum and keeps the linear value
                         const dbl4* __restrict__ Q = LC + (size_t)k * L + b;
@@ -265,8 +284,9 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
                     RB2 = 0.0;
                     bool pos = true;
                     double lr = 0.0;
+                    const bool ok1 = DMFE_IN_BOUNDS(v.st, b >= 0 && b <= L - SW, 5);
 #pragma unroll
-                    for (int m = 0; m < SW; ++m) {
+                    for (int m = 0; m < (ok1 ? SW : 0); ++m) {
                         const dbl4 q = H[b + m];
                         CB2 += w[m] * q.x;
                         RB2 += w[m] * q.z;
@@ -350,7 +370,6 @@ __device__ __forceinline__ void hi_f32_body(const SolverView& v, const double* _
     const int lane = threadIdx.x & 31;
     const float* __restrict__ om32 = v.omega32;
     const float* __restrict__ nu32 = v.nu32;
-    const float fscale = 1.0f / (float)(1u << FIX_FRAC_BITS);
     const int chunk = v.hi_chunk;
 
     for (int u = ub + (threadIdx.x >> 5); u < ue; u += (int)(blockDim.x >> 5)) {
@@ -367,46 +386,66 @@ __device__ __forceinline__ void hi_f32_body(const SolverView& v, const double* _
         const uint32_t* __restrict__ p1r = v.p1 + (size_t)j * L;
         const uint32_t* __restrict__ p2r = v.p2 + (size_t)j * L;
         const uint32_t* __restrict__ p3r = v.p3 + (size_t)j * L;
+        const bool b1ok = DMFE_IN_BOUNDS(v.st, b1d.a0 >= 0 && b1d.a0 < n && b1d.a1 < n, 11);
+        const float4* __restrict__ H0 = H + (size_t)(b1ok ? b1d.a0 : 0) * L;
+        const float4* __restrict__ H1 = (b1d.a1 >= 0 && b1ok) ? H + (size_t)b1d.a1 * L : nullptr;
         Kahan acc[9];
 #pragma unroll
         for (int r = 0; r < 9; ++r) { acc[r].s = 0.f; acc[r].c = 0.f; }
         float c_at_0 = 0.f;
-        for (int i = i0 + lane; i < i1; i += 32) {
-            float CB1, RB1;
-            {
-                float4 h0 = H[(size_t)b1d.a0 * L + i];
-                CB1 = bw0 * h0.x + bw1 * h0.y;
-                RB1 = bw0 * h0.z + bw1 * h0.w;
-                if (b1d.a1 >= 0) {
-                    float4 h1 = H[(size_t)b1d.a1 * L + i];
-                    CB1 += bw2 * h1.x + bw3 * h1.y;
-                    RB1 += bw2 * h1.z + bw3 * h1.w;
-                } else {
-                    float4 r1 = srow[i];
-                    CB1 += bw2 * r1.z;
-                    RB1 += bw2 * r1.w;
-                }
+        // software pipeline: the loads that head each pair's dependence chains (positions,
+        // omega_i, nu_i and the B1 history entries) are issued one index ahead
+        int i = i0 + lane;
+        uint32_t n1 = 0, n2 = 0, n3 = 0;
+        float nom = 0.f, nnu = 0.f;
+        float4 nh0 = make_float4(0.f, 0.f, 0.f, 0.f), nh1 = nh0;
+        if (i < i1) {
+            n1 = p1r[i]; n2 = p2r[i]; n3 = p3r[i]; nom = om32[i]; nnu = nu32[i];
+            nh0 = H0[i];
+            nh1 = H1 ? H1[i] : srow[i];
+        }
+        for (; i < i1; i += 32) {
+            const uint32_t pp1 = n1, pp2 = n2, pp3 = n3;
+            const float omi = nom, nui = nnu;
+            const float4 h0 = nh0, h1 = nh1;
+            const int in = i + 32;
+            if (in < i1) {
+                n1 = p1r[in]; n2 = p2r[in]; n3 = p3r[in]; nom = om32[in]; nnu = nu32[in];
+                nh0 = H0[in];
+                nh1 = H1 ? H1[in] : srow[in];
+            }
+            // ---- B1 (h1 is the stage row's entry when a1 < 0; only its value is used)
+            float CB1 = bw0 * h0.x + bw1 * h0.y;
+            float RB1 = bw0 * h0.z + bw1 * h0.w;
+            if (H1) {
+                CB1 += bw2 * h1.x + bw3 * h1.y;
+                RB1 += bw2 * h1.z + bw3 * h1.w;
+            } else {
+                CB1 += bw2 * h1.z;
+                RB1 += bw2 * h1.w;
             }
             float KA1 = 0.f, DA1 = 0.f, CA1 = 0.f, RA1 = 0.f;
             {
-                uint32_t p = p1r[i];
-                int b = stencil_base<SW>((int)(p >> FIX_FRAC_BITS), L);
+                float uu;
+                const int b = fix_stencil<SW>(pp1, L, uu);
                 float w[SW];
-                lagrange<SW>((float)(p - ((uint32_t)b << FIX_FRAC_BITS)) * fscale, w);
+                lagrange<SW>(uu, w);
+                const bool ok = DMFE_IN_BOUNDS(v.st, b >= 0 && b <= L - SW, 12);
 #pragma unroll
-                for (int k = 0; k < SW; ++k) {
+                for (int k = 0; k < (ok ? SW : 0); ++k) {
                     float4 q = srow[b + k];
                     KA1 += w[k] * q.x; DA1 += w[k] * q.y; CA1 += w[k] * q.z; RA1 += w[k] * q.w;
                 }
             }
             float KA2 = 0.f, RA2 = 0.f;
-            const uint32_t pp2 = p2r[i];
             {
-                int b = stencil_base<SW>((int)(pp2 >> FIX_FRAC_BITS), L);
+                float uu;
+                const int b = fix_stencil<SW>(pp2, L, uu);
                 float w[SW];
-                lagrange<SW>((float)(pp2 - ((uint32_t)b << FIX_FRAC_BITS)) * fscale, w);
+                lagrange<SW>(uu, w);
+                const bool ok = DMFE_IN_BOUNDS(v.st, b >= 0 && b <= L - SW, 13);
 #pragma unroll
-                for (int k = 0; k < SW; ++k) {
+                for (int k = 0; k < (ok ? SW : 0); ++k) {
                     float4 q = srow[b + k];
                     KA2 += w[k] * q.x; RA2 += w[k] * q.w;
                 }
@@ -414,17 +453,18 @@ __device__ __forceinline__ void hi_f32_body(const SolverView& v, const double* _
             float CB2, RB2;
             {
                 // complement of phi2: 1 - phi2 = omega_j omega_i; slice k holds v_k = (t - t_k)/t
-                const float u = omj * om32[i];
+                const float uc = omj * omi;
                 int a0, a1;
                 float w0, w1, w2, w3;
                 if (kmax < 0) {
                     // a single stored slice and the stage at its time
                     a0 = 0; a1 = -1; w0 = 1.f; w1 = 0.f; w2 = 0.f; w3 = 0.f;
                 } else {
-                    int k = scell[pp2 >> FIX_FRAC_BITS];
-                    while (k < kmax && sv[k + 1] >= u) ++k;
-                    while (k > 0 && sv[k] < u) --k;
-                    float sg = (sv[k] - u) * sinv[k];
+                    const int cell = (int)(pp2 >> FIX_FRAC_BITS);
+                    int k = DMFE_IN_BOUNDS(v.st, cell < L, 14) ? scell[cell] : 0;
+                    while (k < kmax && sv[k + 1] >= uc) ++k;
+                    while (k > 0 && sv[k] < uc) --k;
+                    float sg = (sv[k] - uc) * sinv[k];
                     float hh = sdt[k];
                     float om = 1.f - sg;
                     a0 = k; a1 = k + 1;
@@ -433,18 +473,19 @@ __device__ __forceinline__ void hi_f32_body(const SolverView& v, const double* _
                     w2 = sg * sg * (3.f - 2.f * sg);
                     w3 = sg * sg * (sg - 1.f) * hh;
                 }
-                const uint32_t p = p3r[i];
-                int b = stencil_base<SW>((int)(p >> FIX_FRAC_BITS), L);
+                float uu;
+                const int b = fix_stencil<SW>(pp3, L, uu);
                 float w[SW];
-                lagrange<SW>((float)(p - ((uint32_t)b << FIX_FRAC_BITS)) * fscale, w);
+                lagrange<SW>(uu, w);
                 float c0 = 0.f, dc0 = 0.f, r0 = 0.f, dr0 = 0.f, c1 = 0.f, dc1 = 0.f, r1 = 0.f, dr1 = 0.f;
+                const bool ok = DMFE_IN_BOUNDS(v.st, a0 >= 0 && a0 < n && a1 < nsl && b >= 0 && b <= L - SW, 15);
                 const float4* __restrict__ s0 = H + (size_t)a0 * L + b;
 #pragma unroll
-                for (int k = 0; k < SW; ++k) {
+                for (int k = 0; k < (ok ? SW : 0); ++k) {
                     float4 q = s0[k];
                     c0 += w[k] * q.x; dc0 += w[k] * q.y; r0 += w[k] * q.z; dr0 += w[k] * q.w;
                 }
-                if (a1 >= 0) {
+                if (a1 >= 0 && ok) {
                     const float4* __restrict__ s1 = (a1 < n ? H + (size_t)a1 * L : VR) + b;
 #pragma unroll
                     for (int k = 0; k < SW; ++k) {
@@ -455,9 +496,8 @@ __device__ __forceinline__ void hi_f32_body(const SolverView& v, const double* _
                 CB2 = w0 * c0 + w1 * dc0 + w2 * c1 + w3 * dc1;
                 RB2 = w0 * r0 + w1 * dr0 + w2 * r1 + w3 * dr1;
             }
-            const float f1a = fp1(v.poly, CB1), f2a = fp2(v.poly, CB1);
-            const float f1b = fp1(v.poly, CB2), f2b = fp2(v.poly, CB2);
-            const float nui = nu32[i];
+            float f1a, f2a, f1b, f2b;
+            fp12_pair(v.poly, CB1, CB2, f1a, f2a, f1b, f2b);
             acc[0].add(nui * (KA1 * CB1));
             acc[1].add(nui * (KA2 * CB2));
             acc[2].add(nui * (DA1 * RB1));
@@ -497,9 +537,13 @@ __global__ void __launch_bounds__(HI_THREADS, 1) k_hi_f32(SolverView v, const do
 }
 
 // Batched: one persistent launch per stage over the units of every slot of the batch
-// table; each CTA takes an equal share of the batch's pairs (batch_for_my_units).
+// table; each CTA takes an equal share of the batch's pairs (batch_for_my_units). The slot
+// loop's state stays live around the body, so the batched kernels run 384-thread CTAs
+// (up to 168 registers a thread): with 512 threads (128 registers) they spilled.
+constexpr int BATCH_THREADS = 384;
+
 template <int SW, int PREC>
-__global__ void __launch_bounds__(HI_THREADS, 1) k_batch_hi(const BatchTable* __restrict__ bt, int stg) {
+__global__ void __launch_bounds__(BATCH_THREADS, 1) k_batch_hi(const BatchTable* __restrict__ bt, int stg) {
     __shared__ __align__(16) SolverView sview;
     batch_for_my_units(bt, stg, [&](int k, int lb, int le) {
         __syncthreads();  // the previous slot's shared-memory data are no longer read
@@ -612,7 +656,7 @@ int batch_hi_config(int precision, int sw, int max_L, int max_cap, int* grid_cta
     if (sm > (size_t)max_optin) return DMFE_ERR_UNSUPPORTED;
     DMFE_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int per_sm = 0;
-    DMFE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, HI_THREADS, sm));
+    DMFE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BATCH_THREADS, sm));
     if (per_sm < 1) return DMFE_ERR_UNSUPPORTED;
     *grid_ctas = nsm * per_sm;
     *smem = sm;
@@ -623,14 +667,14 @@ int launch_batch_hi(const BatchTable* bt, int precision, int sw, int stg, int gr
     if (precision == DMFE_DOUBLE_FLOAT) return launch_batch_hi_df(bt, sw, stg, grid, smem, s);
     const bool f64 = precision == DMFE_FP64;
     switch (sw) {
-        case 4: if (f64) k_batch_hi<4, DMFE_FP64><<<grid, HI_THREADS, smem, s>>>(bt, stg);
-                else k_batch_hi<4, DMFE_FP32_COMPENSATED><<<grid, HI_THREADS, smem, s>>>(bt, stg); break;
-        case 6: if (f64) k_batch_hi<6, DMFE_FP64><<<grid, HI_THREADS, smem, s>>>(bt, stg);
-                else k_batch_hi<6, DMFE_FP32_COMPENSATED><<<grid, HI_THREADS, smem, s>>>(bt, stg); break;
-        case 8: if (f64) k_batch_hi<8, DMFE_FP64><<<grid, HI_THREADS, smem, s>>>(bt, stg);
-                else k_batch_hi<8, DMFE_FP32_COMPENSATED><<<grid, HI_THREADS, smem, s>>>(bt, stg); break;
-        case 10: if (f64) k_batch_hi<10, DMFE_FP64><<<grid, HI_THREADS, smem, s>>>(bt, stg);
-                 else k_batch_hi<10, DMFE_FP32_COMPENSATED><<<grid, HI_THREADS, smem, s>>>(bt, stg); break;
+        case 4: if (f64) k_batch_hi<4, DMFE_FP64><<<grid, BATCH_THREADS, smem, s>>>(bt, stg);
+                else k_batch_hi<4, DMFE_FP32_COMPENSATED><<<grid, BATCH_THREADS, smem, s>>>(bt, stg); break;
+        case 6: if (f64) k_batch_hi<6, DMFE_FP64><<<grid, BATCH_THREADS, smem, s>>>(bt, stg);
+                else k_batch_hi<6, DMFE_FP32_COMPENSATED><<<grid, BATCH_THREADS, smem, s>>>(bt, stg); break;
+        case 8: if (f64) k_batch_hi<8, DMFE_FP64><<<grid, BATCH_THREADS, smem, s>>>(bt, stg);
+                else k_batch_hi<8, DMFE_FP32_COMPENSATED><<<grid, BATCH_THREADS, smem, s>>>(bt, stg); break;
+        case 10: if (f64) k_batch_hi<10, DMFE_FP64><<<grid, BATCH_THREADS, smem, s>>>(bt, stg);
+                 else k_batch_hi<10, DMFE_FP32_COMPENSATED><<<grid, BATCH_THREADS, smem, s>>>(bt, stg); break;
         default: return DMFE_ERR_UNSUPPORTED;
     }
     DMFE_CUDA_TRY(cudaGetLastError());

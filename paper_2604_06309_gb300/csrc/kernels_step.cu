@@ -601,6 +601,7 @@ __device__ __forceinline__ void sp_residual_body(const SolverView& v, int from_s
     const int lane = threadIdx.x & 31;
     const int nw = ncta * (blockDim.x >> 5);
     for (int n = 1 + cta * (blockDim.x >> 5) + (threadIdx.x >> 5); n <= last; n += nw) {
+        if (!DMFE_IN_BOUNDS(v.st, n + 1 < N && N <= v.cap, 31)) continue;
         const double h1 = ht[n] - ht[n - 1], h2 = ht[n + 1] - ht[n];
         const dbl4* a = H + (size_t)(n - 1) * L;
         const dbl4* b = H + (size_t)n * L;
@@ -706,6 +707,7 @@ __device__ __forceinline__ void sp_compact_body(const SolverView& v, int cta, in
     for (long long q = cta * (long long)blockDim.x + threadIdx.x; q < tot; q += (long long)ncta * blockDim.x) {
         const int k = (int)(q / L), i = (int)(q % L);
         if (!v.keep[k]) continue;
+        if (!DMFE_IN_BOUNDS(v.st, v.newidx[k] >= 0 && v.newidx[k] < v.cap && N <= v.cap, 32)) continue;
         const size_t dst = (size_t)v.newidx[k] * L + i;
         v.hist[nxt][dst] = v.hist[act][q];
         if (v.hist32[act]) v.hist32[nxt][dst] = v.hist32[act][q];

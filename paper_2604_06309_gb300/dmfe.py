@@ -12,7 +12,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libdmfe.so")
+# DMFE_LIBRARY selects another build of the same ABI, e.g. the bounds-checked
+# libdmfe_checked.so next to this file
+LIB_PATH = os.environ.get("DMFE_LIBRARY") or os.path.join(_HERE, "libdmfe.so")
+CHECKED_LIB_PATH = os.path.join(_HERE, "libdmfe_checked.so")
 
 DMFE_OK = 0
 DMFE_ERR_ARG = -1
@@ -57,7 +60,7 @@ class dmfe_stats_t(ctypes.Structure):
                 ("sparsify_passes", ctypes.c_longlong), ("slices_removed", ctypes.c_longlong),
                 ("forced_removals", ctypes.c_longlong), ("n_slices", _i), ("status", _i),
                 ("L", _i), ("history_cap", _i), ("s", _i), ("precision", _i), ("method", _i),
-                ("t_switch", _d), ("rk_switch_dt", _d), ("step_graph", _i)]
+                ("t_switch", _d), ("rk_switch_dt", _d), ("step_graph", _i), ("bounds_site", _i)]
 
 
 class dmfe_result(ctypes.Structure):
@@ -104,6 +107,7 @@ _SIGS = {
     "dmfe_batch_solver": (_p, [_p, _i]),
     "dmfe_batch_step": (_i, [_p, _i]),
     "dmfe_batch_poll": (_i, [_p, _ip, _dp, _ip]),
+    "dmfe_batch_autotune": (_i, [_p, _i, _ip, _dp]),
     "dmfe_footprint": (ctypes.c_ulonglong, [ctypes.POINTER(dmfe_params)]),
     "dmfe_server_start": (_i, [_i, _i, _i, _i, _i, ctypes.c_ulonglong, _i, ctypes.POINTER(_p)]),
     "dmfe_server_submit": (_i, [_p, ctypes.POINTER(dmfe_params), _d, _d, ctypes.POINTER(ctypes.c_longlong)]),
@@ -226,6 +230,15 @@ class Batch:
         _check(self._lib.dmfe_batch_poll(self.h, ctypes.cast(st, _ip), _ptr(tt), ctypes.byref(run)),
                "dmfe_batch_poll")
         return np.array(st[:], dtype=int), tt, run.value
+
+    def autotune(self, steps=4):
+        """dmfe_batch_autotune: (chosen unit size, {candidate: ms per batched step}).
+        The timed steps advance the slots; 0 means one unit per output index."""
+        c = _i()
+        ms = (_d * 5)()
+        _check(self._lib.dmfe_batch_autotune(self.h, int(steps), ctypes.byref(c), ctypes.cast(ms, _dp)),
+               "dmfe_batch_autotune")
+        return c.value, {k: ms[q] for q, k in enumerate((0, 256, 512, 1024, 2048))}
 
     def run(self, poll_every=16):
         """Step until no slot is running."""

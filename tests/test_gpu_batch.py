@@ -14,12 +14,12 @@ CASES = [  # (f, T, L, cap, grid t_max, t_max)
 ]
 
 
-def _alone(case, precision, tol):
+def _alone(case, precision, tol, hi_chunk=0):
     from paper_2604_06309_gb300 import Solver
     f, T, L, cap, gtm, tmax = case
-    # a batch slot runs one work unit per output index (hi_chunk = L): the same here, so
-    # that the summation order, and hence every bit, agrees
-    sv = Solver(f, T, L, gtm, history_cap=cap, precision=precision, hi_chunk=L)
+    # a batch slot runs one work unit per output index (hi_chunk = L) unless given a unit
+    # size: the same here, so that the summation order, and hence every bit, agrees
+    sv = Solver(f, T, L, gtm, history_cap=cap, precision=precision, hi_chunk=hi_chunk or L)
     assert sv.integrate(tmax, tol) == 0
     out = sv.get_history()
     st = sv.stats()
@@ -44,6 +44,31 @@ def test_batch_is_bitwise_equal_to_solo_runs(precision):
         for x, y in zip(got, ref):
             assert np.array_equal(x, y)
         assert b.solver(k).stats()["sparsify_passes"] == st["sparsify_passes"]
+    b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df"])
+def test_autotuned_units_keep_batch_equal_to_solo_runs(precision):
+    """The batch autotuner's choice, given to a fresh batch, keeps every slot bitwise equal
+    to the same solve run alone with that unit size."""
+    need_gpu()
+    from paper_2604_06309_gb300 import Batch
+    tol = 1e-8
+    a = Batch(8, 129, 64, precision=precision)
+    for (f, T, L, cap, gtm, tmax) in CASES:
+        a.add(f, T, L, gtm, tmax, tol, history_cap=cap)
+    a.step(20)
+    chunk, ms = a.autotune(2)
+    a.close()
+    assert chunk in ms and all(v > 0 for v in ms.values())
+    b = Batch(8, 129, 64, precision=precision)
+    slots = [b.add(f, T, L, gtm, tmax, tol, history_cap=cap, hi_chunk=chunk) for (f, T, L, cap, gtm, tmax) in CASES]
+    b.run()
+    for case, k in zip(CASES, slots):
+        ref, st = _alone(case, precision, tol, hi_chunk=chunk)
+        got = b.solver(k).get_history()
+        for x, y in zip(got, ref):
+            assert np.array_equal(x, y)
     b.close()
 
 
