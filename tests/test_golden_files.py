@@ -11,7 +11,7 @@ import pytest
 from oracle import solver as OS
 
 HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-FILES = ["pure3_T0.8_L129.json", "mixed34_T0.5_L2049.json"]
+FILES = ["pure3_T0.8_L129.json", "mixed34_T0.5_L2049.json", "mixed34_T0.5_L4097.json"]
 
 
 def _load(name):
@@ -44,6 +44,24 @@ def test_stored_solves_have_the_invariants(name):
             p, q = next(iter(coefs.items()))
             if q == 0.5:
                 assert abs(cp["mu"] - (c["T"] - p * cp["E"])) < 1e-8
+
+
+@pytest.mark.parametrize("name", ["mixed34_T0.5_L2049.json", "mixed34_T0.5_L4097.json"])
+def test_early_steps_follow_the_step_rule(name):
+    """Sec. 3.5 step rule (reading R7): from dt0 = 1e-4 an accepted step with eps_RK < tol/2
+    multiplies dt by 1.01, and the last step is shortened to land on the target. Before the
+    first checkpoint of the benchmark-grid quenches nothing is rejected or removed, so the
+    stored slice times are the partial sums 1e-4 (1.01^k - 1) / 0.01."""
+    g = _load(name)
+    cp = g["checkpoints"][0]
+    st = cp["stats"]
+    assert st["steps_rejected"] == 0 and st["slices_removed"] == 0
+    ts = np.array(cp["slice_times"])
+    k = np.arange(len(ts) - 1)
+    expect = 1e-4 * (1.01 ** k - 1.0) / 0.01
+    assert len(ts) == st["steps_accepted"] + 1
+    assert np.max(np.abs(ts[:-1] - expect) / np.maximum(expect, 1e-300)) < 1e-13
+    assert ts[-1] == cp["t"] and ts[-1] - ts[-2] <= 1e-4 * 1.01 ** (len(ts) - 2) * (1 + 1e-13)
 
 
 def test_small_quench_first_checkpoint_reproduces():
