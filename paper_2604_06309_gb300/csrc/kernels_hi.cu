@@ -414,6 +414,44 @@ __device__ __forceinline__ void hi_f32_body(const SolverView& v, const double* _
                 nh0 = H0[in];
                 nh1 = H1 ? H1[in] : srow[in];
             }
+            // ---- B2 slice walk and stencil base. Up to stencil width 6 the gathers are
+            // issued here, first, so that the A and B1 arithmetic below covers their
+            // latency; wider stencils load them where they are used (holding 2 x SW gathered
+            // entries across that arithmetic would spill registers)
+            constexpr bool kEarly = SW <= 6;
+            int a0 = 0, a1 = -1, b3 = 0;
+            float sg = 0.f, hh = 0.f, ub = 0.f;
+            bool ok3 = true;
+            float4 g0[kEarly ? SW : 1], g1[kEarly ? SW : 1];
+            auto walk = [&]() {
+                // complement of phi2: 1 - phi2 = omega_j omega_i; slice k holds v_k = (t - t_k)/t
+                const float uc = omj * omi;
+                if (kmax >= 0) {
+                    const int cell = (int)(pp2 >> FIX_FRAC_BITS);
+                    int k = DMFE_IN_BOUNDS(v.st, cell < L, 14) ? scell[cell] : 0;
+                    while (k < kmax && sv[k + 1] >= uc) ++k;
+                    while (k > 0 && sv[k] < uc) --k;
+                    sg = (sv[k] - uc) * sinv[k];
+                    hh = sdt[k];
+                    a0 = k; a1 = k + 1;
+                }
+                b3 = fix_stencil<SW>(pp3, L, ub);
+                ok3 = DMFE_IN_BOUNDS(v.st, a0 >= 0 && a0 < n && a1 < nsl && b3 >= 0 && b3 <= L - SW, 15);
+            };
+            if constexpr (kEarly) {
+                walk();
+                const float4* __restrict__ s0 = H + (size_t)(ok3 ? a0 : 0) * L + (ok3 ? b3 : 0);
+#pragma unroll
+                for (int k = 0; k < SW; ++k) g0[k] = s0[k];
+                if (a1 >= 0 && ok3) {
+                    const float4* __restrict__ s1 = (a1 < n ? H + (size_t)a1 * L : VR) + b3;
+#pragma unroll
+                    for (int k = 0; k < SW; ++k) g1[k] = s1[k];
+                } else {
+#pragma unroll
+                    for (int k = 0; k < SW; ++k) g1[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
             // ---- B1 (h1 is the stage row's entry when a1 < 0; only its value is used)
             float CB1 = bw0 * h0.x + bw1 * h0.y;
             float RB1 = bw0 * h0.z + bw1 * h0.w;
@@ -424,6 +462,7 @@ __device__ __forceinline__ void hi_f32_body(const SolverView& v, const double* _
                 CB1 += bw2 * h1.z;
                 RB1 += bw2 * h1.w;
             }
+            // ---- A1, A2: the stage row at phi1 and phi2
             float KA1 = 0.f, DA1 = 0.f, CA1 = 0.f, RA1 = 0.f;
             {
                 float uu;
@@ -450,46 +489,32 @@ __device__ __forceinline__ void hi_f32_body(const SolverView& v, const double* _
                     KA2 += w[k] * q.x; RA2 += w[k] * q.w;
                 }
             }
+            if constexpr (!kEarly) walk();
+            // ---- B2: the theta stencil at psi on both slices, then cubic Hermite in time
             float CB2, RB2;
             {
-                // complement of phi2: 1 - phi2 = omega_j omega_i; slice k holds v_k = (t - t_k)/t
-                const float uc = omj * omi;
-                int a0, a1;
-                float w0, w1, w2, w3;
-                if (kmax < 0) {
-                    // a single stored slice and the stage at its time
-                    a0 = 0; a1 = -1; w0 = 1.f; w1 = 0.f; w2 = 0.f; w3 = 0.f;
-                } else {
-                    const int cell = (int)(pp2 >> FIX_FRAC_BITS);
-                    int k = DMFE_IN_BOUNDS(v.st, cell < L, 14) ? scell[cell] : 0;
-                    while (k < kmax && sv[k + 1] >= uc) ++k;
-                    while (k > 0 && sv[k] < uc) --k;
-                    float sg = (sv[k] - uc) * sinv[k];
-                    float hh = sdt[k];
-                    float om = 1.f - sg;
-                    a0 = k; a1 = k + 1;
+                float w0 = 1.f, w1 = 0.f, w2 = 0.f, w3 = 0.f;  // a single slice: its value
+                if (kmax >= 0) {
+                    const float om = 1.f - sg;
                     w0 = (1.f + 2.f * sg) * om * om;
                     w1 = sg * om * om * hh;
                     w2 = sg * sg * (3.f - 2.f * sg);
                     w3 = sg * sg * (sg - 1.f) * hh;
                 }
-                float uu;
-                const int b = fix_stencil<SW>(pp3, L, uu);
                 float w[SW];
-                lagrange<SW>(uu, w);
+                lagrange<SW>(ub, w);
                 float c0 = 0.f, dc0 = 0.f, r0 = 0.f, dr0 = 0.f, c1 = 0.f, dc1 = 0.f, r1 = 0.f, dr1 = 0.f;
-                const bool ok = DMFE_IN_BOUNDS(v.st, a0 >= 0 && a0 < n && a1 < nsl && b >= 0 && b <= L - SW, 15);
-                const float4* __restrict__ s0 = H + (size_t)a0 * L + b;
+                const float4* __restrict__ s0 = H + (size_t)a0 * L + b3;
 #pragma unroll
-                for (int k = 0; k < (ok ? SW : 0); ++k) {
-                    float4 q = s0[k];
+                for (int k = 0; k < (ok3 ? SW : 0); ++k) {
+                    const float4 q = kEarly ? g0[kEarly ? k : 0] : s0[k];
                     c0 += w[k] * q.x; dc0 += w[k] * q.y; r0 += w[k] * q.z; dr0 += w[k] * q.w;
                 }
-                if (a1 >= 0 && ok) {
-                    const float4* __restrict__ s1 = (a1 < n ? H + (size_t)a1 * L : VR) + b;
+                if (a1 >= 0 && ok3) {
+                    const float4* __restrict__ s1 = (a1 < n ? H + (size_t)a1 * L : VR) + b3;
 #pragma unroll
                     for (int k = 0; k < SW; ++k) {
-                        float4 q = s1[k];
+                        const float4 q = kEarly ? g1[kEarly ? k : 0] : s1[k];
                         c1 += w[k] * q.x; dc1 += w[k] * q.y; r1 += w[k] * q.z; dr1 += w[k] * q.w;
                     }
                 }
