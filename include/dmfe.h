@@ -17,7 +17,10 @@
  *  - Rows are double arrays of length L in grid order (theta ascending). Histories
  *    are row-major [n][L].
  *  - One solver must not be used from two host threads at once; distinct solvers
- *    are independent (the library keeps no global state besides the CUDA context).
+ *    are independent. The library's only global state besides the CUDA context is a
+ *    mutex-guarded cache of stencil tables: solvers on one device with the same grid,
+ *    stencil and precision share one read-only copy (reference-counted; freed with the
+ *    last of them), and a solver's stream waits for the kernel that built the copy.
  *  - The solver owns all its device memory; dmfe_destroy frees it.
  */
 #ifndef DMFE_H
@@ -94,9 +97,14 @@ typedef struct {
                                    3.3066) reaches the spectral bound ||J|| <= 4 sqrt(f''(1))
                                    of Sec. 3.5; no switch when f''(1) <= 0              */
     int           hi_chunk;     /* summation indices per work unit of the history-integral
-                                   kernel, >= 32; 0 (default): chosen from L and the precision
-                                   for a single solve, L for a batch slot. Changes only the
-                                   summation order (see dmfe_autotune)                   */
+                                   kernel, >= 32; -1: the flat split (the L^2 pairs cut into one
+                                   equal segment per warp of the launch, so every SM gets the
+                                   same work; single solves with L >= 512 and at least 256
+                                   pairs per warp, else as 0); 0 (default): the flat split
+                                   where it applies, else chosen from L and the precision, for
+                                   a single solve; L for a batch slot (a batch slot given -1
+                                   or 0 takes L). Changes only the summation order (see
+                                   dmfe_autotune)                                         */
     int           interp;       /* DMFE_INTERP_*: the theta-stencil scheme (default Lagrange in
                                    the index). The other schemes need DMFE_FP64 (their
                                    weights live in the FP64 stencil tables); otherwise
@@ -251,9 +259,9 @@ int dmfe_checkpoint(dmfe_solver* h, const char* path);
 int dmfe_restore(const char* path, void* stream, dmfe_solver** out);
 
 /* Autotune the work-unit size of the history-integral kernel (summation indices per
- * unit: the candidates 32, 64, ..., 4096, L and L/P for P = 2..16, at least 32)
- * by timing the kernel on the
- * solver's current history and stage row, and keep the fastest. Results are cached per
+ * unit: the candidates 32, 64, ..., 4096, L and L/P for P = 2..16, at least 32, and the flat
+ * split -1 where it applies) by timing the kernel on the solver's current history and
+ * stage row, and keep the fastest. Results are cached per
  * (L, history_cap, s, precision) for the process. Changes the summation order of the
  * sums S (rounding-level differences only). *chunk (may be NULL) receives the choice. */
 int dmfe_autotune(dmfe_solver* h, int* chunk);
@@ -308,7 +316,10 @@ int dmfe_batch_poll(dmfe_batch* b, int* status, double* t, int* running);
 int dmfe_batch_autotune(dmfe_batch* b, int steps, int* chunk, double* ms_per_step);
 
 /* Device bytes a solver with these parameters allocates (dmfe_create), rounded up the way
- * large device allocations are; used for admission by footprint. 0 on invalid input. */
+ * large device allocations are; used for admission by footprint. 0 on invalid input. An
+ * upper bound: the stencil tables (three [L][L] arrays, the bulk of the footprint in FP64)
+ * are shared by every solver on the device with the same grid (L, grid_t_max, alpha, delta),
+ * stencil (s, interp, fh_d) and precision, and are allocated only by the first of them. */
 unsigned long long dmfe_footprint(const dmfe_params* p);
 
 /* A serving loop over a batch (continuous batching): a host worker thread admits queued

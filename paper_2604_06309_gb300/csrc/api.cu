@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "dmfe_internal.h"
+#include "hi_units.h"
 
 struct dmfe_solver {
     dmfe_params p{};
@@ -31,6 +32,8 @@ struct dmfe_solver {
     DevState* hstate = nullptr;  // pinned mirror of the device state
     double* scratch = nullptr;   // device [4L + 16]
     std::vector<void*> allocs;
+    bool table_ref = false;      // holds a reference to a cached stencil-table entry
+    std::tuple<int, int, int, int, int, int, double, double, double> table_key;
 };
 
 namespace {
@@ -42,6 +45,77 @@ int dev_alloc(dmfe_solver* h, void** p, size_t bytes) {
         return DMFE_ERR_OOM;
     }
     h->allocs.push_back(*p);
+    return DMFE_OK;
+}
+
+// ---- stencil tables shared by solvers with the same key ------------------------------
+// The stencil tables (FP64 weight entries, double-float positions or FP32 fixed-point
+// positions for phi1, phi2 and psi) depend only on the device, the precision, the grid
+// (L, gamma, alpha, delta) and the stencil (s, scheme, Floater-Hormann degree), so solvers
+// that agree on all of them -- the members of a sweep over T and f at one grid -- share one
+// copy. Entries are reference-counted (freed with their last solver) and carry an event
+// recorded after the table kernel: a solver that finds an entry orders its stream after it.
+using TableKey = std::tuple<int, int, int, int, int, int, double, double, double>;
+struct TableEntry {
+    void* t[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ready = nullptr;
+    int refs = 0;
+};
+std::mutex g_table_mutex;
+std::map<TableKey, TableEntry> g_tables;
+
+void release_tables(dmfe_solver* h);
+
+// The solver's three stencil tables: an existing entry of its key (its stream then waits
+// for the entry's table kernel), or a new entry built by the table kernel on the solver's
+// stream. Lookup and build are one critical section, so an entry is visible only once its
+// kernel and event are queued. Run after the grid arrays have been queued on the stream.
+int acquire_tables(dmfe_solver* h, size_t fp64_table_bytes) {
+    SolverView& v = h->v;
+    const int L = v.L;
+    const size_t LL = (size_t)L * L;
+    const dmfe_params& pin = h->p;
+    int dev = 0;
+    DMFE_CUDA_TRY(cudaGetDevice(&dev));
+    h->table_key = TableKey(dev, v.precision, L, v.s, v.interp,
+                            (v.interp == DMFE_INTERP_FH_INDEX || v.interp == DMFE_INTERP_FH_THETA) ? v.fh_d : 0,
+                            v.gamma, pin.alpha, pin.delta);
+    const size_t tb = v.precision == DMFE_FP64 ? fp64_table_bytes
+                      : (v.precision == DMFE_FP32_COMPENSATED ? LL * sizeof(uint32_t) : LL * sizeof(df));
+    std::lock_guard<std::mutex> lock(g_table_mutex);
+    auto it = g_tables.find(h->table_key);
+    if (it != g_tables.end()) {
+        DMFE_CUDA_TRY(cudaStreamWaitEvent(h->stream, it->second.ready, 0));
+    } else {
+        TableEntry e;
+        for (int q = 0; q < 3; ++q)
+            if (cudaMalloc(&e.t[q], tb) != cudaSuccess) {
+                cudaGetLastError();
+                for (int r = 0; r < q; ++r) cudaFree(e.t[r]);
+                return DMFE_ERR_OOM;
+            }
+        if (cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming) != cudaSuccess) {
+            for (void* q : e.t) cudaFree(q);
+            return DMFE_ERR_CUDA;
+        }
+        it = g_tables.emplace(h->table_key, e).first;
+    }
+    TableEntry& e = it->second;
+    const bool build = e.refs == 0;
+    e.refs += 1;
+    h->table_ref = true;
+    if (v.precision == DMFE_FP64) {
+        v.wt1 = (unsigned char*)e.t[0]; v.wt2 = (unsigned char*)e.t[1]; v.wt3 = (unsigned char*)e.t[2];
+    } else if (v.precision == DMFE_FP32_COMPENSATED) {
+        v.p1 = (uint32_t*)e.t[0]; v.p2 = (uint32_t*)e.t[1]; v.p3 = (uint32_t*)e.t[2];
+    } else {
+        v.q1 = (df*)e.t[0]; v.q2 = (df*)e.t[1]; v.q3 = (df*)e.t[2];
+    }
+    if (build) {
+        const int rc = launch_tables(v, h->stream);
+        if (rc) return rc;
+        DMFE_CUDA_TRY(cudaEventRecord(e.ready, h->stream));
+    }
     return DMFE_OK;
 }
 
@@ -117,7 +191,7 @@ int validate(const dmfe_params* p) {
     if (p->integrator != DMFE_RK_AUTO && p->integrator != DMFE_RK_DP5 && p->integrator != DMFE_RK_SSPRK104)
         return DMFE_ERR_ARG;
     if (!(p->rk_switch_dt >= 0.0)) return DMFE_ERR_ARG;
-    if (p->hi_chunk != 0 && p->hi_chunk < kMinChunk) return DMFE_ERR_ARG;
+    if (p->hi_chunk != 0 && p->hi_chunk != kFlatSplit && p->hi_chunk < kMinChunk) return DMFE_ERR_ARG;
     if (p->interp < DMFE_INTERP_LAGRANGE_INDEX || p->interp > DMFE_INTERP_FH_THETA) return DMFE_ERR_ARG;
     if ((p->interp == DMFE_INTERP_FH_INDEX || p->interp == DMFE_INTERP_FH_THETA) &&
         (p->fh_d < 0 || p->fh_d > p->s - 1))
@@ -214,18 +288,7 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
     TRY(dev_alloc(h, &p, L * sizeof(float))); v.omega32 = (float*)p;
     TRY(dev_alloc(h, &p, L * sizeof(float))); v.nu32 = (float*)p;
     const size_t wts = 8 + 8 * (size_t)pin->s;  // bytes per stencil entry
-    if (v.precision == DMFE_FP64) {
-        TRY(dev_alloc(h, &p, LL * wts)); v.wt1 = (unsigned char*)p;
-        TRY(dev_alloc(h, &p, LL * wts)); v.wt2 = (unsigned char*)p;
-        TRY(dev_alloc(h, &p, LL * wts)); v.wt3 = (unsigned char*)p;
-    } else if (v.precision == DMFE_FP32_COMPENSATED) {
-        TRY(dev_alloc(h, &p, LL * sizeof(uint32_t))); v.p1 = (uint32_t*)p;
-        TRY(dev_alloc(h, &p, LL * sizeof(uint32_t))); v.p2 = (uint32_t*)p;
-        TRY(dev_alloc(h, &p, LL * sizeof(uint32_t))); v.p3 = (uint32_t*)p;
-    } else {
-        TRY(dev_alloc(h, &p, LL * sizeof(df))); v.q1 = (df*)p;
-        TRY(dev_alloc(h, &p, LL * sizeof(df))); v.q2 = (df*)p;
-        TRY(dev_alloc(h, &p, LL * sizeof(df))); v.q3 = (df*)p;
+    if (v.precision == DMFE_DOUBLE_FLOAT) {
         TRY(dev_alloc(h, &p, L * sizeof(df))); v.omega_df = (df*)p;
         TRY(dev_alloc(h, &p, L * sizeof(df))); v.nu_df = (df*)p;
         TRY(dev_alloc(h, &p, L * sizeof(dfrow))); v.rowdf = (dfrow*)p;
@@ -267,7 +330,16 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
     if (!v.cell) { TRY(dev_alloc(h, &p, L * sizeof(int))); v.cell = (int*)p; }
     TRY(dev_alloc(h, &p, (size_t)L * sizeof(int))); v.jcount = (int*)p;
     DMFE_CUDA_TRY(cudaMemsetAsync(v.jcount, 0, (size_t)L * sizeof(int), h->stream));
-    v.hi_chunk = pin->hi_chunk > 0 ? (pin->hi_chunk < L ? pin->hi_chunk : L) : default_chunk(v.precision, L);
+    // work units of a single solve: the flat split wherever it gives every warp at least 256
+    // pairs (all SMs and warp slots get equal work), else units; dmfe_autotune compares it
+    // with the unit sizes
+    int nsm = 0, dev_ = 0;
+    DMFE_CUDA_TRY(cudaGetDevice(&dev_));
+    DMFE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_));
+    const bool flat_ok = flat_split_fits(L, (long long)nsm * 16);
+    if (pin->hi_chunk == kFlatSplit) v.hi_chunk = flat_ok ? kFlatSplit : default_chunk(v.precision, L);
+    else if (pin->hi_chunk > 0) v.hi_chunk = pin->hi_chunk < L ? pin->hi_chunk : L;
+    else v.hi_chunk = flat_ok ? kFlatSplit : default_chunk(v.precision, L);
     if (const char* e = std::getenv("DMFE_HI_CHUNK")) {
         const int c = std::atoi(e);
         if (c >= kMinChunk) v.hi_chunk = c < L ? c : L;
@@ -303,18 +375,40 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
     h->hstate->method = pin->integrator == DMFE_RK_SSPRK104 ? 1 : 0;
     h->hstate->t_switch = -1.0;
     TRY(write_state(h));
-    TRY(launch_tables(v, h->stream));
+    TRY(acquire_tables(h, LL * wts));
     TRY(launch_initial_slice(v, h->stream));
-    TRY(hi_config(v, &h->hi_grid, &h->hi_smem));
+    if (hi_config(v, &h->hi_grid, &h->hi_smem) != DMFE_OK) {
+        // (a flat split that the launch shape cannot hold falls back to units)
+        if (v.hi_chunk != kFlatSplit) return DMFE_ERR_UNSUPPORTED;
+        v.hi_chunk = default_chunk(v.precision, L);
+        TRY(hi_config(v, &h->hi_grid, &h->hi_smem));
+    }
     DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
     DMFE_CUDA_TRY(cudaGetLastError());
     return DMFE_OK;
+}
+
+void release_tables(dmfe_solver* h) {
+    if (!h->table_ref) return;
+    std::lock_guard<std::mutex> lock(g_table_mutex);
+    auto it = g_tables.find(h->table_key);
+    h->table_ref = false;
+    if (it == g_tables.end()) return;
+    if (--it->second.refs == 0) {
+        // the last user: other solvers' work on these tables has been synchronised by their
+        // own destroy; this solver's stream was synchronised by the caller
+        if (it->second.ready) cudaEventSynchronize(it->second.ready);
+        for (void* q : it->second.t) cudaFree(q);
+        if (it->second.ready) cudaEventDestroy(it->second.ready);
+        g_tables.erase(it);
+    }
 }
 
 void destroy_impl(dmfe_solver* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
+    release_tables(h);
     for (void* p : h->allocs) cudaFree(p);
     if (h->hstate) cudaFreeHost(h->hstate);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -805,6 +899,7 @@ int dmfe_autotune(dmfe_solver* h, int* chunk_out) {
             const int cc = L / P;
             if (cc >= kMinChunk && std::find(cands.begin(), cands.end(), cc) == cands.end()) cands.push_back(cc);
         }
+        cands.push_back(kFlatSplit);  // tried where its launch shape fits (hi_config)
         cudaEvent_t e0, e1;
         DMFE_CUDA_TRY(cudaEventCreate(&e0));
         DMFE_CUDA_TRY(cudaEventCreate(&e1));
@@ -816,6 +911,10 @@ int dmfe_autotune(dmfe_solver* h, int* chunk_out) {
             int grid = 0;
             size_t sm = 0;
             rc = hi_config(v, &grid, &sm);
+            if (rc == DMFE_ERR_UNSUPPORTED && c == kFlatSplit) {
+                rc = DMFE_OK;  // this grid is too small for the flat split
+                continue;
+            }
             if (rc) break;
             float tot = 0.f;
             for (int it = 0; it < 4 && !rc; ++it) {

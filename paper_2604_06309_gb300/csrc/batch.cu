@@ -181,7 +181,7 @@ int dmfe_batch_add(dmfe_batch* b, const dmfe_params* p, double t_max, double tol
     q.stream = b->stream;
     // one unit per output index unless asked otherwise: a batch has parallelism across
     // slots, and larger units carry less per-unit reduction overhead
-    if (q.hi_chunk == 0) q.hi_chunk = q.L;
+    if (q.hi_chunk <= 0) q.hi_chunk = q.L;  // (the flat split is for single solves)
     dmfe_solver* h = nullptr;
     TRYB(dmfe_create(&q, &h));
     const int rc = launch_begin_integrate(solver_view(h), t_max, tol, b->stream);

@@ -12,7 +12,16 @@
 
 #include "dmfe_internal.h"
 
-__host__ __device__ __forceinline__ int hi_parts(int L, int chunk) { return L / chunk > 1 ? L / chunk : 1; }
+// Work-unit size value that selects the flat split (single solves only): the L^2 pairs in
+// row-major order (output index j, then summation index i) are cut into one equal segment
+// per warp of the launch, and a warp takes its segment row by row. The pieces of one row are
+// that output index's parts, in order. Every warp gets the same number of pairs, so all SMs
+// and warp slots finish together.
+constexpr int kFlatSplit = -1;
+
+__host__ __device__ __forceinline__ int hi_parts(int L, int chunk) {
+    return (chunk > 0 && L / chunk > 1) ? L / chunk : 1;
+}
 
 __device__ __forceinline__ void hi_unit_block(int L, int chunk, int* ub, int* ue) {
     const long long U = (long long)hi_parts(L, chunk) * L;
@@ -31,6 +40,44 @@ __device__ __forceinline__ void hi_unit_range(int u, int L, int chunk, int* j, i
     *i1 = p == P - 1 ? L : (p + 1) * chunk;
 }
 
+// Calls f(j, i0, i1, part, nparts) for each piece of work of this warp: the units [ub, ue)
+// of its CTA round-robin over the CTA's warps, or under the flat split the rows of the
+// warp's segment [g LL / G, (g + 1) LL / G) (G warps in the grid, g this warp). Segment s
+// holds pair q when s = ((q + 1) G - 1) / LL (integer division), so row j's parts are the
+// segments from that of its first pair to that of its last; G <= LL keeps every segment
+// non-empty.
+// The flat split needs at least 256 pairs per warp (8 per lane), which also keeps every
+// segment non-empty and a row's parts within the partial-sum buffer (L / 32 parts).
+__host__ __device__ __forceinline__ bool flat_split_fits(int L, long long warps) {
+    return warps > 0 && (long long)L * L >= 256 * warps && L >= 512;
+}
+
+template <typename F>
+__device__ __forceinline__ void hi_for_items(int L, int chunk, int ub, int ue, F&& f) {
+    if (chunk == kFlatSplit) {
+        const long long LL = (long long)L * L;
+        const long long G = (long long)gridDim.x * (blockDim.x >> 5);
+        const long long g = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        const long long q1 = (g + 1) * LL / G;
+        for (long long q = g * LL / G; q < q1;) {
+            const int j = (int)(q / L);
+            const long long rb = (long long)j * L;
+            const long long qe = q1 < rb + L ? q1 : rb + L;
+            const long long s0 = ((rb + 1) * G - 1) / LL;
+            const long long s1 = ((rb + L) * G - 1) / LL;
+            f(j, (int)(q - rb), (int)(qe - rb), (int)(g - s0), (int)(s1 - s0 + 1));
+            q = qe;
+        }
+        return;
+    }
+    const int P = hi_parts(L, chunk);
+    for (int u = ub + (threadIdx.x >> 5); u < ue; u += (int)(blockDim.x >> 5)) {
+        int j, i0, i1;
+        hi_unit_range(u, L, chunk, &j, &i0, &i1);
+        f(j, i0, i1, u / L, P);
+    }
+}
+
 // Sum over the warp of a double-float value (fixed butterfly, FP32 pipes only).
 __device__ __forceinline__ df df_warp_sum(df x) {
 #pragma unroll
@@ -41,11 +88,10 @@ __device__ __forceinline__ df df_warp_sum(df x) {
     return x;
 }
 
-// Called by one lane per unit with the reduced sums of that part.
-__device__ __forceinline__ void hi_finish_unit(const double (&sums)[9], double c_at_0, int u, int L, int chunk,
+// Called by one lane per piece of work with the reduced sums of part p (of P) of output
+// index j.
+__device__ __forceinline__ void hi_finish_part(const double (&sums)[9], double c_at_0, int j, int p, int P, int L,
                                                double* Spart, int* jcount, double* S) {
-    const int P = hi_parts(L, chunk);
-    const int j = u % L, p = u / L;
 #pragma unroll
     for (int r = 0; r < 9; ++r) Spart[((size_t)p * 9 + r) * L + j] = sums[r];
     if (p == 0) S[(size_t)9 * L + j] = c_at_0;

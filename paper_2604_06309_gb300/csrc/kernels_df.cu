@@ -285,9 +285,7 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
     const float bmax = (float)(L - SW);
 
     const int chunk = v.hi_chunk;
-    for (int u_ = ub + (threadIdx.x >> 5); u_ < ue; u_ += (int)(blockDim.x >> 5)) {
-        int j, i0, i1;
-        hi_unit_range(u_, L, chunk, &j, &i0, &i1);
+    hi_for_items(L, chunk, ub, ue, [&](int j, int i0, int i1, int part, int nparts) {
         // ---- per unit: B1 time weights prepared once per stage
         const df omj = omdf[j];
         int a0, a1;
@@ -477,8 +475,8 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
             const df x = df_warp_sum(dacc_get(acc[r]));
             sums[r] = lane == 0 ? df_to_d(x) : 0.0;
         }
-        if (lane == 0) hi_finish_unit(sums, df_to_d(c_at_0), u_, L, chunk, v.Spart, v.jcount, S);
-    }
+        if (lane == 0) hi_finish_part(sums, df_to_d(c_at_0), j, part, nparts, L, v.Spart, v.jcount, S);
+    });
 }
 
 __global__ void k_stage_prep(SolverView v, const double* __restrict__ row, double t_arg, int from_state) {
@@ -553,12 +551,15 @@ int hi_config_df(SolverView& v, int* grid_ctas, size_t* smem) {
     if (sm > (size_t)max_optin) return DMFE_ERR_UNSUPPORTED;
     DMFE_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int warps = 0;
-    const int want = hi_launch_shape((long long)hi_parts(v.L, v.hi_chunk) * v.L, nsm, DF_WARPS, &warps);
+    const bool flat = v.hi_chunk == kFlatSplit;
+    const int want = flat ? 0 : hi_launch_shape((long long)hi_parts(v.L, v.hi_chunk) * v.L, nsm, DF_WARPS, &warps);
+    if (flat) warps = DF_WARPS;
     int per_sm = 0;
     DMFE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, sm));
     if (per_sm < 1) return DMFE_ERR_UNSUPPORTED;
     const int cap = nsm * per_sm;
-    *grid_ctas = want < cap ? want : cap;
+    *grid_ctas = flat ? cap : (want < cap ? want : cap);
+    if (flat && !flat_split_fits(v.L, (long long)cap * warps)) return DMFE_ERR_UNSUPPORTED;
     v.hi_threads = warps * 32;
     *smem = sm;
     return DMFE_OK;

@@ -151,9 +151,7 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
     const double* __restrict__ nu = v.nu;
     const int chunk = v.hi_chunk;
 
-    for (int u = ub + (threadIdx.x >> 5); u < ue; u += (int)(blockDim.x >> 5)) {
-        int j, i0, i1;
-        hi_unit_range(u, L, chunk, &j, &i0, &i1);
+    hi_for_items(L, chunk, ub, ue, [&](int j, int i0, int i1, int part, int nparts) {
         // the stage time of B2, tau2 = phi2 t = theta_j t + (omega_j t) theta_i, by one FMA
         const double thj_t = theta[j] * t, omj_t = omega[j] * t;
         TimeW b1;
@@ -314,8 +312,8 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
         double sums[9];
 #pragma unroll
         for (int r = 0; r < 9; ++r) sums[r] = warp_sum(acc[r]);
-        if (lane == 0) hi_finish_unit(sums, c_at_0, u, L, chunk, v.Spart, v.jcount, S);
-    }
+        if (lane == 0) hi_finish_part(sums, c_at_0, j, part, nparts, L, v.Spart, v.jcount, S);
+    });
 }
 
 // ------------------------------------------------------------------ FP32 variant
@@ -372,9 +370,7 @@ __device__ __forceinline__ void hi_f32_body(const SolverView& v, const double* _
     const float* __restrict__ nu32 = v.nu32;
     const int chunk = v.hi_chunk;
 
-    for (int u = ub + (threadIdx.x >> 5); u < ue; u += (int)(blockDim.x >> 5)) {
-        int j, i0, i1;
-        hi_unit_range(u, L, chunk, &j, &i0, &i1);
+    hi_for_items(L, chunk, ub, ue, [&](int j, int i0, int i1, int part, int nparts) {
         const float omj = om32[j];
         TimeW b1d;
         float bw0, bw1, bw2, bw3;
@@ -541,8 +537,8 @@ __device__ __forceinline__ void hi_f32_body(const SolverView& v, const double* _
             const df x = df_warp_sum(fast_two_sum(acc[r].s, -acc[r].c));
             sums[r] = lane == 0 ? df_to_d(x) : 0.0;
         }
-        if (lane == 0) hi_finish_unit(sums, (double)c_at_0, u, L, chunk, v.Spart, v.jcount, S);
-    }
+        if (lane == 0) hi_finish_part(sums, (double)c_at_0, j, part, nparts, L, v.Spart, v.jcount, S);
+    });
 }
 
 template <int SW, bool LOGR>
@@ -630,12 +626,16 @@ int hi_config(SolverView& v, int* grid_ctas, size_t* smem) {
     if (sm > (size_t)max_optin) return DMFE_ERR_UNSUPPORTED;
     DMFE_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int warps = 0;
-    const int want = hi_launch_shape((long long)hi_parts(v.L, v.hi_chunk) * v.L, nsm, HI_WARPS, &warps);
+    const bool flat = v.hi_chunk == kFlatSplit;
+    const int want = flat ? 0 : hi_launch_shape((long long)hi_parts(v.L, v.hi_chunk) * v.L, nsm, HI_WARPS, &warps);
+    if (flat) warps = HI_WARPS;
     int per_sm = 0;
     DMFE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, sm));
     if (per_sm < 1) return DMFE_ERR_UNSUPPORTED;
     const int cap = nsm * per_sm;
-    *grid_ctas = want < cap ? want : cap;
+    // the flat split: every resident warp slot takes one equal segment of the pairs
+    *grid_ctas = flat ? cap : (want < cap ? want : cap);
+    if (flat && !flat_split_fits(v.L, (long long)cap * warps)) return DMFE_ERR_UNSUPPORTED;
     v.hi_threads = warps * 32;
     *smem = sm;
     return DMFE_OK;

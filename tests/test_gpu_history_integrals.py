@@ -117,7 +117,7 @@ def test_autotune_keeps_results(precision):
     t = hist[0][-1]
     S0, _ = sv.history_integrals(t, hist[1][-1], hist[3][-1])
     chunk = sv.autotune()
-    cands = {256, 512, 1024, L} | {L // P for P in range(2, 17) if L // P >= 256}
+    cands = {-1, 256, 512, 1024, L} | {L // P for P in range(2, 17) if L // P >= 256}  # -1: flat split
     assert chunk in cands
     S1, _ = sv.history_integrals(t, hist[1][-1], hist[3][-1])
     assert np.max(np.abs(S1 - S0)) < (1e-6 if precision == "fp32" else 1e-12)

@@ -331,3 +331,36 @@ def test_solve_variants_match_oracle_step_by_step(kw):
     assert np.max(np.abs(g.get_C(t, tp) - o.get_C(t, tp))) < 1e-9
     assert np.max(np.abs(g.get_R(t, tp) - o.get_R(t, tp))) < 1e-9
     g.close()
+
+
+def test_solvers_with_one_grid_share_their_stencil_tables():
+    """Solvers on one device with the same grid, stencil and precision share one copy of the
+    stencil tables (FP64 weight entries: 3 x L^2 x 40 B = 126 MB at L = 1025): a second
+    such solver allocates that much less, runs bitwise like a solver whose tables were built
+    for it alone, and keeps working after the solver that built the tables is destroyed."""
+    torch = need_gpu()
+    from paper_2604_06309_gb300 import Solver
+    L, gtm = 1025, 1e3
+    table_bytes = 3 * L * L * 40
+
+    def used():
+        torch.cuda.synchronize()
+        free, total = torch.cuda.mem_get_info()
+        return total - free
+
+    u0 = used()
+    a = Solver(PURE_3, 0.8, L, gtm, history_cap=64)
+    u1 = used()
+    b = Solver(MIXED_34, 0.5, L, gtm, history_cap=64)   # other f and T, the same grid
+    u2 = used()
+    assert (u1 - u0) - (u2 - u1) > 0.9 * table_bytes
+    a.close()                                           # the builder goes; b keeps the tables
+    assert b.integrate(0.05, 1e-8) == 0
+    got = b.get_history()
+    b.close()
+    c = Solver(MIXED_34, 0.5, L, gtm, history_cap=64)   # no sharer left: built afresh
+    assert c.integrate(0.05, 1e-8) == 0
+    ref = c.get_history()
+    c.close()
+    for x, y in zip(got, ref):
+        assert np.array_equal(x, y)
