@@ -101,4 +101,9 @@ __device__ __forceinline__ void dacc_add_df(dacc& a, df x) {
 }
 
 __device__ __forceinline__ df dacc_get(dacc a) { return fast_two_sum(a.s, a.lo); }
+
+// The accumulated value as a pair without renormalising (|lo| a few ulps of s): exact as a
+// sum, and fine as an operand of products and of df_add / dacc_add, whose error terms
+// absorb the larger low part (error <= n 2^-48 relative for an n-term sum).
+__device__ __forceinline__ df dacc_raw(dacc a) { return df{a.s, a.lo}; }
 #endif

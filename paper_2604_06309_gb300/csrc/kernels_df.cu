@@ -335,8 +335,8 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
                     dacc_add(c, bw2, r1.C);
                     dacc_add(r, bw2, r1.R);
                 }
-                CB1 = dacc_get(c);
-                RB1 = dacc_get(r);
+                CB1 = dacc_raw(c);
+                RB1 = dacc_raw(r);
             }
             // ---- A1: current row at phi1
             df KA1, DA1, CA1, RA1;
@@ -355,7 +355,7 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
                     dacc_add(c, w[m], q.C);
                     dacc_add(r, w[m], q.R);
                 }
-                KA1 = dacc_get(k); DA1 = dacc_get(d); CA1 = dacc_get(c); RA1 = dacc_get(r);
+                KA1 = dacc_raw(k); DA1 = dacc_raw(d); CA1 = dacc_raw(c); RA1 = dacc_raw(r);
             }
             // ---- A2: current row at phi2
             df KA2, RA2;
@@ -372,7 +372,7 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
                     dacc_add(k, w[m], q.K);
                     dacc_add(r, w[m], q.R);
                 }
-                KA2 = dacc_get(k); RA2 = dacc_get(r);
+                KA2 = dacc_raw(k); RA2 = dacc_raw(r);
             }
             // ---- B2: theta position psi on the slices around phi2 t (complement form)
             df CB2, RB2;
@@ -393,8 +393,10 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
                     const df om = df_add_f(df_neg(sg), 1.f);
                     const df om2 = df_mul(om, om), sg2 = df_mul(sg, sg);
                     s0 = k; s1 = k + 1;
-                    tw0 = df_mul(df_add_f(df_mul_f(sg, 2.f), 1.f), om2);
-                    tw2 = df_mul(sg2, df_add_f(df_mul_f(sg, -2.f), 3.f));
+                    // h01 = sg^2 (3 - 2 sg) and h00 = 1 - h01 (the value weights sum to one);
+                    // the doubling of sg is exact
+                    tw2 = df_mul(sg2, df_add_f(df{-2.f * sg.hi, -2.f * sg.lo}, 3.f));
+                    tw0 = df_add_f(df_neg(tw2), 1.f);
                     const df a1 = df_mul(sg, om2), a3 = df_mul(sg2, df_add_f(sg, -1.f));
                     if (k < n - 1) {
                         // a stored interval: its width in FP32 (the derivative terms are
@@ -427,7 +429,7 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
                         dacc_add(ar, w[m], e.R);
                         dacc_add(adr, w[m], e.dR);
                     }
-                    c0 = dacc_get(ac); dc0 = dacc_get(adc); r0 = dacc_get(ar); dr0 = dacc_get(adr);
+                    c0 = dacc_raw(ac); dc0 = dacc_raw(adc); r0 = dacc_raw(ar); dr0 = dacc_raw(adr);
                 }
                 dacc tc = dacc_prod(tw0, c0), tr = dacc_prod(tw0, r0);
                 dacc_add(tc, tw1, dc0);
@@ -445,13 +447,13 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
                         dacc_add(ar, w[m], e.R);
                         dacc_add(adr, w[m], e.dR);
                     }
-                    dacc_add(tc, tw2, dacc_get(ac));
-                    dacc_add(tc, tw3, dacc_get(adc));
-                    dacc_add(tr, tw2, dacc_get(ar));
-                    dacc_add(tr, tw3, dacc_get(adr));
+                    dacc_add(tc, tw2, dacc_raw(ac));
+                    dacc_add(tc, tw3, dacc_raw(adc));
+                    dacc_add(tr, tw2, dacc_raw(ar));
+                    dacc_add(tr, tw3, dacc_raw(adr));
                 }
-                CB2 = dacc_get(tc);
-                RB2 = dacc_get(tr);
+                CB2 = dacc_raw(tc);
+                RB2 = dacc_raw(tr);
             }
             df f1a, f2a, f1b, f2b;
             poly12_df_pair(v.poly, CB1, CB2, f1a, f2a, f1b, f2b);
