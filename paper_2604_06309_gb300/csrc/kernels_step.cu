@@ -588,113 +588,180 @@ __device__ __forceinline__ bool sp_active(const DevState* st, int from_step) {
     return from_step ? (st->sp_left > 0 && st->status == 0) : true;
 }
 
-// eps_sparse(n) for candidates n = 1 .. N-12: one warp per candidate.
-__device__ __forceinline__ void sp_residual_body(const SolverView& v, int from_step, int cta, int ncta) {
+// eps_sparse(n) for candidates n = 1 .. N-12: one CTA per candidate (CTA `cta` takes n =
+// cta + 1), its threads striding over the grid index; each thread adds its terms in i
+// order, the warps reduce with a fixed butterfly and the first thread adds the warp sums in
+// warp order, so the result is deterministic.
+constexpr int SP_RES_THREADS = 128;
+
+__device__ __forceinline__ void sp_residual_body(const SolverView& v, int from_step, int cta) {
     const DevState* st = v.st;
     if (!sp_active(st, from_step)) return;
     const int L = v.L;
     const int N = st->n;
-    const int last = N - 12;
+    const int n = cta + 1;
+    if (n > N - 12) return;
+    if (!DMFE_IN_BOUNDS(v.st, n + 1 < N && N <= v.cap, 31)) return;
     const int act = st->active;
     const dbl4* H = v.hist[act];
     const double* ht = v.ht[act];
-    const int lane = threadIdx.x & 31;
-    const int nw = ncta * (blockDim.x >> 5);
-    for (int n = 1 + cta * (blockDim.x >> 5) + (threadIdx.x >> 5); n <= last; n += nw) {
-        if (!DMFE_IN_BOUNDS(v.st, n + 1 < N && N <= v.cap, 31)) continue;
-        const double h1 = ht[n] - ht[n - 1], h2 = ht[n + 1] - ht[n];
-        const dbl4* a = H + (size_t)(n - 1) * L;
-        const dbl4* b = H + (size_t)n * L;
-        const dbl4* c = H + (size_t)(n + 1) * L;
-        double acc = 0.0;
-        // unrolled so that several iterations' loads are in flight (the sum order is kept)
+    const double h1 = ht[n] - ht[n - 1], h2 = ht[n + 1] - ht[n];
+    const dbl4* a = H + (size_t)(n - 1) * L;
+    const dbl4* b = H + (size_t)n * L;
+    const dbl4* c = H + (size_t)(n + 1) * L;
+    double acc = 0.0;
 #pragma unroll 4
-        for (int i = lane; i < L; i += 32) {
-            const dbl4 A = a[i], B = b[i], Cc = c[i];
-            const double wC = herm_int(A.x, A.y, B.x, B.y, h1) + herm_int(B.x, B.y, Cc.x, Cc.y, h2);
-            const double oC = herm_int(A.x, A.y, Cc.x, Cc.y, h1 + h2);
-            const double wR = herm_int(A.z, A.w, B.z, B.w, h1) + herm_int(B.z, B.w, Cc.z, Cc.w, h2);
-            const double oR = herm_int(A.z, A.w, Cc.z, Cc.w, h1 + h2);
-            acc += fabs(wC - oC) + fabs(wR - oR);
-        }
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const dbl4 A = a[i], B = b[i], Cc = c[i];
+        const double wC = herm_int(A.x, A.y, B.x, B.y, h1) + herm_int(B.x, B.y, Cc.x, Cc.y, h2);
+        const double oC = herm_int(A.x, A.y, Cc.x, Cc.y, h1 + h2);
+        const double wR = herm_int(A.z, A.w, B.z, B.w, h1) + herm_int(B.z, B.w, Cc.z, Cc.w, h2);
+        const double oR = herm_int(A.z, A.w, Cc.z, Cc.w, h1 + h2);
+        acc += fabs(wC - oC) + fabs(wR - oR);
+    }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) v.eps_sp[n] = acc;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double wsum[SP_RES_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double e = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) e += wsum[w];
+        v.eps_sp[n] = e;
     }
 }
 
-// Greedy scan of Sec. 3.6 (remove n if eps < tol/10, then skip n+1), forced removal of the
-// smallest residual when nothing qualifies, and the compaction map. Single thread: the
-// scan is sequential by definition and runs once per pass. It visits every candidate with
-// a skip flag (rather than stepping by two after a removal), so the loads of the residuals
-// do not wait on the decisions and the unrolled loop keeps several in flight; the map
-// (kept slices before each slice) is formed in the same pass.
+// Exclusive scan over the threads of the CTA (Hillis-Steele in shared memory, fixed
+// order); *total receives the combination over all threads.
+template <typename T, typename Op>
+__device__ __forceinline__ T block_exclusive_scan(T x, T identity, Op op, T* buf, T* total) {
+    const int t = threadIdx.x, nt = blockDim.x;
+    buf[t] = x;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {
+        const T y = t >= off ? buf[t - off] : identity;
+        __syncthreads();
+        buf[t] = op(buf[t], y);
+        __syncthreads();
+    }
+    const T excl = t > 0 ? buf[t - 1] : identity;
+    *total = buf[nt - 1];
+    __syncthreads();
+    return excl;
+}
+
+// Selection of a pass (Sec. 3.6) by one CTA. The greedy scan -- remove n if eps(n) < tol/10,
+// then skip n+1 -- removes, within each maximal run of consecutive qualifying candidates, the
+// run's 1st, 3rd, 5th, ... members, so a candidate's fate depends only on its position in
+// its run: an exclusive max-scan gives the last non-qualifying index before each index, and
+// an exclusive sum-scan of the kept slices gives the compaction map. A pass that may force a
+// removal and finds none removes the candidate with the smallest residual (the first of
+// equal ones). Thread t takes the contiguous indices [t P, (t + 1) P) of [0, N),
+// P = ceil(N / blockDim).
 __device__ __forceinline__ void sp_select_body(const SolverView& v, int from_step, double tol_arg) {
+    __shared__ int s_int[CTL_THREADS];
+    __shared__ double s_dbl[CTL_THREADS];
     DevState* st = v.st;
-    if (!sp_active(st, from_step) || threadIdx.x != 0) return;
-    if (from_step) st->sp_left -= 1;
+    // every thread reads the pass's state before thread 0 changes it
+    if (!sp_active(st, from_step)) return;
     // the first pass of a full-store round (and an explicit pass) must free a slot, so it
     // may force a removal; the other passes remove only slices that qualify
     const bool force = from_step ? st->pending != 0 : true;
     const int N = st->n;
-    const int last = N - 12;
     const double tol = from_step ? st->tol : tol_arg;
-    st->sp_ran = 0;
+    const double mx0 = st->max_eps_sparse;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (from_step) st->sp_left -= 1;
+        st->sp_ran = 0;
+    }
+    const int last = N - 12;
     if (last < 1) {
-        if (from_step && force) st->status = DMFE_ERR_CAPACITY;
+        if (threadIdx.x == 0 && from_step && force) st->status = DMFE_ERR_CAPACITY;
         return;
     }
     const double thr = tol / 10.0;
     const double* __restrict__ eps = v.eps_sp;
-    int removed = 0;
-    double mx = st->max_eps_sparse;
-    v.keep[0] = 1;
-    v.newidx[0] = 0;
-    int c = 1;
-    bool skip = false;
-#pragma unroll 8
-    for (int k = 1; k <= last; ++k) {
-        const double e = eps[k];
-        const bool rm = !skip && e < thr;
-        v.keep[k] = rm ? 0 : 1;
-        v.newidx[k] = c;
-        c += rm ? 0 : 1;
-        removed += rm ? 1 : 0;
-        mx = rm ? fmax(mx, e) : mx;
-        skip = rm;
+    const int T = blockDim.x, t = threadIdx.x;
+    const int P = (N + T - 1) / T;
+    const int lo = t * P < N ? t * P : N, hi = lo + P < N ? lo + P : N;
+    auto ok = [&](int k) { return k >= 1 && k <= last && eps[k] < thr; };
+    // last non-qualifying index before this thread's block
+    int zmax = -1;
+    for (int k = lo; k < hi; ++k)
+        if (!ok(k)) zmax = k;
+    int zall;
+    const int pf0 = block_exclusive_scan(zmax, -1, [](int x, int y) { return x > y ? x : y; }, s_int, &zall);
+    // decisions and the kept count of the block
+    int kept = 0, removed_loc = 0;
+    double mx = -1.0;
+    {
+        int pf = pf0;
+        for (int k = lo; k < hi; ++k) {
+            const bool q = ok(k);
+            const bool rm = q && ((k - pf - 1) % 2 == 0);
+            if (!q) pf = k;
+            kept += rm ? 0 : 1;
+            removed_loc += rm ? 1 : 0;
+            if (rm) mx = fmax(mx, eps[k]);
+        }
     }
-    for (int k = last + 1; k < N; ++k) {
-        v.keep[k] = 1;
-        v.newidx[k] = c++;
+    int kept_all;
+    const int base = block_exclusive_scan(kept, 0, [](int x, int y) { return x + y; }, s_int, &kept_all);
+    double mx_all;
+    block_exclusive_scan(mx, -1.0, [](double x, double y) { return fmax(x, y); }, s_dbl, &mx_all);
+    {
+        int pf = pf0, c = base;
+        for (int k = lo; k < hi; ++k) {
+            const bool q = ok(k);
+            const bool rm = q && ((k - pf - 1) % 2 == 0);
+            if (!q) pf = k;
+            v.keep[k] = rm ? 0 : 1;
+            v.newidx[k] = c;
+            c += rm ? 0 : 1;
+        }
     }
+    int removed = N - kept_all;
     if (removed == 0 && !force) {
         // nothing qualifies and nothing is forced: the pass counts, the history stays
-        st->sparsify_passes += 1;
-        st->removed_count = 0;
+        if (t == 0) {
+            st->sparsify_passes += 1;
+            st->removed_count = 0;
+        }
         return;
     }
+    double mx_new = fmax(mx0, mx_all);
     if (removed == 0) {
-        // every slice was kept, so newidx[k] = k; removing m shifts the slices after it
-        int m = 1;
-        double em = eps[1];
-#pragma unroll 8
-        for (int k = 2; k <= last; ++k) {
-            const double e = eps[k];
-            if (e < em) { em = e; m = k; }
+        // every slice was kept, so newidx[k] = k; remove the smallest residual m (the first
+        // of equal ones): a block minimum of the value, then of the index among equal values
+        double em = INFINITY;
+        for (int k = lo; k < hi; ++k)
+            if (k >= 1 && k <= last && eps[k] < em) em = eps[k];
+        double em_all;
+        block_exclusive_scan(em, (double)INFINITY, [](double x, double y) { return fmin(x, y); }, s_dbl, &em_all);
+        int m_loc = 0x7fffffff;
+        for (int k = lo; k < hi; ++k)
+            if (k >= 1 && k <= last && eps[k] == em_all) { m_loc = k; break; }
+        int m;
+        block_exclusive_scan(m_loc, 0x7fffffff, [](int x, int y) { return x < y ? x : y; }, s_int, &m);
+        if (m == 0x7fffffff) m = 1;  // no finite minimum (NaN residuals): the first candidate, as the scan
+        for (int k = lo; k < hi; ++k) {
+            if (k == m) v.keep[k] = 0;
+            if (k > m) v.newidx[k] = k - 1;
         }
-        v.keep[m] = 0;
-        for (int k = m + 1; k < N; ++k) v.newidx[k] = k - 1;
-        c = N - 1;
+        kept_all = N - 1;
         removed = 1;
-        mx = fmax(mx, em);
-        st->forced_removals += 1;
+        mx_new = fmax(mx_new, em_all);
+        if (t == 0) st->forced_removals += 1;
     }
-    st->max_eps_sparse = mx;
-    st->sparsify_passes += 1;
-    st->slices_removed += removed;
-    st->removed_count = removed;
-    st->n_new = c;
-    st->sp_ran = 1;
+    if (t == 0) {
+        st->max_eps_sparse = mx_new;
+        st->sparsify_passes += 1;
+        st->slices_removed += removed;
+        st->removed_count = removed;
+        st->n_new = kept_all;
+        st->sp_ran = 1;
+    }
 }
 
 __device__ __forceinline__ void sp_compact_body(const SolverView& v, int cta, int ncta) {
@@ -751,17 +818,21 @@ __device__ __forceinline__ void sp_finish_body(const SolverView& v) {
     }
 }
 
-__global__ void k_sp_residual(SolverView v, int from_step) { sp_residual_body(v, from_step, blockIdx.x, gridDim.x); }
-__global__ void k_sp_select(SolverView v, int from_step, double tol_arg) { sp_select_body(v, from_step, tol_arg); }
+__global__ void __launch_bounds__(SP_RES_THREADS) k_sp_residual(SolverView v, int from_step) {
+    sp_residual_body(v, from_step, blockIdx.x);
+}
+__global__ void __launch_bounds__(CTL_THREADS) k_sp_select(SolverView v, int from_step, double tol_arg) {
+    sp_select_body(v, from_step, tol_arg);
+}
 __global__ void k_sp_compact(SolverView v) { sp_compact_body(v, blockIdx.x, gridDim.x); }
 __global__ void __launch_bounds__(CTL_THREADS) k_sp_finish(SolverView v) { sp_finish_body(v); }
 
-__global__ void k_batch_sp_residual(const BatchTable* __restrict__ bt) {
+__global__ void __launch_bounds__(SP_RES_THREADS) k_batch_sp_residual(const BatchTable* __restrict__ bt) {
     const int k = blockIdx.y;
     if (k >= bt->count || !bt->active[k]) return;
-    sp_residual_body(bt->views[k], 1, blockIdx.x, gridDim.x);
+    sp_residual_body(bt->views[k], 1, blockIdx.x);
 }
-__global__ void k_batch_sp_select(const BatchTable* __restrict__ bt) {
+__global__ void __launch_bounds__(CTL_THREADS) k_batch_sp_select(const BatchTable* __restrict__ bt) {
     const int k = blockIdx.x;
     if (k >= bt->count || !bt->active[k]) return;
     sp_select_body(bt->views[k], 1, 0.0);
@@ -894,8 +965,8 @@ int launch_begin_integrate(const SolverView& v, double t_target, double tol, cud
 
 int launch_sparsify(const SolverView& v, bool from_step, double tol, cudaStream_t s) {
     const int fs = from_step ? 1 : 0;
-    k_sp_residual<<<grid_for((long long)v.cap * 32, 256), 256, 0, s>>>(v, fs);
-    k_sp_select<<<1, 32, 0, s>>>(v, fs, tol);
+    k_sp_residual<<<v.cap > 13 ? v.cap - 12 : 1, SP_RES_THREADS, 0, s>>>(v, fs);
+    k_sp_select<<<1, CTL_THREADS, 0, s>>>(v, fs, tol);
     k_sp_compact<<<grid_for((long long)v.cap * v.L, 256), 256, 0, s>>>(v);
     k_sp_finish<<<1, CTL_THREADS, 0, s>>>(v);
     DMFE_CUDA_TRY(cudaGetLastError());
@@ -1000,8 +1071,8 @@ int launch_batch_step_tail(const BatchTable* bt, int precision, int sw, int max_
 }
 
 int launch_batch_step_sparsify(const BatchTable* bt, int max_cap, int slots, cudaStream_t s) {
-    k_batch_sp_residual<<<dim3((max_cap + 7) / 8, slots), 256, 0, s>>>(bt);
-    k_batch_sp_select<<<slots, 32, 0, s>>>(bt);
+    k_batch_sp_residual<<<dim3(max_cap > 13 ? max_cap - 12 : 1, slots), SP_RES_THREADS, 0, s>>>(bt);
+    k_batch_sp_select<<<slots, CTL_THREADS, 0, s>>>(bt);
     k_batch_sp_compact<<<dim3(64, slots), 256, 0, s>>>(bt);
     k_batch_sp_finish<<<slots, CTL_THREADS, 0, s>>>(bt);
     DMFE_CUDA_TRY(cudaGetLastError());

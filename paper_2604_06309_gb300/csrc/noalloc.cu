@@ -54,30 +54,41 @@ __device__ __forceinline__ double herm_int_na(double y0, double d0, double y1, d
     return 0.5 * h * (y0 + y1) + h * h * (d0 - d1) / 12.0;
 }
 
-// eps_sparse(k) for candidates k = 1 .. n-12 (Sec. 3.6), one warp per candidate; the
-// same per-lane order and warp butterfly as the solver's residual kernel.
-__global__ void k_na_residual(const double* __restrict__ t, const double* __restrict__ C,
-                              const double* __restrict__ dC, const double* __restrict__ R,
-                              const double* __restrict__ dR, int n, int L, double* __restrict__ eps) {
-    const int last = n - 12;
-    const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x * (blockDim.x >> 5);
-    for (int k = 1 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k <= last; k += nw) {
-        const double h1 = t[k] - t[k - 1], h2 = t[k + 1] - t[k];
-        const size_t a = (size_t)(k - 1) * L, b = (size_t)k * L, c = (size_t)(k + 1) * L;
-        double acc = 0.0;
-        for (int i = lane; i < L; i += 32) {
-            const double wC = herm_int_na(C[a + i], dC[a + i], C[b + i], dC[b + i], h1) +
-                              herm_int_na(C[b + i], dC[b + i], C[c + i], dC[c + i], h2);
-            const double oC = herm_int_na(C[a + i], dC[a + i], C[c + i], dC[c + i], h1 + h2);
-            const double wR = herm_int_na(R[a + i], dR[a + i], R[b + i], dR[b + i], h1) +
-                              herm_int_na(R[b + i], dR[b + i], R[c + i], dR[c + i], h2);
-            const double oR = herm_int_na(R[a + i], dR[a + i], R[c + i], dR[c + i], h1 + h2);
-            acc += fabs(wC - oC) + fabs(wR - oR);
-        }
+// eps_sparse(k) for candidates k = 1 .. n-12 (Sec. 3.6), one CTA per candidate (CTA b takes
+// k = b + 1); the same per-thread order, warp butterfly and warp-order sum as the solver's
+// residual kernel, so the residuals are the same numbers.
+constexpr int kNaResThreads = 128;
+
+__global__ void __launch_bounds__(kNaResThreads) k_na_residual(const double* __restrict__ t,
+                                                              const double* __restrict__ C,
+                                                              const double* __restrict__ dC,
+                                                              const double* __restrict__ R,
+                                                              const double* __restrict__ dR, int n, int L,
+                                                              double* __restrict__ eps) {
+    const int k = blockIdx.x + 1;
+    if (k > n - 12) return;
+    const double h1 = t[k] - t[k - 1], h2 = t[k + 1] - t[k];
+    const size_t a = (size_t)(k - 1) * L, b = (size_t)k * L, c = (size_t)(k + 1) * L;
+    double acc = 0.0;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const double wC = herm_int_na(C[a + i], dC[a + i], C[b + i], dC[b + i], h1) +
+                          herm_int_na(C[b + i], dC[b + i], C[c + i], dC[c + i], h2);
+        const double oC = herm_int_na(C[a + i], dC[a + i], C[c + i], dC[c + i], h1 + h2);
+        const double wR = herm_int_na(R[a + i], dR[a + i], R[b + i], dR[b + i], h1) +
+                          herm_int_na(R[b + i], dR[b + i], R[c + i], dR[c + i], h2);
+        const double oR = herm_int_na(R[a + i], dR[a + i], R[c + i], dR[c + i], h1 + h2);
+        acc += fabs(wC - oC) + fabs(wR - oR);
+    }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) eps[k] = acc;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double wsum[kNaResThreads / 32];
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double e = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) e += wsum[w];
+        eps[k] = e;
     }
 }
 
@@ -118,10 +129,7 @@ extern "C" int dmfe_sparsify_select_noalloc(const double* t_dev, const double* C
     double* eps = nullptr;
     int rc = scratch_address(s, &eps);
     if (rc) return rc;
-    const int warps_per_cta = 8;
-    int ctas = (n + warps_per_cta - 1) / warps_per_cta;
-    ctas = ctas < 1 ? 1 : (ctas > 2048 ? 2048 : ctas);
-    k_na_residual<<<ctas, 32 * warps_per_cta, 0, s>>>(t_dev, C_dev, dC_dev, R_dev, dR_dev, n, L, eps);
+    k_na_residual<<<n > 13 ? n - 12 : 1, kNaResThreads, 0, s>>>(t_dev, C_dev, dC_dev, R_dev, dR_dev, n, L, eps);
     k_na_select<<<1, 32, 0, s>>>(eps, n, tol, removed_dev);
     if (cudaGetLastError() != cudaSuccess) return DMFE_ERR_CUDA;
     return DMFE_OK;
