@@ -32,6 +32,8 @@ struct dmfe_solver {
     DevState* hstate = nullptr;  // pinned mirror of the device state
     double* scratch = nullptr;   // device [4L + 16]
     std::vector<void*> allocs;
+    std::vector<int2> flat_seg_h, flat_row_h;  // tables of the flat split (host copies)
+    int flat_G = 0;              // warps the device tables were built for (0: none)
     bool table_ref = false;      // holds a reference to a cached stencil-table entry
     std::tuple<int, int, int, int, int, int, double, double, double> table_key;
 };
@@ -65,6 +67,28 @@ std::mutex g_table_mutex;
 std::map<TableKey, TableEntry> g_tables;
 
 void release_tables(dmfe_solver* h);
+
+// The flat split's segment and row tables for a launch of `grid` CTAs of v.hi_threads
+// threads (rebuilt only when the warp count changes); stream-ordered before any launch.
+int set_flat_tables(dmfe_solver* h, int grid) {
+    SolverView& v = h->v;
+    const int G = grid * (v.hi_threads / 32);
+    if (G == h->flat_G) return DMFE_OK;
+    flat_split_tables(v.L, G, h->flat_seg_h, h->flat_row_h);
+    void* p = nullptr;
+    int rc = dev_alloc(h, &p, h->flat_seg_h.size() * sizeof(int2));
+    if (rc) return rc;
+    v.flat_seg = (const int2*)p;
+    rc = dev_alloc(h, &p, h->flat_row_h.size() * sizeof(int2));
+    if (rc) return rc;
+    v.flat_row = (const int2*)p;
+    DMFE_CUDA_TRY(cudaMemcpyAsync((void*)v.flat_seg, h->flat_seg_h.data(), h->flat_seg_h.size() * sizeof(int2),
+                                  cudaMemcpyHostToDevice, h->stream));
+    DMFE_CUDA_TRY(cudaMemcpyAsync((void*)v.flat_row, h->flat_row_h.data(), h->flat_row_h.size() * sizeof(int2),
+                                  cudaMemcpyHostToDevice, h->stream));
+    h->flat_G = G;
+    return DMFE_OK;
+}
 
 // The solver's three stencil tables: an existing entry of its key (its stream then waits
 // for the entry's table kernel), or a new entry built by the table kernel on the solver's
@@ -383,6 +407,7 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
         v.hi_chunk = default_chunk(v.precision, L);
         TRY(hi_config(v, &h->hi_grid, &h->hi_smem));
     }
+    if (v.hi_chunk == kFlatSplit) TRY(set_flat_tables(h, h->hi_grid));
     DMFE_CUDA_TRY(cudaStreamSynchronize(h->stream));
     DMFE_CUDA_TRY(cudaGetLastError());
     return DMFE_OK;
@@ -915,6 +940,7 @@ int dmfe_autotune(dmfe_solver* h, int* chunk_out) {
                 rc = DMFE_OK;  // this grid is too small for the flat split
                 continue;
             }
+            if (!rc && c == kFlatSplit) rc = set_flat_tables(h, grid);
             if (rc) break;
             float tot = 0.f;
             for (int it = 0; it < 4 && !rc; ++it) {
@@ -937,6 +963,7 @@ int dmfe_autotune(dmfe_solver* h, int* chunk_out) {
         if (rc) {
             v.hi_chunk = saved;
             hi_config(v, &h->hi_grid, &h->hi_smem);
+            if (saved == kFlatSplit) set_flat_tables(h, h->hi_grid);
             return rc;
         }
         std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -944,6 +971,7 @@ int dmfe_autotune(dmfe_solver* h, int* chunk_out) {
     }
     v.hi_chunk = best;
     TRY(hi_config(v, &h->hi_grid, &h->hi_smem));
+    if (best == kFlatSplit) TRY(set_flat_tables(h, h->hi_grid));
     if (h->step_exec) {  // the captured step holds the old launch configuration
         cudaGraphExecDestroy(h->step_exec);
         h->step_exec = nullptr;

@@ -153,6 +153,22 @@ __device__ __forceinline__ bool dmfe_in_bounds(DevState* st, bool ok, int site) 
 #define DMFE_IN_BOUNDS(st, cond, site) true
 #endif
 
+// Sparsification residual of one grid point (Sec. 3.6): the Hermite integrals over
+// [t_{n-1}, t_n] and [t_n, t_{n+1}] minus the one over [t_{n-1}, t_{n+1}] without slice n,
+// written as one linear form in the values y and derivatives d of slices n-1, n, n+1.
+struct SpWeights {
+    double ya, yb, yc, da, db, dc;
+};
+__host__ __device__ __forceinline__ SpWeights sp_weights(double h1, double h2) {
+    const double h = h1 + h2;
+    return SpWeights{-0.5 * h2, 0.5 * h, -0.5 * h1, (h1 * h1 - h * h) / 12.0, (h2 * h2 - h1 * h1) / 12.0,
+                     (h * h - h2 * h2) / 12.0};
+}
+__device__ __forceinline__ double sp_delta(const SpWeights& w, double ya, double da, double yb, double db, double yc,
+                                           double dc) {
+    return fma(w.ya, ya, fma(w.yb, yb, fma(w.yc, yc, fma(w.da, da, fma(w.db, db, w.dc * dc)))));
+}
+
 // Gate of the kernels of stage `stage` (>= 1) of a step: they do nothing once the solve
 // has stopped (error or target reached) or when the step's method has fewer stages.
 // stage == 0 marks an explicit call outside the step loop (never gated).
@@ -205,7 +221,9 @@ struct SolverView {
     float4* vrow32;       // [L] FP32 path: the same in FP32
     int* cell;            // [L] slice of time theta_m t
     B1Desc* b1;           // [L] per-stage B1 time weights
-    int hi_chunk;         // summation indices per work unit
+    int hi_chunk;         // summation indices per work unit (-1: the flat split)
+    const int2* flat_seg; // flat split: [G + 1] {first pair, its row} of each warp's segment
+    const int2* flat_row; // flat split: [L] {first segment, segments} of each row
     DevState* st;
     double* Y;            // [2][2L] stage rows (C then R), double-buffered: stage stg reads
                           // Y + (stg & 1) * 2L and writes the other buffer

@@ -10,6 +10,8 @@
 // unit ever waits for another.
 #pragma once
 
+#include <vector>
+
 #include "dmfe_internal.h"
 
 // Work-unit size value that selects the flat split (single solves only): the L^2 pairs in
@@ -40,32 +42,28 @@ __device__ __forceinline__ void hi_unit_range(int u, int L, int chunk, int* j, i
     *i1 = p == P - 1 ? L : (p + 1) * chunk;
 }
 
-// Calls f(j, i0, i1, part, nparts) for each piece of work of this warp: the units [ub, ue)
-// of its CTA round-robin over the CTA's warps, or under the flat split the rows of the
-// warp's segment [g LL / G, (g + 1) LL / G) (G warps in the grid, g this warp). Segment s
-// holds pair q when s = ((q + 1) G - 1) / LL (integer division), so row j's parts are the
-// segments from that of its first pair to that of its last; G <= LL keeps every segment
-// non-empty.
 // The flat split needs at least 256 pairs per warp (8 per lane), which also keeps every
 // segment non-empty and a row's parts within the partial-sum buffer (L / 32 parts).
 __host__ __device__ __forceinline__ bool flat_split_fits(int L, long long warps) {
     return warps > 0 && (long long)L * L >= 256 * warps && L >= 512;
 }
 
+// Calls f(j, i0, i1, part, nparts) for each piece of work of this warp: the units [ub, ue)
+// of its CTA round-robin over the CTA's warps, or under the flat split the rows of the
+// warp's segment, read from the split's tables (flat_split_tables): seg[g] = {first pair, its
+// row} of segment g (seg[G] = {L^2, L}), row[j] = {first segment, segments} of row j.
 template <typename F>
-__device__ __forceinline__ void hi_for_items(int L, int chunk, int ub, int ue, F&& f) {
+__device__ __forceinline__ void hi_for_items(int L, int chunk, int ub, int ue, const int2* __restrict__ seg,
+                                             const int2* __restrict__ row, F&& f) {
     if (chunk == kFlatSplit) {
-        const long long LL = (long long)L * L;
-        const long long G = (long long)gridDim.x * (blockDim.x >> 5);
-        const long long g = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-        const long long q1 = (g + 1) * LL / G;
-        for (long long q = g * LL / G; q < q1;) {
-            const int j = (int)(q / L);
-            const long long rb = (long long)j * L;
-            const long long qe = q1 < rb + L ? q1 : rb + L;
-            const long long s0 = ((rb + 1) * G - 1) / LL;
-            const long long s1 = ((rb + L) * G - 1) / LL;
-            f(j, (int)(q - rb), (int)(qe - rb), (int)(g - s0), (int)(s1 - s0 + 1));
+        const int g = (int)blockIdx.x * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
+        const int2 a = seg[g], b = seg[g + 1];
+        int j = a.y;
+        for (int q = a.x; q < b.x; ++j) {
+            const int rb = j * L;
+            const int qe = b.x < rb + L ? b.x : rb + L;
+            const int2 r = row[j];
+            f(j, q - rb, qe - rb, g - r.x, r.y);
             q = qe;
         }
         return;
@@ -75,6 +73,25 @@ __device__ __forceinline__ void hi_for_items(int L, int chunk, int ub, int ue, F
         int j, i0, i1;
         hi_unit_range(u, L, chunk, &j, &i0, &i1);
         f(j, i0, i1, u / L, P);
+    }
+}
+
+// Host: the tables of the flat split over G warps. Segment g covers the pairs
+// [g L^2 / G, (g + 1) L^2 / G) in row-major order; pair q lies in segment
+// ((q + 1) G - 1) / L^2, so row j's parts are the segments from that of its first pair to
+// that of its last. seg has G + 1 entries, row L.
+inline void flat_split_tables(int L, int G, std::vector<int2>& seg, std::vector<int2>& row) {
+    const long long LL = (long long)L * L;
+    seg.resize((size_t)G + 1);
+    for (int g = 0; g <= G; ++g) {
+        const long long q = (long long)g * LL / G;
+        seg[g] = make_int2((int)q, (int)(q / L));
+    }
+    row.resize(L);
+    for (int j = 0; j < L; ++j) {
+        const long long rb = (long long)j * L;
+        const long long s0 = ((rb + 1) * G - 1) / LL, s1 = ((rb + L) * G - 1) / LL;
+        row[j] = make_int2((int)s0, (int)(s1 - s0 + 1));
     }
 }
 

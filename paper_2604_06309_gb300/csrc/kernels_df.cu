@@ -285,7 +285,7 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
     const float bmax = (float)(L - SW);
 
     const int chunk = v.hi_chunk;
-    hi_for_items(L, chunk, ub, ue, [&](int j, int i0, int i1, int part, int nparts) {
+    hi_for_items(L, chunk, ub, ue, v.flat_seg, v.flat_row, [&](int j, int i0, int i1, int part, int nparts) {
         // ---- per unit: B1 time weights prepared once per stage
         const df omj = omdf[j];
         int a0, a1;

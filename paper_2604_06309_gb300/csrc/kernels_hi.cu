@@ -151,7 +151,7 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
     const double* __restrict__ nu = v.nu;
     const int chunk = v.hi_chunk;
 
-    hi_for_items(L, chunk, ub, ue, [&](int j, int i0, int i1, int part, int nparts) {
+    hi_for_items(L, chunk, ub, ue, v.flat_seg, v.flat_row, [&](int j, int i0, int i1, int part, int nparts) {
         // the stage time of B2, tau2 = phi2 t = theta_j t + (omega_j t) theta_i, by one FMA
         const double thj_t = theta[j] * t, omj_t = omega[j] * t;
         TimeW b1;
@@ -370,7 +370,7 @@ __device__ __forceinline__ void hi_f32_body(const SolverView& v, const double* _
     const float* __restrict__ nu32 = v.nu32;
     const int chunk = v.hi_chunk;
 
-    hi_for_items(L, chunk, ub, ue, [&](int j, int i0, int i1, int part, int nparts) {
+    hi_for_items(L, chunk, ub, ue, v.flat_seg, v.flat_row, [&](int j, int i0, int i1, int part, int nparts) {
         const float omj = om32[j];
         TimeW b1d;
         float bw0, bw1, bw2, bw3;

@@ -577,9 +577,7 @@ __global__ void __launch_bounds__(kCtlThreads) k_batch_stage_end(const BatchTabl
 }
 
 // ---------------------------------------------------------------- sparsification
-__device__ __forceinline__ double herm_int(double y0, double d0, double y1, double d1, double h) {
-    return 0.5 * h * (y0 + y1) + h * h * (d0 - d1) / 12.0;
-}
+
 
 // A pass of the step graph runs while the current round has passes left (a round is set
 // by the step decision: on a full store, or after every sp_every-th accepted step); an
@@ -609,15 +607,16 @@ __device__ __forceinline__ void sp_residual_body(const SolverView& v, int from_s
     const dbl4* a = H + (size_t)(n - 1) * L;
     const dbl4* b = H + (size_t)n * L;
     const dbl4* c = H + (size_t)(n + 1) * L;
+    // Delta_n = (I[t_{n-1}, t_n] + I[t_n, t_{n+1}]) - I[t_{n-1}, t_{n+1}] with the Hermite
+    // integral I = h (y0 + y1)/2 + h^2 (y0' - y1')/12 is linear in the six stored values:
+    // weights -h2/2, (h1 + h2)/2, -h1/2 on the values and (h1^2 - h^2)/12, (h2^2 - h1^2)/12,
+    // (h^2 - h2^2)/12 on the derivatives (h = h1 + h2), formed once per candidate
+    const SpWeights wt = sp_weights(h1, h2);
     double acc = 0.0;
 #pragma unroll 4
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         const dbl4 A = a[i], B = b[i], Cc = c[i];
-        const double wC = herm_int(A.x, A.y, B.x, B.y, h1) + herm_int(B.x, B.y, Cc.x, Cc.y, h2);
-        const double oC = herm_int(A.x, A.y, Cc.x, Cc.y, h1 + h2);
-        const double wR = herm_int(A.z, A.w, B.z, B.w, h1) + herm_int(B.z, B.w, Cc.z, Cc.w, h2);
-        const double oR = herm_int(A.z, A.w, Cc.z, Cc.w, h1 + h2);
-        acc += fabs(wC - oC) + fabs(wR - oR);
+        acc += fabs(sp_delta(wt, A.x, A.y, B.x, B.y, Cc.x, Cc.y)) + fabs(sp_delta(wt, A.z, A.w, B.z, B.w, Cc.z, Cc.w));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);

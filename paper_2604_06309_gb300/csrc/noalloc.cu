@@ -50,9 +50,6 @@ int scratch_address(cudaStream_t stream, double** out) {
     return DMFE_OK;
 }
 
-__device__ __forceinline__ double herm_int_na(double y0, double d0, double y1, double d1, double h) {
-    return 0.5 * h * (y0 + y1) + h * h * (d0 - d1) / 12.0;
-}
 
 // eps_sparse(k) for candidates k = 1 .. n-12 (Sec. 3.6), one CTA per candidate (CTA b takes
 // k = b + 1); the same per-thread order, warp butterfly and warp-order sum as the solver's
@@ -69,16 +66,12 @@ __global__ void __launch_bounds__(kNaResThreads) k_na_residual(const double* __r
     if (k > n - 12) return;
     const double h1 = t[k] - t[k - 1], h2 = t[k + 1] - t[k];
     const size_t a = (size_t)(k - 1) * L, b = (size_t)k * L, c = (size_t)(k + 1) * L;
+    const SpWeights wt = sp_weights(h1, h2);
     double acc = 0.0;
 #pragma unroll 4
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        const double wC = herm_int_na(C[a + i], dC[a + i], C[b + i], dC[b + i], h1) +
-                          herm_int_na(C[b + i], dC[b + i], C[c + i], dC[c + i], h2);
-        const double oC = herm_int_na(C[a + i], dC[a + i], C[c + i], dC[c + i], h1 + h2);
-        const double wR = herm_int_na(R[a + i], dR[a + i], R[b + i], dR[b + i], h1) +
-                          herm_int_na(R[b + i], dR[b + i], R[c + i], dR[c + i], h2);
-        const double oR = herm_int_na(R[a + i], dR[a + i], R[c + i], dR[c + i], h1 + h2);
-        acc += fabs(wC - oC) + fabs(wR - oR);
+        acc += fabs(sp_delta(wt, C[a + i], dC[a + i], C[b + i], dC[b + i], C[c + i], dC[c + i])) +
+               fabs(sp_delta(wt, R[a + i], dR[a + i], R[b + i], dR[b + i], R[c + i], dR[c + i]));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
