@@ -204,6 +204,41 @@ def test_sparsify_decisions_are_identical():
     g.close()
 
 
+def test_sparsify_selection_on_random_runs_of_removable_slices():
+    """The device selection (the run-parity form of the greedy scan, evaluated in parallel)
+    against the oracle's scan: a 700-slice history lying on one cubic in time, with random
+    slices broken, gives runs of removable candidates of random lengths (and one history
+    with every slice broken, where the pass force-removes the smallest residual)."""
+    need_gpu()
+    from paper_2604_06309_gb300 import Solver
+    L, N, tol = 33, 700, 1e-8
+    g = Solver(MIXED_34, 0.5, L, 1e3, history_cap=N)
+    rng = np.random.default_rng(7)
+    t = np.concatenate([[0.0], np.cumsum(rng.uniform(0.05, 0.2, N - 1))])
+    c = rng.normal(size=(4, L)) * 1e-3
+    cub = lambda x: c[0] + c[1] * x + c[2] * x ** 2 + c[3] * x ** 3
+    dcub = lambda x: c[1] + 2 * c[2] * x + 3 * c[3] * x ** 2
+    for trial in range(6):
+        C = np.array([cub(x) for x in t])
+        dC = np.array([dcub(x) for x in t])
+        if trial == 5:
+            broken = np.arange(1, N - 1)
+        else:
+            broken = rng.choice(np.arange(1, N - 1), size=int(rng.integers(5, 200)), replace=False)
+        C[broken] += 1e-4 * rng.uniform(0.5, 1.5, size=(len(broken), L))
+        R, dR = 0.5 * C, 0.5 * dC
+        g.set_history(t, C, dC, R, dR)
+        H = OI.History(t, C, dC, R, dR)
+        removed = g.sparsify(tol)
+        H2, ran = OS.sparsify_pass(H, tol)
+        assert ran
+        assert np.array_equal(removed, ~np.isin(H.t, H2.t)), trial
+        assert np.array_equal(g.get_history()[0], H2.t), trial
+        if trial == 5:
+            assert removed.sum() == 1
+    g.close()
+
+
 def test_checkpoint_restore_continues_bit_identically(tmp_path):
     need_gpu()
     from paper_2604_06309_gb300 import Solver
