@@ -325,7 +325,15 @@ int create_impl(const dmfe_params* pin, dmfe_solver* h) {
         TRY(dev_alloc(h, &p, (size_t)cap * L * sizeof(dbl4))); v.hist[b] = (dbl4*)p;
         if (v.precision == DMFE_FP32_COMPENSATED) {
             TRY(dev_alloc(h, &p, (size_t)cap * L * sizeof(float4))); v.hist32[b] = (float4*)p;
-            if (b == 0) { TRY(dev_alloc(h, &p, L * sizeof(float4))); v.vrow32 = (float4*)p; }
+            if (b == 0) {
+                TRY(dev_alloc(h, &p, L * sizeof(float4))); v.vrow32 = (float4*)p;
+                TRY(dev_alloc(h, &p, L * sizeof(float4))); v.row32f = (float4*)p;
+                TRY(dev_alloc(h, &p, (cap + 1) * sizeof(float4))); v.slice32 = (float4*)p;
+            }
+        }
+        if (v.precision == DMFE_FP64 && b == 0) {
+            TRY(dev_alloc(h, &p, L * sizeof(dbl4))); v.row64 = (dbl4*)p;
+            TRY(dev_alloc(h, &p, (cap + 1) * sizeof(double))); v.slice64 = (double*)p;
         }
         if (v.precision == DMFE_DOUBLE_FLOAT) {
             TRY(dev_alloc(h, &p, (size_t)cap * L * sizeof(df8))); v.histdf[b] = (df8*)p;

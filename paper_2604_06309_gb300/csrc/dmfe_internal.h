@@ -219,6 +219,10 @@ struct SolverView {
     dfslice* slicedf;     // [cap + 1] (entry n: the stage time, for a stage beyond the last slice)
     df8* vrowdf;          // [L] double-float path: virtual slice at the stage time (see prep)
     float4* vrow32;       // [L] FP32 path: the same in FP32
+    dbl4* row64;          // [L] FP64 path: the stage row {K, D, C, R} (written by the prep kernel)
+    double* slice64;      // [cap + 1] FP64 path: 1/(t_{k+1} - t_k) of each interval (prep kernel)
+    float4* row32f;       // [L] FP32 path: the stage row {K, D, C, R} in FP32 (prep kernel)
+    float4* slice32;      // [cap + 1] FP32 path: {(t - t_k)/t, t/(t_{k+1} - t_k), t_{k+1} - t_k, 0}
     int* cell;            // [L] slice of time theta_m t
     B1Desc* b1;           // [L] per-stage B1 time weights
     int hi_chunk;         // summation indices per work unit (-1: the flat split)

@@ -53,6 +53,10 @@ __device__ __forceinline__ void stage_prep_body(const SolverView& v, const doubl
             const double Dq = fp1(v.poly, Cq);
             pm += v.nu[q] * (fp2(v.poly, Cq) * Rq * Cq + Dq * Rq);
             pe += v.nu[q] * (Dq * Rq);
+            // the stage row as the FP64 and FP32 kernels read it (once per stage here instead
+            // of once per CTA there; the same operations)
+            if (v.row64) v.row64[q] = dbl4{fp2(v.poly, Cq) * Rq, Dq, Cq, Rq};
+            if (v.row32f) v.row32f[q] = make_float4((float)(fp2(v.poly, Cq) * Rq), (float)Dq, (float)Cq, (float)Rq);
             const double tau = v.theta[q] * t;
             const int c = find_slice_g(ht, n, tau);
             v.cell[q] = c;
@@ -116,6 +120,20 @@ __device__ __forceinline__ void stage_prep_body(const SolverView& v, const doubl
                     v.vrowdf[q] = df8{df_from_d(C), df_from_d(dCv), df_from_d(R), df_from_d(dRv)};
                 }
             }
+        }
+        if (q < n && v.slice64) v.slice64[q] = q + 1 < n ? 1.0 / (ht[q + 1] - ht[q]) : (ext ? 1.0 / hx : 0.0);
+        if (v.slice32 && q < (ext ? n + 1 : n)) {
+            // FP32 path: slice q (q = n: the stage time itself, the virtual slice of an
+            // extension) as complements, reciprocal widths and widths
+            const int nsl = ext ? n + 1 : n;
+            const double tk = q < n ? ht[q] : t;
+            float4 e = make_float4((float)((t - tk) / t), 0.f, 0.f, 0.f);
+            if (q + 1 < nsl) {
+                const double tk1 = q + 1 < n ? ht[q + 1] : t;
+                e.y = (float)(t / (tk1 - tk));
+                e.z = (float)(tk1 - tk);
+            }
+            v.slice32[q] = e;
         }
         if (q <= n && v.slicedf) {
             // slice q (q = n: the stage time itself, the virtual slice of an extension)

@@ -133,13 +133,12 @@ __device__ __forceinline__ void hi_f64_body(const SolverView& v, const double* _
     double* sht = reinterpret_cast<double*>(srow + L);              // [cap + 1] slice times
     double* sinvh = sht + v.cap + 1;                                // [cap + 1] 1/(t_{k+1} - t_k)
     int* scell = reinterpret_cast<int*>(sinvh + v.cap + 1);         // [L]
-    for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        double C = row[i], R = row[L + i];
-        srow[i] = dbl4{fp2(v.poly, C) * R, fp1(v.poly, C), C, R};
-    }
+    // the stage row {K, D, C, R} and the reciprocal interval widths, prepared once per stage
+    // by the prep kernel
+    for (int i = threadIdx.x; i < L; i += blockDim.x) srow[i] = v.row64[i];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         sht[i] = ht[i];
-        sinvh[i] = i + 1 < n ? 1.0 / (ht[i + 1] - ht[i]) : (ext ? 1.0 / hx : 0.0);
+        sinvh[i] = v.slice64[i];
     }
     if (threadIdx.x == 0) sht[n] = t;
     for (int m = threadIdx.x; m < L; m += blockDim.x) scell[m] = v.cell[m];
@@ -350,18 +349,13 @@ __device__ __forceinline__ void hi_f32_body(const SolverView& v, const double* _
     float* sinv = sv + v.cap + 1;                                   // [cap + 1] 1/(v_k - v_{k+1})
     float* sdt = sinv + v.cap + 1;                                  // [cap + 1] t_{k+1} - t_k
     int* scell = reinterpret_cast<int*>(sdt + v.cap + 1);           // [L]
-    for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        double C = row[i], R = row[L + i];
-        srow[i] = make_float4((float)(fp2(v.poly, C) * R), (float)fp1(v.poly, C), (float)C, (float)R);
-    }
+    // the stage row in FP32 and the slice constants, prepared once per stage by the prep kernel
+    for (int i = threadIdx.x; i < L; i += blockDim.x) srow[i] = v.row32f[i];
     for (int i = threadIdx.x; i < nsl; i += blockDim.x) {
-        const double tk = i < n ? ht[i] : t;
-        sv[i] = (float)((t - tk) / t);
-        if (i + 1 < nsl) {
-            const double tk1 = i + 1 < n ? ht[i + 1] : t;
-            sinv[i] = (float)(t / (tk1 - tk));
-            sdt[i] = (float)(tk1 - tk);
-        }
+        const float4 e = v.slice32[i];
+        sv[i] = e.x;
+        sinv[i] = e.y;
+        sdt[i] = e.z;
     }
     for (int m = threadIdx.x; m < L; m += blockDim.x) scell[m] = v.cell[m];
     __syncthreads();
