@@ -78,7 +78,7 @@ SSPRK104_REAL_STABILITY = 13.917
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "df"])
@@ -155,44 +155,86 @@ def workload(L):
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling (every 100 ms) around the timed region: the sampler is running
+    before the region starts (the constructor waits for its first sample), and the summary
+    keeps the samples whose timestamps fall inside the region that mark() and stop()
+    bracket on the host clock."""
+
+    QUERY = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, idx):
         self.p = None
+        self.t0 = None
         # the raw samples (the JSON line carries their summary); DMFE_CLOCKS_LOG keeps them
         self.path = os.environ.get("DMFE_CLOCKS_LOG") or os.path.join(tempfile.gettempdir(), "clocks_bench.csv")
         try:
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(
-                ["nvidia-smi", "-i", str(idx), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
-                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                ["nvidia-smi", "-i", str(idx), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+            return
+        deadline = time.time() + 5.0
+        while time.time() < deadline and self.p.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
+
+    def mark(self):
+        """Host time at which the timed region starts."""
+        self.t0 = time.time()
+
+    @staticmethod
+    def _stamp(x):
+        from datetime import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.strptime(x, fmt).timestamp()
+            except ValueError:
+                pass
+        return None
 
     def stop(self):
         if self.p is None:
             return None
+        t1 = time.time()
+        time.sleep(0.15)  # the sample that covers the region's end
         self.p.terminate()
         self.p.wait()
         self.f.close()
+        with open(self.path) as f:
+            return self.summarize(f.read().splitlines(), self.t0 if self.t0 is not None else t1, t1)
+
+    @classmethod
+    def summarize(cls, lines, t0, t1):
+        """Median loaded SM clock, maximum clock and active throttle reasons of the samples
+        taken in [t0, t1] (host seconds; 0.1 s of slack on each side), else of the one
+        nearest to the region's middle."""
         rows = []
-        for line in open(self.path):
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 7:
+            if len(parts) < 8:
                 continue
             try:
-                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+                rows.append((cls._stamp(parts[0]), float(parts[1]), float(parts[2]), parts[4:8]))
             except ValueError:
                 continue
         if not rows:
             return None
+        inside = [r for r in rows if r[0] is not None and t0 - 0.1 <= r[0] <= t1 + 0.1]
+        if not inside:
+            mid = 0.5 * (t0 + t1)
+            stamped = [r for r in rows if r[0] is not None]
+            inside = [min(stamped, key=lambda r: abs(r[0] - mid))] if stamped else rows[-1:]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
-        mx = max(r[1] for r in rows)
-        loaded = [r[0] for r in rows if r[0] > 0.5 * mx] or [r[0] for r in rows]
-        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+        reasons = sorted({names[k] for *_, r in inside for k in range(4) if r[k].lower() == "active"})
+        mx = max(r[2] for r in inside)
+        loaded = [r[1] for r in inside if r[1] > 0.5 * mx] or [r[1] for r in inside]
+        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(inside), "region_s": round(t1 - t0, 3)}
 
 
 def reduce_max_over_ranks(vals, world):
@@ -331,6 +373,7 @@ def _run_ours(args, rank, world, dev, stream):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(dev)
+    clocks.mark()
     evs = []
     torch.cuda.nvtx.range_push("timed_steps")
     for k in range(args.steps):
@@ -750,6 +793,7 @@ def run_batch(args):
         st0 = [b.solver(k).stats() for k in range(len(reqs))]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+        clocks.mark()
         e0.record(stream)
         tw = time.perf_counter()
         nsteps = 0
@@ -915,6 +959,7 @@ def run_serving(args, rate=20.0, seed=20260406):
     next_arrival = rng.exponential(1.0 / rate)
     submitted, results, peak_bytes, samples = 0, [], 0, []
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.mark()
     while True:
         now = time.perf_counter() - t0
         if now >= args.window:
