@@ -698,6 +698,11 @@ def run_solve(args):
                         "dt": st["dt"], "method": "ssprk104" if st["method"] == 2 else "dp5",
                         "t_switch": st["t_switch"], "E": E, "mu": mu,
                         "C": sv.get_C(t, tp).tolist(), "R": sv.get_R(t, tp).tolist()})
+            if args.out:
+                # the checkpoints so far, rewritten after each one: a run that is cut off
+                # still leaves them
+                with open(args.out + ".partial", "w") as f:
+                    json.dump(dict(runs, **{prec: {"checkpoints": rec, "time_limit_s": limit}}), f)
         runs[prec] = {"checkpoints": rec, "truncated": truncated, "time_limit_s": limit}
         sv.close()
         torch.cuda.synchronize()
