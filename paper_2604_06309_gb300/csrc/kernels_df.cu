@@ -170,7 +170,10 @@ __device__ __forceinline__ void stage_prep_body(const SolverView& v, const doubl
     }
 }
 
-// Lagrange weights on nodes 0..SW-1 at the double-float position u.
+// Lagrange weights on nodes 0..SW-1 at the double-float position u, 0 <= u <= SW - 1 (the
+// stencil base is clamped so that the position lies on the stencil). The differences u - m
+// are formed exactly as pairs (df_add_exact_const: m >= u.hi, or u.hi > m >= 1 with an
+// exactly representable difference).
 template <int SW>
 __device__ __forceinline__ void lagrange_df(df u, df (&w)[SW]);
 
@@ -178,7 +181,7 @@ __device__ __forceinline__ void lagrange_df(df u, df (&w)[SW]);
 // w3 = u(u-1)(u-2)/6, with the shared products u(u-1) and (u-2)(u-3).
 template <>
 __device__ __forceinline__ void lagrange_df<4>(df u, df (&w)[4]) {
-    const df u1 = df_add_f(u, -1.f), u2 = df_add_f(u, -2.f), u3 = df_add_f(u, -3.f);
+    const df u1 = df_add_exact_const(u, -1.f), u2 = df_add_exact_const(u, -2.f), u3 = df_add_exact_const(u, -3.f);
     const df ab = df_mul(u, u1), cd = df_mul(u2, u3);
     const df sixth = df{0.16666667163372040f, -4.9670538e-09f};  // 1/6 as a double-float
     w[0] = df_neg(df_mul(df_mul(u1, cd), sixth));
@@ -193,7 +196,7 @@ template <int SW>
 __device__ __forceinline__ void lagrange_df(df u, df (&w)[SW]) {
     df um[SW];
 #pragma unroll
-    for (int k = 0; k < SW; ++k) um[k] = df_add_f(u, -(float)k);
+    for (int k = 0; k < SW; ++k) um[k] = df_add_exact_const(u, -(float)k);
     df pre[SW], suf[SW];
     pre[0] = df{1.f, 0.f};
 #pragma unroll
@@ -408,14 +411,17 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
                     while (k < kmax && df_ge(sv[k + 1], u)) ++k;
                     while (k > 0 && df_lt(sv[k], u)) --k;
                     const df sg = df_mul(df_sub(sv[k], u), sinv[k]);
-                    const df om = df_add_f(df_neg(sg), 1.f);
+                    // 1 - sg, 3 - 2 sg and 1 - h01 exactly as pairs: 0 <= sg <= 1 up to
+                    // rounding, so each constant dominates (or Sterbenz applies)
+                    const df om = df_add_exact_const(df_neg(sg), 1.f);
                     const df om2 = df_mul(om, om), sg2 = df_mul(sg, sg);
                     s0 = k; s1 = k + 1;
                     // h01 = sg^2 (3 - 2 sg) and h00 = 1 - h01 (the value weights sum to one);
                     // the doubling of sg is exact
-                    tw2 = df_mul(sg2, df_add_f(df{-2.f * sg.hi, -2.f * sg.lo}, 3.f));
-                    tw0 = df_add_f(df_neg(tw2), 1.f);
-                    const df a1 = df_mul(sg, om2), a3 = df_mul(sg2, df_add_f(sg, -1.f));
+                    tw2 = df_mul(sg2, df_add_exact_const(df{-2.f * sg.hi, -2.f * sg.lo}, 3.f));
+                    tw0 = df_add_exact_const(df_neg(tw2), 1.f);
+                    // sg^2 (sg - 1) = -(sg^2 (1 - sg))
+                    const df a1 = df_mul(sg, om2), a3 = df_neg(df_mul(sg2, om));
                     if (k < n - 1) {
                         // a stored interval: its width in FP32 (the derivative terms are
                         // O(h) corrections)
