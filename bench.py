@@ -55,10 +55,10 @@ TOL = 1e-8
 # weighted products and sums 23.
 FLOP_PER_PAIR_S4 = 32 + 16 + 12 + 80 + 20 + 23
 # Double-float kernel, FP32 flops of the double-float arithmetic: Lagrange weights from the
-# stored positions 3 x 100, B1 110, A1 220, A2 110, B2 685, f' and f'' 210, products and
-# sums 226 (a double-float product 10, a general sum 10 or 11, a sum with a small constant
-# that is exact as a pair 4).
-DF_FP32_FLOP_PER_PAIR_S4 = 300 + 110 + 220 + 110 + 685 + 210 + 226
+# stored positions 3 x 76, B1 110, A1 220, A2 110, B2 661, f' and f'' 186, products and
+# sums 205 (a renormalised double-float product 10, one left as a raw pair 7, a general sum
+# 10 or 11, a sum with a small constant that is exact as a pair 4).
+DF_FP32_FLOP_PER_PAIR_S4 = 228 + 110 + 220 + 110 + 661 + 186 + 205
 # DRAM bytes (read + write) of one history-integral launch at this workload's state come
 # from ncu captures recorded by paper_2604_06309_gb300.traffic (null once a kernel source
 # has changed since its capture).

@@ -77,8 +77,27 @@ __device__ __forceinline__ df df_mul_f(df a, float b) {
     return fast_two_sum(p, e);
 }
 
-// a * b + c
-__device__ __forceinline__ df df_fma(df a, df b, df c) { return df_add(df_mul(a, b), c); }
+// a * b left as the pair {p, e} without the final FastTwoSum (|e| up to about 3 ulp(p) / 2
+// instead of ulp(p) / 2), for products that feed further double-float products and sums:
+// their error terms carry the larger low part, and the neglected lo * lo term grows from
+// 2^-48 to about 2^-45 of the product.
+__device__ __forceinline__ df df_mul_raw(df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df{p, e};
+}
+
+__device__ __forceinline__ df df_mul_f_raw(df a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return df{p, e};
+}
+
+// a * b + c (the sum renormalises, so the product need not)
+__device__ __forceinline__ df df_fma(df a, df b, df c) { return df_add(df_mul_raw(a, b), c); }
 
 __device__ __forceinline__ bool df_lt(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 __device__ __forceinline__ bool df_ge(df a, df b) { return !df_lt(a, b); }

@@ -182,14 +182,14 @@ __device__ __forceinline__ void lagrange_df(df u, df (&w)[SW]);
 template <>
 __device__ __forceinline__ void lagrange_df<4>(df u, df (&w)[4]) {
     const df u1 = df_add_exact_const(u, -1.f), u2 = df_add_exact_const(u, -2.f), u3 = df_add_exact_const(u, -3.f);
-    const df ab = df_mul(u, u1), cd = df_mul(u2, u3);
+    const df ab = df_mul_raw(u, u1), cd = df_mul_raw(u2, u3);
     const df sixth = df{0.16666667163372040f, -4.9670538e-09f};  // 1/6 as a double-float
-    w[0] = df_neg(df_mul(df_mul(u1, cd), sixth));
-    const df h1 = df_mul(u, cd);
+    w[0] = df_neg(df_mul_raw(df_mul_raw(u1, cd), sixth));
+    const df h1 = df_mul_raw(u, cd);
     w[1] = df{h1.hi * 0.5f, h1.lo * 0.5f};
-    const df h2 = df_mul(ab, u3);
+    const df h2 = df_mul_raw(ab, u3);
     w[2] = df{h2.hi * -0.5f, h2.lo * -0.5f};
-    w[3] = df_mul(df_mul(ab, u2), sixth);
+    w[3] = df_mul_raw(df_mul_raw(ab, u2), sixth);
 }
 
 template <int SW>
@@ -200,10 +200,10 @@ __device__ __forceinline__ void lagrange_df(df u, df (&w)[SW]) {
     df pre[SW], suf[SW];
     pre[0] = df{1.f, 0.f};
 #pragma unroll
-    for (int k = 1; k < SW; ++k) pre[k] = df_mul(pre[k - 1], um[k - 1]);
+    for (int k = 1; k < SW; ++k) pre[k] = df_mul_raw(pre[k - 1], um[k - 1]);
     suf[SW - 1] = df{1.f, 0.f};
 #pragma unroll
-    for (int k = SW - 2; k >= 0; --k) suf[k] = df_mul(suf[k + 1], um[k + 1]);
+    for (int k = SW - 2; k >= 0; --k) suf[k] = df_mul_raw(suf[k + 1], um[k + 1]);
 #pragma unroll
     for (int k = 0; k < SW; ++k) {
         // 1 / prod_{m != k} (k - m) as a double-float constant
@@ -213,7 +213,7 @@ __device__ __forceinline__ void lagrange_df(df u, df (&w)[SW]) {
             if (m != k) c /= (double)(k - m);
         const float ch = (float)c;
         const float cl = (float)(c - (double)ch);
-        w[k] = df_mul(df_mul(pre[k], suf[k]), df{ch, cl});
+        w[k] = df_mul_raw(df_mul_raw(pre[k], suf[k]), df{ch, cl});
     }
 }
 
@@ -410,28 +410,28 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
                     int k = scell[c2 < L ? c2 : L - 1];
                     while (k < kmax && df_ge(sv[k + 1], u)) ++k;
                     while (k > 0 && df_lt(sv[k], u)) --k;
-                    const df sg = df_mul(df_sub(sv[k], u), sinv[k]);
+                    const df sg = df_mul_raw(df_sub(sv[k], u), sinv[k]);
                     // 1 - sg, 3 - 2 sg and 1 - h01 exactly as pairs: 0 <= sg <= 1 up to
                     // rounding, so each constant dominates (or Sterbenz applies)
                     const df om = df_add_exact_const(df_neg(sg), 1.f);
-                    const df om2 = df_mul(om, om), sg2 = df_mul(sg, sg);
+                    const df om2 = df_mul_raw(om, om), sg2 = df_mul_raw(sg, sg);
                     s0 = k; s1 = k + 1;
                     // h01 = sg^2 (3 - 2 sg) and h00 = 1 - h01 (the value weights sum to one);
                     // the doubling of sg is exact
-                    tw2 = df_mul(sg2, df_add_exact_const(df{-2.f * sg.hi, -2.f * sg.lo}, 3.f));
+                    tw2 = df_mul_raw(sg2, df_add_exact_const(df{-2.f * sg.hi, -2.f * sg.lo}, 3.f));
                     tw0 = df_add_exact_const(df_neg(tw2), 1.f);
                     // sg^2 (sg - 1) = -(sg^2 (1 - sg))
-                    const df a1 = df_mul(sg, om2), a3 = df_neg(df_mul(sg2, om));
+                    const df a1 = df_mul_raw(sg, om2), a3 = df_neg(df_mul_raw(sg2, om));
                     if (k < n - 1) {
                         // a stored interval: its width in FP32 (the derivative terms are
                         // O(h) corrections)
-                        tw1 = df_mul_f(a1, sh[k]);
-                        tw3 = df_mul_f(a3, sh[k]);
+                        tw1 = df_mul_f_raw(a1, sh[k]);
+                        tw3 = df_mul_f_raw(a3, sh[k]);
                     } else {
                         // the virtual interval: the width in full double-float, since the
                         // virtual slice's derivative need not be small
-                        tw1 = df_mul(a1, hx_df);
-                        tw3 = df_mul(a3, hx_df);
+                        tw1 = df_mul_raw(a1, hx_df);
+                        tw3 = df_mul_raw(a3, hx_df);
                     }
                 }
                 df w[SW];
@@ -481,17 +481,17 @@ __device__ __forceinline__ void hi_df_body(const SolverView& v, double t_arg, in
             }
             df f1a, f2a, f1b, f2b;
             poly12_df_pair(v.poly, CB1, CB2, f1a, f2a, f1b, f2b);
-            const df nRB1 = df_mul(nui, RB1);
-            const df nRA2 = df_mul(nui, RA2);
-            const df nKA2 = df_mul(nui, KA2);
-            dacc_add(acc[0], df_mul(nui, KA1), CB1);
+            const df nRB1 = df_mul_raw(nui, RB1);
+            const df nRA2 = df_mul_raw(nui, RA2);
+            const df nKA2 = df_mul_raw(nui, KA2);
+            dacc_add(acc[0], df_mul_raw(nui, KA1), CB1);
             dacc_add(acc[1], nKA2, CB2);
             dacc_add(acc[2], DA1, nRB1);
             dacc_add(acc[3], nKA2, RB2);
-            dacc_add(acc[4], df_mul(f2a, CA1), nRB1);
-            dacc_add(acc[5], df_mul(nui, f1a), RA1);
+            dacc_add(acc[4], df_mul_raw(f2a, CA1), nRB1);
+            dacc_add(acc[5], df_mul_raw(nui, f1a), RA1);
             dacc_add(acc[6], f1b, nRA2);
-            dacc_add(acc[7], df_mul(f2b, RB2), nRA2);
+            dacc_add(acc[7], df_mul_raw(f2b, RB2), nRA2);
             dacc_add(acc[8], df_fma(f2a, CB1, f1a), nRB1);
             if (i == 0) c_at_0 = CB1;
         }
